@@ -1,0 +1,447 @@
+"""Pins of the CPU oracle to facts fixed by the mathematics, not by itself.
+
+Each oracle routine is checked against at least one of: a closed form (the
+decay factor of a discrete Fourier/sine mode, the leapfrog recurrence of a
+plane wave), an invariant (constant fields, sum conservation, the maximum
+principle, the discrete leapfrog energy), an exact golden fixture (Example 1
+of Sec. III-A in rational arithmetic), brute force through an explicitly
+assembled operator matrix on tiny grids, and for the adjoint the dot-product
+identity and central finite differences.  The cases are picked so that a
+dropped term, a wrong sign, a wrong index or a transposed operand fails one.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.taylor import taylor_second_derivative_coeffs
+from paper_2512_19851_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ---------------------------------------------------------------- helpers
+def assemble(shape, offsets, weights, periodic, bc_value):
+    """Dense matrix A and vector b with u_{t+1} = A u_t + b, built point by
+    point from the neighbour list (brute force, tiny grids only)."""
+    shape = tuple(shape)
+    n = int(np.prod(shape))
+    A = np.zeros((n, n))
+    b = np.zeros(n)
+    for p in np.ndindex(*shape):
+        ip = np.ravel_multi_index(p, shape)
+        for o, w in zip(offsets, weights):
+            q = [pi + oi for pi, oi in zip(p, o)]
+            if periodic:
+                q = [qi % si for qi, si in zip(q, shape)]
+            elif any(qi < 0 or qi >= si for qi, si in zip(q, shape)):
+                b[ip] += w * bc_value
+                continue
+            A[ip, np.ravel_multi_index(tuple(q), shape)] += w
+    return A, b
+
+
+def assemble_varcoef7(kappa, periodic, bc_value):
+    shape = kappa.shape
+    offs = [(0, 0, -1), (0, 0, 1), (0, -1, 0), (0, 1, 0), (-1, 0, 0), (1, 0, 0)]
+    n = kappa.size
+    A = np.zeros((n, n))
+    b = np.zeros(n)
+    for p in np.ndindex(*shape):
+        ip = np.ravel_multi_index(p, shape)
+        k = kappa[p]
+        A[ip, ip] += 1.0 - 6.0 * k
+        for o in offs:
+            q = [pi + oi for pi, oi in zip(p, o)]
+            if periodic:
+                q = [qi % si for qi, si in zip(q, shape)]
+            elif any(qi < 0 or qi >= si for qi, si in zip(q, shape)):
+                b[ip] += k * bc_value
+                continue
+            A[ip, np.ravel_multi_index(tuple(q), shape)] += k
+    return A, b
+
+
+def five_point(a):
+    return inputs.OFFSETS_5PT, [1 - 4 * a, a, a, a, a]
+
+
+def seven_point(a):
+    return inputs.OFFSETS_7PT, [1 - 6 * a] + [a] * 6
+
+
+# ---------------------------------------------------------------- golden
+def test_example1_golden_exact():
+    """Example 1 (Sec. III-A): boundary 1, weight 1/4, 10 iterations.  All
+    values are dyadic, so double precision must match the exact fixture."""
+    rows = []
+    with open(os.path.join(HERE, "golden", "example1_laplace_8x6_10it.txt")) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            rows.append([float(Fraction(t)) for t in line.split()])
+    gold = np.array(rows)
+    offs = [(-1, 0), (1, 0), (0, -1), (0, 1)]
+    got = oracle.sweep_const(np.zeros(gold.shape), offs, [0.25] * 4, False, 1.0, 10)
+    assert np.array_equal(got, gold)
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("shape,k,a,steps", [((9, 13), (2, 3), 0.2, 17), ((16, 11), (1, 2), 0.2, 100),
+                                             ((7, 7), (1, 3), 0.1, 20)])
+def test_dirichlet_sine_mode_decay(shape, k, a, steps):
+    """A Dirichlet sine mode sin(pi k (i+1)/(n+1)) decays by
+    1 - 4a (sin^2(pi ky/(2(ny+1))) + sin^2(pi kx/(2(nx+1)))) per step."""
+    ny, nx = shape
+    ky, kx = k
+    my = np.sin(np.pi * ky * np.arange(1, ny + 1) / (ny + 1))
+    mx = np.sin(np.pi * kx * np.arange(1, nx + 1) / (nx + 1))
+    u0 = my[:, None] * mx[None, :]
+    lam = 1 - 4 * a * (math.sin(math.pi * ky / (2 * (ny + 1))) ** 2 +
+                       math.sin(math.pi * kx / (2 * (nx + 1))) ** 2)
+    offs, w = five_point(a)
+    got = oracle.sweep_const(u0, offs, w, False, 0.0, steps)
+    assert oracle.normwise_error(got, lam ** steps * u0) < 1e-13
+
+
+def test_periodic_2d_fourier_decay():
+    """Periodic 2D: the eigenvalue of a Fourier mode is the one quoted in the
+    workload description, 1 - 4a(sin^2(pi kx/N) + sin^2(pi ky/N))."""
+    n, a, steps = 24, 0.2, 30
+    kx, ky = 1, 2
+    i = np.arange(n)
+    u0 = np.cos(2 * np.pi * ky * i / n)[:, None] * np.sin(2 * np.pi * kx * i / n)[None, :]
+    lam = 1 - 4 * a * (math.sin(math.pi * kx / n) ** 2 + math.sin(math.pi * ky / n) ** 2)
+    offs, w = five_point(a)
+    got = oracle.sweep_const(u0, offs, w, True, 0.0, steps)
+    assert oracle.normwise_error(got, lam ** steps * u0) < 1e-13
+
+
+def test_periodic_3d_sine_modes_closed_form():
+    """heat3d recipe without noise: sum of product-of-sines modes, each
+    decaying by 1 - 4 alpha sum_d sin^2(pi k_d / N_d)."""
+    shape = (12, 10, 16)
+    alpha, steps = 0.1, 25
+    h = inputs.heat3d(shape=shape, noise=False)
+    expect = np.zeros(shape)
+    for (kz, ky, kx), amp in zip(h.wavenumbers, h.amplitudes):
+        lam = 1 - 4 * alpha * sum(math.sin(math.pi * kd / nd) ** 2
+                                  for kd, nd in zip((kz, ky, kx), shape))
+        mode = (np.sin(2 * np.pi * kz * np.arange(shape[0]) / shape[0])[:, None, None] *
+                np.sin(2 * np.pi * ky * np.arange(shape[1]) / shape[1])[None, :, None] *
+                np.sin(2 * np.pi * kx * np.arange(shape[2]) / shape[2])[None, None, :])
+        expect += amp * lam ** steps * mode
+    offs, w = seven_point(alpha)
+    got = oracle.sweep_const(h.u0, offs, w, True, 0.0, steps)
+    assert oracle.normwise_error(got, expect) < 1e-12
+
+
+# ---------------------------------------------------------------- invariants
+def test_constant_field_invariant():
+    """Paper's boundary value 1 with a constant interior of 1 stays 1 under
+    weights 1/4 (exact), and a periodic constant stays under 7-point."""
+    u = np.ones((10, 7))
+    got = oracle.sweep_const(u, [(-1, 0), (1, 0), (0, -1), (0, 1)], [0.25] * 4, False, 1.0, 50)
+    assert np.array_equal(got, u)
+    v = np.full((6, 5, 7), 3.5)
+    offs, w = seven_point(0.125)
+    assert np.array_equal(oracle.sweep_const(v, offs, w, True, 0.0, 9), v)
+
+
+def test_periodic_sum_conserved():
+    u0 = inputs.heat3d(shape=(8, 9, 10)).u0
+    offs, w = seven_point(0.1)
+    s0 = math.fsum(u0.ravel())
+    got = oracle.sweep_const(u0, offs, w, True, 0.0, 30)
+    assert abs(math.fsum(got.ravel()) - s0) < 1e-12 * np.abs(u0).sum()
+
+
+def test_max_principle():
+    u0 = inputs.heat2d(shape=(20, 17))
+    offs, w = five_point(0.2)
+    lo, hi = u0.min(), u0.max()
+    u = u0
+    for _ in range(10):
+        u = oracle.sweep_const(u, offs, w, False, 0.0, 3)
+        assert u.min() >= min(lo, 0.0) - 1e-15 and u.max() <= hi + 1e-15
+    # mass leaks out through a zero Dirichlet boundary
+    assert u.sum() < u0.sum()
+
+
+def test_linearity_periodic():
+    shape = (6, 7, 5)
+    rng = np.random.default_rng(11)
+    x, y = rng.standard_normal(shape), rng.standard_normal(shape)
+    offs, w = seven_point(0.1)
+    lhs = oracle.sweep_const(2.5 * x - 0.75 * y, offs, w, True, 0.0, 6)
+    rhs = 2.5 * oracle.sweep_const(x, offs, w, True, 0.0, 6) - 0.75 * oracle.sweep_const(y, offs, w, True, 0.0, 6)
+    assert oracle.normwise_error(lhs, rhs) < 1e-13
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("shape", [(6, 7), (4, 5, 3)])
+def test_sweep_vs_assembled_matrix(shape, periodic):
+    """Asymmetric offsets (radius 2) and unequal weights: the oracle equals
+    u_S = A(...(A u_0 + b)...) + b with A, b assembled point by point."""
+    rng = np.random.default_rng(7)
+    nd = len(shape)
+    offs = [tuple(int(v) for v in rng.integers(-2, 3, size=nd)) for _ in range(6)]
+    offs[0] = (0,) * nd
+    w = list(rng.standard_normal(6) * 0.3)
+    u0 = rng.standard_normal(shape)
+    steps = 5
+    A, b = assemble(shape, offs, w, periodic, 0.7)
+    v = u0.ravel().copy()
+    for _ in range(steps):
+        v = A @ v + b
+    got = oracle.sweep_const(u0, offs, w, periodic, 0.7, steps)
+    assert oracle.normwise_error(got.ravel(), v) < 1e-13
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_varcoef7_vs_assembled_matrix(periodic):
+    shape = (4, 3, 5)
+    rng = np.random.default_rng(3)
+    kappa = rng.uniform(0.0, 0.16, size=shape)
+    u0 = rng.random(shape)
+    A, b = assemble_varcoef7(kappa, periodic, 0.3)
+    v = u0.ravel().copy()
+    for _ in range(7):
+        v = A @ v + b
+    got = oracle.varcoef7_forward(u0, kappa, periodic, 0.3, 7)
+    assert oracle.normwise_error(got.ravel(), v) < 1e-13
+
+
+# ---------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("periodic", [False, True])
+def test_adjoint_equals_matrix_transpose(periodic):
+    """lambda_0 = (A_S ... A_1)^T lambda_S with the assembled matrices, and
+    the dot-product identity <S x, y> = <x, S^T y>."""
+    shape = (3, 4, 5)
+    rng = np.random.default_rng(5)
+    kappa = rng.uniform(0.0, 0.16, size=shape)
+    A, _ = assemble_varcoef7(kappa, periodic, 0.0)
+    steps = 6
+    x = rng.standard_normal(shape)
+    y = rng.standard_normal(shape)
+    _, states = oracle.varcoef7_forward(x, kappa, periodic, 0.0, steps, store_states=True)
+    lam0, _ = oracle.varcoef7_adjoint(states[:steps], kappa, y, periodic, 0.0)
+    M = np.linalg.matrix_power(A, steps)
+    assert oracle.normwise_error(lam0.ravel(), M.T @ y.ravel()) < 1e-13
+    sx = states[steps]
+    lhs = float(np.dot(sx.ravel(), y.ravel()))
+    rhs = float(np.dot(x.ravel(), lam0.ravel()))
+    assert abs(lhs - rhs) < 1e-13 * (abs(lhs) + 1.0)
+
+
+def test_adjoint_symmetric_special_case():
+    """Constant kappa with a periodic boundary gives a symmetric operator:
+    one transpose step equals one forward step."""
+    shape = (6, 5, 4)
+    kappa = np.full(shape, 0.11)
+    y = np.random.default_rng(9).standard_normal(shape)
+    _, states = oracle.varcoef7_forward(np.zeros(shape), kappa, True, 0.0, 1, store_states=True)
+    lam, _ = oracle.varcoef7_adjoint(states[:1], kappa, y, True, 0.0)
+    fwd = oracle.varcoef7_forward(y, kappa, True, 0.0, 1)
+    assert oracle.normwise_error(lam, fwd) < 1e-15
+
+
+def test_gradient_central_differences():
+    """Loss 0.5||u_S - target||^2: gradients w.r.t. u_0 and kappa against
+    central differences (double precision, 8 random directions + coordinates)."""
+    shape = (5, 4, 6)
+    v = inputs.varcoef3d(shape=shape)
+    steps, bc = 12, 0.25
+    loss, _, g_u0, g_k = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, False, bc, steps, 4)
+
+    def L(u0, kappa):
+        uT = oracle.varcoef7_forward(u0, kappa, False, bc, steps)
+        return 0.5 * float(np.sum((uT - v.target) ** 2))
+
+    assert abs(L(v.u0, v.kappa) - loss) < 1e-12 * loss
+    rng = np.random.default_rng(1)
+    eps = 1e-6
+    for i in range(8):
+        du = rng.standard_normal(shape)
+        du /= np.linalg.norm(du)
+        dk = rng.standard_normal(shape)
+        dk /= np.linalg.norm(dk)
+        fd_u = (L(v.u0 + eps * du, v.kappa) - L(v.u0 - eps * du, v.kappa)) / (2 * eps)
+        fd_k = (L(v.u0, v.kappa + eps * dk) - L(v.u0, v.kappa - eps * dk)) / (2 * eps)
+        assert abs(fd_u - np.sum(g_u0 * du)) < 1e-7 * (abs(fd_u) + 1e-3)
+        assert abs(fd_k - np.sum(g_k * dk)) < 1e-7 * (abs(fd_k) + 1e-3)
+    for j in range(16):
+        p = tuple(int(c) for c in rng.integers(0, shape))
+        e = np.zeros(shape)
+        e[p] = 1.0
+        fd_k = (L(v.u0, v.kappa + eps * e) - L(v.u0, v.kappa - eps * e)) / (2 * eps)
+        assert abs(fd_k - g_k[p]) < 1e-7 * (abs(fd_k) + 1e-3)
+
+
+def test_checkpointing_bitwise_equal_store_all():
+    shape = (6, 5, 7)
+    v = inputs.varcoef3d(shape=shape)
+    a = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, False, 0.0, 20, 20)
+    for m in (1, 3, 7):
+        b = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, False, 0.0, 20, m)
+        assert a[0] == b[0]
+        assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+
+
+def test_adjoint_threads_bitwise():
+    shape = (9, 6, 5)
+    v = inputs.varcoef3d(shape=shape)
+    for periodic in (False, True):
+        r1 = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, 0.0, 8, 3, threads=1)
+        r4 = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, 0.0, 8, 3, threads=4)
+        assert np.array_equal(r1[2], r4[2]) and np.array_equal(r1[3], r4[3])
+
+
+# ---------------------------------------------------------------- wave / leapfrog
+def test_taylor_coefficients():
+    """The solved coefficients satisfy the moment conditions (checked here by
+    direct summation) and the symbol a_0 + 2 sum a_j cos(j t) matches -t^2 to
+    8th order."""
+    a = taylor_second_derivative_coeffs(4)
+    for q in range(0, 5):
+        mom = (a[0] if q == 0 else 0) + 2 * sum(a[j] * Fraction(j) ** (2 * q) for j in range(1, 5))
+        assert mom == (2 if q == 1 else 0)
+    af = [float(x) for x in a]
+    for t in (0.05, 0.1, 0.2):
+        sym = af[0] + 2 * sum(af[j] * math.cos(j * t) for j in range(1, 5))
+        assert abs(sym + t * t) < 0.1 * t ** 10
+    assert abs(af[0] + 205 / 72) < 1e-15 and abs(af[4] + 1 / 560) < 1e-18
+
+
+def _lap8(u, a, periodic):
+    """Radius-4 star Laplacian by array shifts (zero ghosts or wrap)."""
+    out = 3 * a[0] * u
+    for ax in range(3):
+        for j in range(1, 5):
+            if periodic:
+                out = out + a[j] * (np.roll(u, -j, axis=ax) + np.roll(u, j, axis=ax))
+            else:
+                pad = [(0, 0)] * 3
+                pad[ax] = (4, 4)
+                up = np.pad(u, pad)
+                sl_p = [slice(None)] * 3
+                sl_m = [slice(None)] * 3
+                sl_p[ax] = slice(4 + j, 4 + j + u.shape[ax])
+                sl_m[ax] = slice(4 - j, 4 - j + u.shape[ax])
+                out = out + a[j] * (up[tuple(sl_p)] + up[tuple(sl_m)])
+    return out
+
+
+def test_wave_plane_wave_recurrence():
+    """Periodic, constant m: a cosine mode obeys the scalar recurrence
+    g_{n+1} = (2 + m sigma) g_n - g_{n-1}, sigma = sum_d sym(theta_d)."""
+    shape = (16, 12, 20)
+    a = [float(x) for x in taylor_second_derivative_coeffs(4)]
+    k = (2, 1, 3)
+    th = [2 * math.pi * kd / nd for kd, nd in zip(k, shape)]
+    mode = (np.cos(th[0] * np.arange(shape[0]))[:, None, None] *
+            np.cos(th[1] * np.arange(shape[1]))[None, :, None] *
+            np.cos(th[2] * np.arange(shape[2]))[None, None, :])
+    sigma = sum(a[0] + 2 * sum(a[j] * math.cos(j * t) for j in range(1, 5)) for t in th)
+    mval = 0.09
+    g_nm1, g_n = 0.8, 1.0
+    steps = 57
+    un, unm1 = oracle.wave25(g_n * mode, g_nm1 * mode, np.full(shape, mval), a, None, None,
+                             True, 0.0, steps)
+    for _ in range(steps):
+        g_nm1, g_n = g_n, (2 + mval * sigma) * g_n - g_nm1
+    assert oracle.normwise_error(un, g_n * mode) < 1e-12
+    assert oracle.normwise_error(unm1, g_nm1 * mode) < 1e-12
+
+
+def test_wave_source_injection():
+    shape = (11, 11, 11)
+    a = [float(x) for x in taylor_second_derivative_coeffs(4)]
+    m = np.full(shape, 0.05)
+    src = (5, 5, 5)
+    s = [0.7, -0.2]
+    z = np.zeros(shape)
+    u1, u0 = oracle.wave25(z, z, m, a, src, s, False, 0.0, 1)
+    e = np.zeros(shape)
+    e[src] = 0.7
+    assert np.array_equal(u1, e) and np.array_equal(u0, z)
+    u2, u1b = oracle.wave25(z, z, m, a, src, s, False, 0.0, 2)
+    expect = 2 * e + m * _lap8(e, a, False)
+    expect[src] += -0.2
+    assert np.array_equal(u1b, e)
+    assert oracle.normwise_error(u2, expect) < 1e-15
+
+
+def test_wave_energy_conserved():
+    """Dirichlet-zero, layered m, no source: the discrete leapfrog energy
+    E = (u1-u0)^T M^-1 (u1-u0) - u1^T L u0 is constant."""
+    shape = (12, 9, 10)
+    a = [float(x) for x in taylor_second_derivative_coeffs(4)]
+    rng = np.random.default_rng(2)
+    m = np.repeat(rng.uniform(0.02, 0.15, size=shape[0]), shape[1] * shape[2]).reshape(shape)
+    u_nm1 = rng.standard_normal(shape)
+    u_n = u_nm1 + 0.1 * rng.standard_normal(shape)
+
+    def energy(u1, u0):
+        d = u1 - u0
+        return float(np.sum(d * d / m) - np.sum(u1 * _lap8(u0, a, False)))
+
+    e0 = energy(u_n, u_nm1)
+    cur, old = u_n, u_nm1
+    for _ in range(6):
+        cur, old = oracle.wave25(cur, old, m, a, None, None, False, 0.0, 5)
+        assert abs(energy(cur, old) - e0) < 1e-11 * abs(e0)
+
+
+def test_wave_matches_shift_formula_dirichlet():
+    """Variable m, Dirichlet: the oracle's gather equals the update written
+    with array shifts on a zero-padded copy (independent indexing)."""
+    shape = (7, 9, 8)
+    a = [float(x) for x in taylor_second_derivative_coeffs(4)]
+    rng = np.random.default_rng(4)
+    m = rng.uniform(0.01, 0.15, size=shape)
+    un, unm1 = rng.standard_normal(shape), rng.standard_normal(shape)
+    got, prev = oracle.wave25(un, unm1, m, a, (3, 4, 2), [0.5], False, 0.0, 1)
+    expect = 2 * un - unm1 + m * _lap8(un, a, False)
+    expect[3, 4, 2] += 0.5
+    assert np.array_equal(prev, un)
+    assert oracle.normwise_error(got, expect) < 1e-14
+
+
+# ---------------------------------------------------------------- reductions / threads / fp32
+def test_reduce_matches_fsum():
+    rng = np.random.default_rng(8)
+    a = rng.standard_normal(10007)
+    b = rng.standard_normal(10007)
+    s, q, mx = oracle.reduce(a, b)
+    d = a - b
+    # recursive summation error bound |s - exact| <= (n-1) u sum|d_i|
+    u = 2.0 ** -53
+    assert abs(s - math.fsum(d)) <= (d.size - 1) * u * math.fsum(np.abs(d))
+    assert abs(q - math.fsum(d * d)) <= d.size * u * math.fsum(d * d)
+    assert mx == float(np.max(np.abs(d)))
+    assert oracle.reduce(np.array([3.0, -4.0]))[1] == 25.0
+
+
+def test_threads_bitwise_identical():
+    u0 = inputs.heat3d(shape=(10, 12, 9)).u0
+    offs, w = seven_point(0.1)
+    r1 = oracle.sweep_const(u0, offs, w, True, 0.0, 7, threads=1)
+    r4 = oracle.sweep_const(u0, offs, w, True, 0.0, 7, threads=4)
+    assert np.array_equal(r1, r4)
+
+
+def test_single_precision_build_same_definition():
+    """The float build evaluates the same definition: close to the double
+    result at float accuracy, but not bitwise equal."""
+    u0 = inputs.heat2d(shape=(33, 40))
+    offs, w = five_point(0.2)
+    r64 = oracle.sweep_const(u0, offs, w, False, 0.0, 50)
+    r32 = oracle.sweep_const(u0, offs, w, False, 0.0, 50, dtype=np.float32)
+    err = oracle.normwise_error(r32, r64)
+    assert r32.dtype == np.float32
+    assert 1e-9 < err < 1e-5
