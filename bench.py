@@ -1,0 +1,453 @@
+"""Benchmark of the stencil hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--headline-only]
+
+Workload (one "step"): the 3D 7-point heat sweep on a 512^3 periodic grid,
+u <- u + 0.1 (sum of 6 neighbours - 6u), 100 sweeps, FP32 storage and
+arithmetic, followed by the FP64 interior reduction (sum, sum of squares,
+max |u|) of the result.  Inputs are the seeded synthetic heat3d field (8 sine
+modes + N(0, 0.01) noise), resident in HBM before timing; each buffer is
+512 MiB, larger than the 129 MB L2, so no flush is needed between steps.
+
+Metric: grid-point updates per second (GLUP/s = 1e9 interior updates / s)
+and the fraction of the HBM roofline of the dominant kernel (the sweep):
+algorithmic bytes = 8 per point per sweep (one FP32 read, one FP32 write).
+
+Printed: one JSON line (rank 0).  Also measured in the same run unless
+--headline-only: the FP64 variant, the 2D 5-point FP64 256^2 case, the
+radius-4 leapfrog wave, the variable-coefficient forward and adjoint, and the
+batched 512-grid form, each with its own roofline numbers.
+
+--impl reference times the CPU oracle (plain C loops, double precision) on
+the host cores on the same workload, a bounded slab per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N3 = 512
+SWEEPS = 100
+WORKLOAD = "heat3d 7-point periodic 512^3, 100 sweeps per step, FP32 + FP64 reduction"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_sha(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2512_19851_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key: str, sha: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[key]
+        return float(e["dram_bytes_per_launch"]) if e.get("source_sha") == sha else None
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2512_19851_gb300 import abi, inputs
+    from paper_2512_19851_gb300.grid import Grid
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the GPU arm has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    hbm_peak, peak_kind = peaks()
+
+    h = inputs.heat3d(n=N3)
+    u0 = h.u0
+    w = [0.4] + [0.1] * 6
+    g = Grid((N3, N3, N3), inputs.OFFSETS_7PT, w, periodic=True, dtype=torch.float32, device=dev)
+    g.set_field(u0)
+    stream = torch.cuda.Stream(device=dev)
+    red = torch.empty(3, dtype=torch.float64, device=dev)
+
+    def one_step():
+        abi.stencil_step(g.h, SWEEPS, stream)
+        cur = g.bufs[g.current_slot()]
+        abi.stencil_reduce(g.h, cur.data_ptr(), 0, red.data_ptr(), stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            abi.stencil_step(g.h, SWEEPS, stream)
+            ev[i][1].record(stream)
+            cur = g.bufs[g.current_slot()]
+            abi.stencil_reduce(g.h, cur.data_ptr(), 0, red.data_ptr(), stream)
+            ev[i][2].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    ms_total = t0.elapsed_time(t1)
+    sweep_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    red_ms = [b.elapsed_time(c) for _, b, c in ev]
+    if pg:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    pts = N3 ** 3 * SWEEPS
+    value = ws * pts * args.steps / (ms_total * 1e-3) / 1e9
+    per_sweep_s = statistics.mean(sweep_ms) * 1e-3 / SWEEPS
+    achieved = 8.0 * N3 ** 3 / per_sweep_s / 1e9
+    kname = g.kernel
+    sha = source_sha("k_star3d.cu")
+    traffic = ncu_traffic("heat3d_f32", sha)
+    clocks = clk.summary()
+    result = float(red[1].item())
+    assert np.isfinite(result)
+
+    # ---------------- end to end through the public API (host buffers)
+    src = torch.from_numpy(u0.astype(np.float32)).pin_memory()
+    dst = torch.empty((N3, N3, N3), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        abi.stencil_run_host(g.h, SWEEPS, src.data_ptr(), dst.data_ptr(), stream)
+    torch.cuda.synchronize(dev)
+    e_steps = max(3, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        abi.stencil_run_host(g.h, SWEEPS, src.data_ptr(), dst.data_ptr(), stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e_ms = e0.elapsed_time(e1) / e_steps
+    if pg:
+        t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e_ms = float(t.item())
+    e2e = {"value": ws * pts / (e_ms * 1e-3) / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": int(src.numel() * 4),
+           "d2h_bytes_per_step": int(dst.numel() * 4), "ms_per_step": e_ms,
+           "api": "stencil_run_host (pinned host in, 100 sweeps, pinned host out)"}
+    g.close()
+    del src, dst
+
+    line = {
+        "metric": "grid-point updates/s (GLUP/s) and % of HBM roofline, forward and adjoint",
+        "value": value,
+        "unit": "GLUP/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded heat3d: 8 sine modes + N(0,0.01) noise)",
+        "config": {"workload": WORKLOAD, "grid": [N3, N3, N3], "sweeps_per_step": SWEEPS, "boundary": "periodic",
+                   "l2": "inputs larger than L2 (512 MiB per buffer), no flush", "parallelism":
+                   "replicas only" if ws > 1 else "single GPU", "kernel": kname},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_kind,
+                     "kernel": kname, "algorithmic_bytes_per_launch": 8 * N3 ** 3,
+                     "sweep_us": per_sweep_s * 1e6, "reduce_us": statistics.mean(red_ms) * 1e3},
+        "e2e": e2e,
+        "gpu_launches": args.steps * (SWEEPS + 2),
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.headline_only:
+        line["extra"] = extra_configs(dev, hbm_peak)
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def _time(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps * 1e-3
+
+
+def extra_configs(dev, hbm_peak):
+    """The other workloads, each timed with CUDA events (seconds per call)."""
+    import numpy as np
+    import torch
+
+    from paper_2512_19851_gb300 import abi, inputs, stencils
+    from paper_2512_19851_gb300.grid import Batch, Grid, VarCoefProblem
+
+    out = {}
+    s = torch.cuda.Stream(device=dev)
+    # heat3d FP64 (same workload, double)
+    h = inputs.heat3d(n=N3)
+    g = Grid((N3,) * 3, inputs.OFFSETS_7PT, [0.4] + [0.1] * 6, periodic=True, dtype=torch.float64, device=dev)
+    g.set_field(h.u0)
+    del h
+    t = _time(lambda: abi.stencil_step(g.h, SWEEPS, s), 2, s)
+    per = t / SWEEPS
+    out["heat3d_f64"] = {"glups": N3 ** 3 * SWEEPS / t / 1e9, "us_per_sweep": per * 1e6,
+                         "hbm_gbs": 16 * N3 ** 3 / per / 1e9, "hbm_frac": 16 * N3 ** 3 / per / 1e9 / hbm_peak,
+                         "kernel": g.kernel}
+    g.close()
+    torch.cuda.empty_cache()
+    # heat2d FP64 256^2 Dirichlet, 100 steps
+    u0 = inputs.heat2d()
+    g = Grid((256, 256), inputs.OFFSETS_5PT, [0.2] * 5, dtype=torch.float64, device=dev)
+    g.set_field(u0)
+    t = _time(lambda: abi.stencil_step(g.h, 100, s), 20, s)
+    out["heat2d_f64"] = {"glups": 256 * 256 * 100 / t / 1e9, "us_per_step": t / 100 * 1e6,
+                         "us_per_run": t * 1e6, "kernel": g.kernel}
+    g.close()
+    # wave, radius-4 leapfrog FP32, 1000 steps
+    wv = inputs.wave3d(n=N3, steps=1000)
+    offs, alpha, beta = stencils.wave25()
+    g = Grid((N3,) * 3, offs, alpha, beta, periodic=False, dtype=torch.float32, time_levels=2,
+             device=dev)
+    g.set_coeff(wv.m)
+    z = np.zeros((N3,) * 3, dtype=np.float32)
+    g.set_levels(z, z)
+    g.set_source(wv.src, wv.amps)
+    del wv, z
+
+    def wave_run():
+        g.set_step_index(0)
+        abi.stencil_step(g.h, 1000, s)
+
+    t = _time(wave_run, 1, s)
+    per = t / 1000
+    out["wave3d_f32"] = {"glups": N3 ** 3 * 1000 / t / 1e9, "us_per_step": per * 1e6,
+                         "hbm_gbs": 16 * N3 ** 3 / per / 1e9, "hbm_frac": 16 * N3 ** 3 / per / 1e9 / hbm_peak,
+                         "kernel": g.kernel, "bytes_per_point": 16}
+    g.close()
+    torch.cuda.empty_cache()
+    # variable-coefficient forward + adjoint, 256^3, 200 steps, ckpt 20
+    v = inputs.varcoef3d(n=256)
+    g = Grid((256,) * 3, inputs.OFFSETS_7PT, [1.0] + [0.0] * 6, [-6.0] + [1.0] * 6, dtype=torch.float32, device=dev)
+    p = VarCoefProblem(g, 200, 20)
+    g.set_field(v.u0)
+    g.set_coeff(v.kappa)
+    t_fwd = _time(lambda: abi.stencil_step(g.h, 200, s), 3, s)
+    tgt = g.new_field()
+    g.interior(tgt).copy_(torch.as_tensor(v.target, dtype=torch.float32))
+    del v
+
+    def fwd_ckpt():
+        abi.stencil_set_current(g.h, 0)
+        abi.stencil_step_ckpt(g.h, 200, 20, p.ws.data_ptr(), s)
+
+    def adj():
+        cur = g.bufs[g.current_slot()]
+        abi.stencil_residual(g.h, cur.data_ptr(), tgt.data_ptr(), p.lam.data_ptr(), p.loss.data_ptr(), s)
+        abi.stencil_adjoint(g.h, 200, 20, p.ws.data_ptr(), p.lam.data_ptr(), p.lam_tmp.data_ptr(),
+                            p.gk.data_ptr(), s)
+
+    fwd_ckpt()
+    t_adj = _time(adj, 2, s)
+    n4 = 256 ** 3
+    out["varcoef3d_f32"] = {"fwd_glups": n4 * 200 / t_fwd / 1e9, "fwd_us_per_step": t_fwd / 200 * 1e6,
+                            "fwd_hbm_frac": 12 * n4 / (t_fwd / 200) / 1e9 / hbm_peak,
+                            "adj_glups": n4 * 200 / t_adj / 1e9, "adj_us_per_step": t_adj / 200 * 1e6,
+                            "adj_over_fwd": t_adj / t_fwd, "kernel": g.kernel}
+    g.close()
+    del p
+    torch.cuda.empty_cache()
+    # batched 512 grids, FP32, 50 steps
+    b = inputs.batch2d()
+    bt = Batch(b.shapes, inputs.OFFSETS_BOX9, b.weights, periodic=True, dtype=torch.float32, device=dev)
+    bt.set_fields(b.fields)
+    npts = int((b.shapes[:, 0] * b.shapes[:, 1]).sum())
+    del b
+    cfg = bt.tune(50, s)
+    t = _time(lambda: bt.step(50, s), 3, s)
+    out["batch2d_f32"] = {"glups": npts * 50 / t / 1e9, "ms_per_run": t * 1e3,
+                          "nominal_hbm_frac": 8 * npts * 50 / t / 1e9 / hbm_peak, "config": list(cfg)}
+    bt.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(target_s: float = 15.0):
+    """The oracle on the host cores: 7-point periodic sweeps of a slab of the
+    512^3 workload (all 512x512 points of nz planes), double precision."""
+    import numpy as np
+
+    import oracle
+    from paper_2512_19851_gb300 import inputs
+
+    cores = oracle.default_threads()
+    probe = inputs.heat3d(shape=(8, N3, N3)).u0
+    w = [0.4] + [0.1] * 6
+    t = time.perf_counter()
+    oracle.sweep_const(probe, inputs.OFFSETS_7PT, w, True, 0.0, 1, threads=cores)
+    rate = probe.size / (time.perf_counter() - t)
+    nz = int(max(8, min(N3, target_s * rate / (N3 * N3) / 2)))
+    slab = inputs.heat3d(shape=(nz, N3, N3)).u0
+    t = time.perf_counter()
+    oracle.sweep_const(slab, inputs.OFFSETS_7PT, w, True, 0.0, 2, threads=cores)
+    dt = time.perf_counter() - t
+    del np
+    return {"value": slab.size * 2 / dt / 1e9, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
+            "sample": f"2 periodic 7-point sweeps of a {nz}x512x512 slab, FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm, on rank 0 only."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2512_19851_gb300 import inputs
+
+    cores = oracle.default_threads()
+    w = [0.4] + [0.1] * 6
+    probe = inputs.heat3d(shape=(8, N3, N3)).u0
+    t = time.perf_counter()
+    oracle.sweep_const(probe, inputs.OFFSETS_7PT, w, True, 0.0, 1, threads=cores)
+    rate = probe.size / (time.perf_counter() - t)
+    budget = 120.0 / max(1, args.steps + args.warmup)  # seconds per step
+    nz = int(max(1, min(N3, budget * rate / (N3 * N3))))
+    slab = inputs.heat3d(shape=(nz, N3, N3)).u0
+    for _ in range(args.warmup):
+        oracle.sweep_const(slab, inputs.OFFSETS_7PT, w, True, 0.0, 1, threads=cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sweep_const(slab, inputs.OFFSETS_7PT, w, True, 0.0, 1, threads=cores)
+    dt = time.perf_counter() - t
+    val = slab.size * args.steps / dt / 1e9
+    sample = f"per step: 1 periodic 7-point sweep of a {nz}x512x512 slab of the 512^3 workload, FP64"
+    line = {"impl": "reference", "metric": "grid-point updates/s (GLUP/s) and % of HBM roofline, forward and adjoint",
+            "value": val, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded heat3d)",
+            "config": {"workload": WORKLOAD, "grid": [N3, N3, N3]},
+            "cpu_baseline": {"value": val, "unit": "GLUP/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--headline-only", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,279 @@
+/*
+ * stencil.h -- C ABI of the GB300 stencil-sweep library (libstencil.so).
+ *
+ * The library computes repeated sweeps of a fixed-radius stencil over a
+ * structured 2D/3D grid with a ghost (halo) region, the operation that the
+ * CharmStencil abstraction ("An Adaptive Distributed Stencil Abstraction for
+ * GPUs") compiles every slice-assignment expression into (Sec. III-A,
+ * Example 1; Sec. III-C "Code generation"):
+ *
+ *     u_{t+1}[p] = sum_k w_k(p) * u_t[p + o_k]                      (1)
+ *
+ * with the per-point weights written in an affine form
+ *
+ *     w_k(p) = alpha_k + beta_k * kappa[p]                          (2)
+ *
+ * (beta = NULL: constant weights; otherwise one coefficient field kappa),
+ * optionally in a two-level leapfrog form
+ *
+ *     u_{t+1}[p] = sum_k w_k(p) u_t[p + o_k] - u_{t-1}[p] + s_t [p == src]   (3)
+ *
+ * The output of a step is never an input of the same step (the paper's
+ * dependency rule, Sec. III-A): two buffers are used and swap roles after
+ * every step, as `u1, u2 = u2, u1` does in Example 1.
+ *
+ * Ghost region (Sec. III-C "Data layout"): its width is the largest offset
+ * component over all points, as the paper's analysis pass derives it.  The
+ * domain lives on one GPU, so the paper's ghost exchange between tiles
+ * (Sec. III-C "DAG execution") becomes a device-local boundary rule folded
+ * into the sweep: Dirichlet ghosts hold a constant that the sweep never
+ * writes (Example 1's boundary ring); periodic neighbours wrap around.
+ *
+ * Conventions for every entry point
+ *   - Return value: ST_OK or a negative st_status.  Nothing aborts or throws
+ *     across the ABI; stencil_last_error() gives a thread-local message.
+ *   - Device buffers are BORROWED: the caller allocates and frees them and
+ *     keeps them alive while a handle uses them.  The library allocates only
+ *     its own scratch (status word, reduction partials, source table, batch
+ *     tables, tuning copies) in create/bind/set/tune calls, never in a step.
+ *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *     void*, NULL = legacy default stream) and is asynchronous, except
+ *     stencil_sync() and the *_tune() calls, which synchronise that stream.
+ *   - Errors detected on the device (a bounded wait that ran out) set a
+ *     per-handle status word that stencil_sync() reports.
+ *   - A handle is not thread safe; distinct handles are independent.
+ *
+ * Layout of a field buffer (one per time level, plus the coefficient field)
+ *   Padded C-order array  [nz + 2r][ny + 2r][pitch]  (3D)  or
+ *                         [ny + 2r][pitch]           (2D),
+ *   x fastest.  The interior point (z, y, x) sits at padded index
+ *   (z + r, y + r, x + xl) where xl >= r is chosen so the first interior
+ *   column is 16-byte aligned; pitch >= xl + nx + r is a multiple of 16 bytes.
+ *   stencil_layout() returns the padded shape and the interior origin.  The
+ *   buffer's base address must be 16-byte aligned.  Ghost cells belong to the
+ *   library: it (re)writes them before a step when the buffer was bound or
+ *   marked dirty.
+ */
+#ifndef STENCIL_H
+#define STENCIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct st_grid_s* st_grid_t;
+typedef struct st_batch_s* st_batch_t;
+
+typedef enum {
+    ST_OK = 0,
+    ST_ERR_ARG = -1,            /* invalid argument (shape, offset, pointer, slot, count) */
+    ST_ERR_ALIAS = -2,          /* two bound buffers overlap (output would be read in the same step) */
+    ST_ERR_UNSUPPORTED = -3,    /* valid request this build does not implement */
+    ST_ERR_CUDA = -4,           /* a CUDA runtime call failed (message has the CUDA error) */
+    ST_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait ran out (reported by stencil_sync) */
+    ST_ERR_BOUNDS = -6,         /* a device-side bounds check fired (reported by stencil_sync) */
+    ST_ERR_OOM = -7,            /* library scratch allocation failed */
+    ST_ERR_STATE = -8           /* call out of order (e.g. step before bind) */
+} st_status;
+
+typedef enum { ST_F32 = 0, ST_F64 = 1 } st_dtype;
+typedef enum { ST_DIRICHLET = 0, ST_PERIODIC = 1 } st_bc;
+
+/* stencil_create flags */
+#define ST_FLAG_GENERIC 1u   /* always use the one-thread-per-point kernel (the
+                                paper's generated-kernel shape, Sec. III-C) */
+
+#define ST_MAX_POINTS 64     /* most neighbour points per stencil */
+#define ST_MAX_RADIUS 8      /* widest ghost region */
+
+/* Slots of stencil_bind */
+#define ST_SLOT_A 0          /* time level buffer A */
+#define ST_SLOT_B 1          /* time level buffer B */
+#define ST_SLOT_COEFF 2      /* coefficient field kappa of (2) */
+
+/* Library version string. */
+const char* stencil_version(void);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* stencil_last_error(void);
+
+/*
+ * Create a grid handle for the update (1)-(3).
+ *   ndim        2 or 3.
+ *   dims        interior extents in C order: {ny, nx} or {nz, ny, nx}, each >= 1.
+ *   radius      ghost width; 0 derives it as max |offset component| (the
+ *               paper's analysis pass, Sec. III-C); a larger value is kept.
+ *   npts        number of neighbour points, 1..ST_MAX_POINTS.
+ *   offsets     npts*ndim int32, point k's offset in C order ({dy,dx} or
+ *               {dz,dy,dx}); |component| <= ST_MAX_RADIUS, and with a
+ *               periodic boundary |component| < the extent of its axis.
+ *   alpha       npts doubles (the constant part of each weight).
+ *   beta        npts doubles, or NULL for constant weights; non-NULL
+ *               requires a coefficient buffer bound at ST_SLOT_COEFF.
+ *   bc          ST_DIRICHLET (ghosts = bc_value) or ST_PERIODIC.
+ *   dtype       storage and arithmetic type of the fields.
+ *   time_levels 1: form (1); 2: leapfrog form (3).
+ *   flags       ST_FLAG_GENERIC or 0.
+ * Copies all arrays; allocates only library scratch.  *out is NULL on error.
+ */
+st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radius, int npts,
+                         const int32_t* offsets, const double* alpha, const double* beta,
+                         st_bc bc, double bc_value, st_dtype dtype, int time_levels,
+                         uint32_t flags);
+
+/* Release the handle and its scratch (not the borrowed buffers).  NULL is a no-op. */
+st_status stencil_destroy(st_grid_t g);
+
+/*
+ * Layout of every field-shaped buffer of this grid (see the header comment).
+ *   padded_dims  ndim int64: padded extents in C order (last one = pitch).
+ *   origin       ndim int64: padded index of interior point 0.
+ *   elems        total element count of one buffer.
+ * Any output pointer may be NULL.
+ */
+st_status stencil_layout(st_grid_t g, int64_t* padded_dims, int64_t* origin, int64_t* elems);
+
+/* Radius, point count and the kernel family the handle dispatches to
+ * (name is a static string, e.g. "star3d_r1_tma"). */
+st_status stencil_info(st_grid_t g, int* radius, int* npts, const char** kernel_name);
+
+/*
+ * Bind a device buffer (layout above, the grid's dtype) to a slot:
+ * ST_SLOT_A / ST_SLOT_B (time levels) or ST_SLOT_COEFF.  Overlap with another
+ * bound slot is ST_ERR_ALIAS.  Binding marks the buffer's ghosts stale.
+ * Binding slot A makes it the current level.
+ */
+st_status stencil_bind(st_grid_t g, int slot, void* dev_ptr);
+
+/* Tell the library the caller rewrote a bound buffer: its ghosts are
+ * refreshed before the next step (the paper's generation epochs, Sec. III-C). */
+st_status stencil_mark_dirty(st_grid_t g, int slot);
+
+/* Which time-level slot (ST_SLOT_A or ST_SLOT_B) holds the newest level u_t.
+ * With two time levels the other slot holds u_{t-1}. */
+st_status stencil_current(st_grid_t g, int* slot);
+st_status stencil_set_current(st_grid_t g, int slot);
+
+/*
+ * Point source of the leapfrog form (3): amplitudes[t] is added at interior
+ * point `index` (ndim int64, C order) by the step that computes level t+1,
+ * where t is the handle's step counter.  Steps past `count` add nothing.
+ * Copies the host amplitudes to library scratch.  count = 0 removes it.
+ */
+st_status stencil_set_source(st_grid_t g, const int64_t* index, const double* amplitudes,
+                             int64_t count);
+
+/* Set / read the step counter t used by the source (0 after create). */
+st_status stencil_set_step_index(st_grid_t g, int64_t t);
+st_status stencil_get_step_index(st_grid_t g, int64_t* t);
+
+/*
+ * Advance nsteps >= 0 steps on `stream`: refresh stale ghosts, then sweep,
+ * swapping the current slot after every step.  Enqueued as one CUDA graph
+ * per (handle, nsteps parity) after the first call with that nsteps; the
+ * launch sequence is the same either way.
+ */
+st_status stencil_step(st_grid_t g, int nsteps, void* stream);
+
+/*
+ * End-to-end form of stencil_step for callers whose data is on the host:
+ * copies host_u0 (dense interior, C order, the grid's dtype) into the current
+ * level, runs nsteps, copies the newest level's interior to host_uT.  Both
+ * copies are enqueued on `stream` (pinned host memory makes them
+ * asynchronous); the call returns after enqueueing.  One time level only.
+ */
+st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* host_uT,
+                           void* stream);
+
+/* Synchronise the last stream used by this handle and report device-side
+ * errors (ST_ERR_DEVICE_TIMEOUT, ST_ERR_BOUNDS); clears the status word. */
+st_status stencil_sync(st_grid_t g);
+
+/*
+ * Interior reductions in double precision over a (and b, if not NULL), two
+ * buffers in this grid's layout and dtype:
+ *   dev_out[0] = sum (a - b), dev_out[1] = sum (a - b)^2, dev_out[2] = max |a - b|.
+ * dev_out: 3 doubles in device memory.  Deterministic: fixed block partials
+ * summed in a fixed order by a second pass.
+ */
+st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_out,
+                         void* stream);
+
+/*
+ * Loss residual: lambda = u - target on the interior (lambda's ghosts set to
+ * 0) and dev_loss[0] = 0.5 * sum (u - target)^2 in double precision.
+ */
+st_status stencil_residual(st_grid_t g, const void* u, const void* target, void* lambda,
+                           double* dev_loss, void* stream);
+
+/*
+ * Adjoint with checkpoint-every-m recomputation (one time level only).
+ * Workspace bytes for a run of nsteps with checkpoints every ckpt_every steps
+ * (ceil(nsteps/ckpt_every) checkpoints + ckpt_every-1 recomputed levels).
+ */
+st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int ckpt_every, size_t* bytes);
+
+/* Forward nsteps from the current level, storing u at t = 0, m, 2m, ... in
+ * `workspace` (device, >= stencil_adjoint_workspace bytes, 16-byte aligned). */
+st_status stencil_step_ckpt(st_grid_t g, int nsteps, int ckpt_every, void* workspace,
+                            void* stream);
+
+/*
+ * Reverse pass of a run recorded by stencil_step_ckpt with the same nsteps
+ * and ckpt_every.  lambda (in: dL/du_T, out: dL/du_0) and lambda_tmp are
+ * field-layout buffers of the grid's dtype; grad_coeff (may be NULL) is a
+ * field-layout buffer of DOUBLES into which
+ *     sum_t lambda_{t+1}[p] * sum_k beta_k u_t[p + o_k]     (= dL/dkappa_p)
+ * is ACCUMULATED (+=).  The transpose step is
+ *     lambda_t[q] = sum_k w_k(q - o_k) lambda_{t+1}[q - o_k],
+ * over the points q - o_k that are interior (wrapped when periodic); ghost
+ * cells are boundary data, not variables.  The current level is unchanged.
+ */
+st_status stencil_adjoint(st_grid_t g, int nsteps, int ckpt_every, const void* workspace,
+                          void* lambda, void* lambda_tmp, double* grad_coeff, void* stream);
+
+/* ----------------------------------------------------------------------------
+ * Batched form: many independent 2D grids with the same neighbour offsets,
+ * their own sizes and weights, advanced by one persistent launch per call.
+ * --------------------------------------------------------------------------*/
+
+/*
+ * ngrids >= 1; dims: ngrids*2 int64 {ny, nx}; offsets: npts*2 int32 {dy, dx}
+ * shared by all grids; weights: ngrids*npts doubles (constant per grid).
+ */
+st_status stencil_batch_create(st_batch_t* out, int ngrids, const int64_t* dims, int npts,
+                               const int32_t* offsets, const double* weights, st_bc bc,
+                               double bc_value, st_dtype dtype, uint32_t flags);
+st_status stencil_batch_destroy(st_batch_t b);
+
+/* Layout of grid g (same rules as stencil_layout, 2D). */
+st_status stencil_batch_layout(st_batch_t b, int g, int64_t* padded_dims, int64_t* origin,
+                               int64_t* elems);
+
+/* Bind both time levels of every grid: host arrays of ngrids device pointers. */
+st_status stencil_batch_bind(st_batch_t b, void* const* dev_ptrs_a, void* const* dev_ptrs_b);
+
+/*
+ * Autotune the launch configuration for nsteps-step calls: times each
+ * candidate (tile shape, threads per block, steps per pass) on the bound data
+ * and keeps the fastest; the bound buffers are restored afterwards.
+ * Synchronises `stream`.  Without a call a default configuration is used.
+ */
+st_status stencil_batch_tune(st_batch_t b, int nsteps, void* stream);
+
+/* The configuration in use: cfg[0] tile x, cfg[1] tile y, cfg[2] threads,
+ * cfg[3] steps per pass. */
+st_status stencil_batch_config(st_batch_t b, int* cfg);
+
+/* Advance every grid nsteps steps. */
+st_status stencil_batch_step(st_batch_t b, int nsteps, void* stream);
+st_status stencil_batch_current(st_batch_t b, int* slot);
+st_status stencil_batch_sync(st_batch_t b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STENCIL_H */

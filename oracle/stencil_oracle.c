@@ -42,8 +42,9 @@
 
 static int64_t orc_wrap(int64_t i, int64_t n)
 {
-    int64_t r = i % n;
-    return r < 0 ? r + n : r;
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
 }
 
 /* Value of field f at (z, y, x), which may lie outside the interior. */

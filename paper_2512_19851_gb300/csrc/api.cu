@@ -1,0 +1,834 @@
+// Host side of the C ABI declared in include/stencil.h: handle life cycle,
+// argument validation, the padded layout, ghost refresh, the step driver
+// (CUDA graphs of the sweep launches), checkpointed adjoint, reductions and
+// the batched form.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "families.cuh"
+
+namespace st {
+
+static thread_local std::string t_err;
+
+void set_error(const std::string& msg) { t_err = msg; }
+
+st_status fail(st_status code, const std::string& msg)
+{
+    t_err = msg;
+    return code;
+}
+
+st_status cuda_fail(cudaError_t e, const char* what)
+{
+    t_err = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();  // clear a sticky launch error of this thread
+    return ST_ERR_CUDA;
+}
+
+static int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+Geom make_geom(int ndim, const int64_t* dims, int r, int esize)
+{
+    Geom g{};
+    g.ndim = ndim;
+    g.r = r;
+    g.rz = (ndim == 3) ? r : 0;
+    g.esize = esize;
+    g.nz = (ndim == 3) ? dims[0] : 1;
+    g.ny = dims[ndim - 2];
+    g.nx = dims[ndim - 1];
+    const int64_t a = 16 / esize;  // elements per 16 bytes
+    g.xl = round_up(r, a);
+    g.pitch = round_up(g.xl + g.nx + r, a);
+    g.pny = g.ny + 2 * r;
+    g.pnz = g.nz + 2 * g.rz;
+    g.plane = g.pny * g.pitch;
+    g.elems = g.pnz * g.plane;
+    g.origin = g.rz * g.plane + (int64_t)r * g.pitch + g.xl;
+    g.npoints = g.nz * g.ny * g.nx;
+    return g;
+}
+
+}  // namespace st
+
+using namespace st;
+
+// ---------------------------------------------------------------------------
+// Grid handle
+// ---------------------------------------------------------------------------
+struct st_grid_s {
+    Geom g{};
+    int npts = 0;
+    int radius = 0;
+    std::vector<int32_t> off;  // npts * 3: dz, dy, dx (dz = 0 in 2D)
+    std::vector<double> alpha, beta;
+    bool has_beta = false;
+    st_bc bc = ST_DIRICHLET;
+    double bc_value = 0.0;
+    st_dtype dtype = ST_F64;
+    int levels = 1;
+    uint32_t flags = 0;
+    Family fam{};
+
+    void* buf[3] = {nullptr, nullptr, nullptr};
+    bool stale[3] = {false, false, false};
+    int cur = ST_SLOT_A;
+    int64_t step = 0;
+
+    int64_t src = -1;
+    double* d_src = nullptr;
+    int64_t src_count = 0;
+
+    bool scratch = false;
+    int device = -1;
+    int* d_status = nullptr;
+    double* d_partials = nullptr;
+    int red_blocks = 0;
+    cudaStream_t cap = nullptr;
+    cudaStream_t last = nullptr;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+};
+
+static void drop_graphs(st_grid_t g)
+{
+    for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
+    g->graphs.clear();
+}
+
+static st_status ensure_scratch(st_grid_t g)
+{
+    if (g->scratch) return ST_OK;
+    ST_CUDA_TRY(cudaGetDevice(&g->device));
+    const int64_t rows = g->g.nz * g->g.ny;
+    g->red_blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, rows));
+    if (cudaMalloc(&g->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&g->d_partials, sizeof(double) * 3 * g->red_blocks) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ST_ERR_OOM, "stencil_bind: scratch allocation failed");
+    }
+    ST_CUDA_TRY(cudaMemset(g->d_status, 0, sizeof(int)));
+    ST_CUDA_TRY(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
+    g->scratch = true;
+    return ST_OK;
+}
+
+static bool is_star(const std::vector<int32_t>& off, int npts, int ndim)
+{
+    for (int k = 0; k < npts; ++k) {
+        int nz = (off[3 * k] != 0) + (off[3 * k + 1] != 0) + (off[3 * k + 2] != 0);
+        if (nz > 1) return false;
+        if (ndim == 2 && off[3 * k] != 0) return false;
+    }
+    return true;
+}
+
+extern "C" {
+
+const char* stencil_version(void) { return "gb300-stencil 0.1 (sm_103a)"; }
+
+const char* stencil_last_error(void) { return t_err.c_str(); }
+
+st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radius, int npts,
+                         const int32_t* offsets, const double* alpha, const double* beta,
+                         st_bc bc, double bc_value, st_dtype dtype, int time_levels,
+                         uint32_t flags)
+{
+    if (!out) return fail(ST_ERR_ARG, "stencil_create: out is NULL");
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return fail(ST_ERR_ARG, "stencil_create: ndim must be 2 or 3");
+    if (!dims || !offsets || !alpha) return fail(ST_ERR_ARG, "stencil_create: NULL dims/offsets/alpha");
+    if (npts < 1 || npts > ST_MAX_POINTS) return fail(ST_ERR_ARG, "stencil_create: npts out of range");
+    if (bc != ST_DIRICHLET && bc != ST_PERIODIC) return fail(ST_ERR_ARG, "stencil_create: bad bc");
+    if (dtype != ST_F32 && dtype != ST_F64) return fail(ST_ERR_ARG, "stencil_create: bad dtype");
+    if (time_levels != 1 && time_levels != 2) return fail(ST_ERR_ARG, "stencil_create: time_levels must be 1 or 2");
+    if (flags & ~ST_FLAG_GENERIC) return fail(ST_ERR_ARG, "stencil_create: unknown flags");
+    if (radius < 0 || radius > ST_MAX_RADIUS) return fail(ST_ERR_ARG, "stencil_create: radius out of range");
+    int64_t d3[3] = {1, 1, 1};
+    for (int i = 0; i < ndim; ++i) {
+        if (dims[i] < 1 || dims[i] > (int64_t)1 << 24)
+            return fail(ST_ERR_ARG, "stencil_create: extent out of range [1, 2^24]");
+        d3[3 - ndim + i] = dims[i];
+    }
+    if (d3[0] > 65535) return fail(ST_ERR_ARG, "stencil_create: nz > 65535");
+    std::vector<int32_t> off(3 * npts, 0);
+    int derived = 0;
+    for (int k = 0; k < npts; ++k) {
+        for (int i = 0; i < ndim; ++i) {
+            const int32_t o = offsets[k * ndim + i];
+            if (o < -ST_MAX_RADIUS || o > ST_MAX_RADIUS)
+                return fail(ST_ERR_ARG, "stencil_create: offset component beyond ST_MAX_RADIUS");
+            if (bc == ST_PERIODIC && (int64_t)(o < 0 ? -o : o) >= d3[3 - ndim + i])
+                return fail(ST_ERR_ARG, "stencil_create: periodic offset not smaller than the extent");
+            off[3 * k + 3 - ndim + i] = o;
+            derived = std::max(derived, o < 0 ? -o : o);
+        }
+    }
+    if (radius == 0) radius = derived;
+    if (radius < derived) return fail(ST_ERR_ARG, "stencil_create: radius smaller than the largest offset");
+    if (bc == ST_DIRICHLET) {
+        // the paper's limitation (Sec. III-D): dependence distance within the domain
+        for (int i = 0; i < ndim; ++i)
+            if (dims[i] < 1) return fail(ST_ERR_ARG, "stencil_create: empty extent");
+    }
+    for (int k = 0; k < npts; ++k)
+        if (!(alpha[k] == alpha[k]) || (beta && !(beta[k] == beta[k])))
+            return fail(ST_ERR_ARG, "stencil_create: NaN weight");
+
+    st_grid_t g = new (std::nothrow) st_grid_s();
+    if (!g) return fail(ST_ERR_OOM, "stencil_create: out of host memory");
+    g->g = make_geom(ndim, dims, radius, dtype == ST_F64 ? 8 : 4);
+    g->npts = npts;
+    g->radius = radius;
+    g->off = off;
+    g->alpha.assign(alpha, alpha + npts);
+    g->has_beta = beta != nullptr;
+    g->beta.assign(npts, 0.0);
+    if (beta) g->beta.assign(beta, beta + npts);
+    g->bc = bc;
+    g->bc_value = bc_value;
+    g->dtype = dtype;
+    g->levels = time_levels;
+    g->flags = flags;
+    FamilyDesc d{};
+    d.g = g->g;
+    d.npts = npts;
+    d.off = g->off.data();
+    d.alpha = g->alpha.data();
+    d.beta = g->beta.data();
+    d.has_beta = g->has_beta;
+    d.periodic = bc == ST_PERIODIC;
+    d.levels = time_levels;
+    d.star = is_star(g->off, npts, ndim);
+    d.force_generic = (flags & ST_FLAG_GENERIC) != 0;
+    g->fam = select_family(d);
+    *out = g;
+    return ST_OK;
+}
+
+st_status stencil_destroy(st_grid_t g)
+{
+    if (!g) return ST_OK;
+    drop_graphs(g);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    if (g->d_status) cudaFree(g->d_status);
+    if (g->d_partials) cudaFree(g->d_partials);
+    if (g->d_src) cudaFree(g->d_src);
+    delete g;
+    return ST_OK;
+}
+
+st_status stencil_layout(st_grid_t g, int64_t* padded_dims, int64_t* origin, int64_t* elems)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_layout: NULL handle");
+    const Geom& G = g->g;
+    if (padded_dims) {
+        if (G.ndim == 3) {
+            padded_dims[0] = G.pnz;
+            padded_dims[1] = G.pny;
+            padded_dims[2] = G.pitch;
+        } else {
+            padded_dims[0] = G.pny;
+            padded_dims[1] = G.pitch;
+        }
+    }
+    if (origin) {
+        if (G.ndim == 3) {
+            origin[0] = G.rz;
+            origin[1] = G.r;
+            origin[2] = G.xl;
+        } else {
+            origin[0] = G.r;
+            origin[1] = G.xl;
+        }
+    }
+    if (elems) *elems = G.elems;
+    return ST_OK;
+}
+
+st_status stencil_info(st_grid_t g, int* radius, int* npts, const char** kernel_name)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_info: NULL handle");
+    if (radius) *radius = g->radius;
+    if (npts) *npts = g->npts;
+    if (kernel_name) *kernel_name = g->fam.name;
+    return ST_OK;
+}
+
+st_status stencil_bind(st_grid_t g, int slot, void* ptr)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_bind: NULL handle");
+    if (slot < 0 || slot > 2) return fail(ST_ERR_ARG, "stencil_bind: slot must be 0, 1 or 2");
+    if (!ptr) return fail(ST_ERR_ARG, "stencil_bind: NULL pointer");
+    if (((uintptr_t)ptr & 15u) != 0) return fail(ST_ERR_ARG, "stencil_bind: pointer not 16-byte aligned");
+    const size_t bytes = (size_t)g->g.elems * g->g.esize;
+    const uintptr_t lo = (uintptr_t)ptr, hi = lo + bytes;
+    for (int s = 0; s < 3; ++s) {
+        if (s == slot || !g->buf[s]) continue;
+        const uintptr_t l2 = (uintptr_t)g->buf[s], h2 = l2 + bytes;
+        if (lo < h2 && l2 < hi) return fail(ST_ERR_ALIAS, "stencil_bind: buffer overlaps another bound slot");
+    }
+    st_status rc = ensure_scratch(g);
+    if (rc != ST_OK) return rc;
+    cudaPointerAttributes at{};
+    ST_CUDA_TRY(cudaPointerGetAttributes(&at, ptr));
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(ST_ERR_ARG, "stencil_bind: not a device pointer");
+    g->buf[slot] = ptr;
+    g->stale[slot] = true;
+    if (slot == ST_SLOT_A) g->cur = ST_SLOT_A;
+    drop_graphs(g);
+    return ST_OK;
+}
+
+st_status stencil_mark_dirty(st_grid_t g, int slot)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_mark_dirty: NULL handle");
+    if (slot < 0 || slot > 2) return fail(ST_ERR_ARG, "stencil_mark_dirty: bad slot");
+    g->stale[slot] = true;
+    return ST_OK;
+}
+
+st_status stencil_current(st_grid_t g, int* slot)
+{
+    if (!g || !slot) return fail(ST_ERR_ARG, "stencil_current: NULL argument");
+    *slot = g->cur;
+    return ST_OK;
+}
+
+st_status stencil_set_current(st_grid_t g, int slot)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_set_current: NULL handle");
+    if (slot != ST_SLOT_A && slot != ST_SLOT_B) return fail(ST_ERR_ARG, "stencil_set_current: slot must be 0 or 1");
+    g->cur = slot;
+    return ST_OK;
+}
+
+st_status stencil_set_source(st_grid_t g, const int64_t* index, const double* amplitudes, int64_t count)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_set_source: NULL handle");
+    if (count < 0) return fail(ST_ERR_ARG, "stencil_set_source: negative count");
+    if (g->d_src) {
+        cudaFree(g->d_src);
+        g->d_src = nullptr;
+    }
+    g->src = -1;
+    g->src_count = 0;
+    drop_graphs(g);
+    if (count == 0) return ST_OK;
+    if (!index || !amplitudes) return fail(ST_ERR_ARG, "stencil_set_source: NULL index/amplitudes");
+    if (g->levels != 2) return fail(ST_ERR_UNSUPPORTED, "stencil_set_source: source needs the leapfrog form");
+    const Geom& G = g->g;
+    int64_t c[3] = {0, 0, 0};
+    for (int i = 0; i < G.ndim; ++i) c[3 - G.ndim + i] = index[i];
+    if (c[0] < 0 || c[0] >= G.nz || c[1] < 0 || c[1] >= G.ny || c[2] < 0 || c[2] >= G.nx)
+        return fail(ST_ERR_ARG, "stencil_set_source: index outside the interior");
+    if (cudaMalloc(&g->d_src, sizeof(double) * count) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ST_ERR_OOM, "stencil_set_source: allocation failed");
+    }
+    ST_CUDA_TRY(cudaMemcpy(g->d_src, amplitudes, sizeof(double) * count, cudaMemcpyHostToDevice));
+    g->src = G.origin + c[0] * G.plane + c[1] * G.pitch + c[2];
+    g->src_count = count;
+    return ST_OK;
+}
+
+st_status stencil_set_step_index(st_grid_t g, int64_t t)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_set_step_index: NULL handle");
+    if (t < 0) return fail(ST_ERR_ARG, "stencil_set_step_index: negative");
+    g->step = t;
+    return ST_OK;
+}
+
+st_status stencil_get_step_index(st_grid_t g, int64_t* t)
+{
+    if (!g || !t) return fail(ST_ERR_ARG, "stencil_get_step_index: NULL argument");
+    *t = g->step;
+    return ST_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Step machinery
+// ---------------------------------------------------------------------------
+static SweepArgs sweep_args(st_grid_t g, const void* in, void* out, int64_t step)
+{
+    SweepArgs a{};
+    a.in = in;
+    a.out = out;
+    a.prev = (g->levels == 2) ? out : nullptr;
+    a.kappa = g->has_beta ? g->buf[ST_SLOT_COEFF] : nullptr;
+    a.step = step;
+    a.src = g->src;
+    a.src_amp = g->d_src;
+    a.src_count = g->src_count;
+    a.status = g->d_status;
+    return a;
+}
+
+static st_status refresh_ghosts(st_grid_t g, cudaStream_t s)
+{
+    for (int slot = 0; slot < 3; ++slot) {
+        if (!g->stale[slot] || !g->buf[slot]) continue;
+        if (g->bc == ST_DIRICHLET || slot == ST_SLOT_COEFF) {
+            const double v = (slot == ST_SLOT_COEFF) ? 0.0 : g->bc_value;
+            ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, g->buf[slot], g->g, v, s));
+        }
+        g->stale[slot] = false;
+    }
+    return ST_OK;
+}
+
+static st_status check_ready(st_grid_t g, const char* who)
+{
+    if (!g->buf[ST_SLOT_A] || !g->buf[ST_SLOT_B])
+        return fail(ST_ERR_STATE, std::string(who) + ": both time-level slots must be bound");
+    if (g->has_beta && !g->buf[ST_SLOT_COEFF])
+        return fail(ST_ERR_STATE, std::string(who) + ": per-cell weights need ST_SLOT_COEFF bound");
+    return ST_OK;
+}
+
+static st_status enqueue_steps(st_grid_t g, int cur, int64_t step0, int n, cudaStream_t s)
+{
+    for (int i = 0; i < n; ++i) {
+        const int nxt = 1 - cur;
+        SweepArgs a = sweep_args(g, g->buf[cur], g->buf[nxt], step0 + i);
+        ST_CUDA_TRY(launch_family(g->fam, a, s));
+        cur = nxt;
+    }
+    return ST_OK;
+}
+
+extern "C" {
+
+st_status stencil_step(st_grid_t g, int nsteps, void* stream)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_step: NULL handle");
+    if (nsteps < 0) return fail(ST_ERR_ARG, "stencil_step: negative step count");
+    st_status rc = check_ready(g, "stencil_step");
+    if (rc != ST_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last = s;
+    rc = refresh_ghosts(g, s);
+    if (rc != ST_OK) return rc;
+    if (nsteps == 0 || g->g.npoints == 0) return ST_OK;
+    // Sources change per step (step index is a launch parameter): launch directly.
+    const bool use_graph = (g->src < 0) && nsteps >= 2;
+    if (!use_graph) {
+        rc = enqueue_steps(g, g->cur, g->step, nsteps, s);
+        if (rc != ST_OK) return rc;
+    } else {
+        auto key = std::make_pair(nsteps, g->cur);
+        auto it = g->graphs.find(key);
+        if (it == g->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            ST_CUDA_TRY(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+            st_status erc = enqueue_steps(g, g->cur, g->step, nsteps, g->cap);
+            cudaError_t ce = cudaStreamEndCapture(g->cap, &graph);
+            if (erc != ST_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return erc;
+            }
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+            it = g->graphs.emplace(key, exec).first;
+        }
+        ST_CUDA_TRY(cudaGraphLaunch(it->second, s));
+    }
+    if (nsteps & 1) g->cur = 1 - g->cur;
+    g->step += nsteps;
+    return ST_OK;
+}
+
+st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* host_uT, void* stream)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_run_host: NULL handle");
+    if (!host_u0 || !host_uT) return fail(ST_ERR_ARG, "stencil_run_host: NULL host buffer");
+    if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_run_host: one time level only");
+    st_status rc = check_ready(g, "stencil_run_host");
+    if (rc != ST_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geom& G = g->g;
+    const size_t es = G.esize;
+    cudaMemcpy3DParms in{};
+    in.srcPtr = make_cudaPitchedPtr(const_cast<void*>(host_u0), G.nx * es, G.nx, G.ny);
+    in.dstPtr = make_cudaPitchedPtr(g->buf[g->cur], G.pitch * es, G.pitch, G.pny);
+    in.dstPos = make_cudaPos(G.xl * es, G.r, G.rz);
+    in.extent = make_cudaExtent(G.nx * es, G.ny, G.nz);
+    in.kind = cudaMemcpyHostToDevice;
+    ST_CUDA_TRY(cudaMemcpy3DAsync(&in, s));
+    rc = stencil_step(g, nsteps, stream);
+    if (rc != ST_OK) return rc;
+    cudaMemcpy3DParms o{};
+    o.srcPtr = make_cudaPitchedPtr(g->buf[g->cur], G.pitch * es, G.pitch, G.pny);
+    o.srcPos = make_cudaPos(G.xl * es, G.r, G.rz);
+    o.dstPtr = make_cudaPitchedPtr(host_uT, G.nx * es, G.nx, G.ny);
+    o.extent = make_cudaExtent(G.nx * es, G.ny, G.nz);
+    o.kind = cudaMemcpyDeviceToHost;
+    ST_CUDA_TRY(cudaMemcpy3DAsync(&o, s));
+    return ST_OK;
+}
+
+st_status stencil_sync(st_grid_t g)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_sync: NULL handle");
+    ST_CUDA_TRY(cudaStreamSynchronize(g->last));
+    if (!g->scratch) return ST_OK;
+    int code = 0;
+    ST_CUDA_TRY(cudaMemcpy(&code, g->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code != 0) {
+        ST_CUDA_TRY(cudaMemset(g->d_status, 0, sizeof(int)));
+        if (code == ST_ERR_DEVICE_TIMEOUT) return fail(ST_ERR_DEVICE_TIMEOUT, "device: bounded wait ran out");
+        return fail(ST_ERR_BOUNDS, "device: bounds check fired");
+    }
+    return ST_OK;
+}
+
+st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_out, void* stream)
+{
+    if (!g || !a || !dev_out) return fail(ST_ERR_ARG, "stencil_reduce: NULL argument");
+    st_status rc = ensure_scratch(g);
+    if (rc != ST_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last = s;
+    ST_CUDA_TRY(launch_reduce(g->g.esize, a, b, g->g, g->d_partials, g->red_blocks, dev_out, 0, nullptr, s));
+    return ST_OK;
+}
+
+st_status stencil_residual(st_grid_t g, const void* u, const void* target, void* lambda, double* dev_loss,
+                           void* stream)
+{
+    if (!g || !u || !target || !lambda || !dev_loss) return fail(ST_ERR_ARG, "stencil_residual: NULL argument");
+    if (lambda == u || lambda == target) return fail(ST_ERR_ALIAS, "stencil_residual: lambda aliases an input");
+    st_status rc = ensure_scratch(g);
+    if (rc != ST_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last = s;
+    ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, lambda, g->g, 0.0, s));
+    ST_CUDA_TRY(launch_reduce(g->g.esize, u, target, g->g, g->d_partials, g->red_blocks, dev_loss, 1, lambda, s));
+    return ST_OK;
+}
+
+static size_t state_bytes(st_grid_t g) { return (size_t)((g->g.elems * g->g.esize + 255) / 256 * 256); }
+
+st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* bytes)
+{
+    if (!g || !bytes) return fail(ST_ERR_ARG, "stencil_adjoint_workspace: NULL argument");
+    if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_adjoint_workspace: nsteps >= 0, ckpt_every >= 1");
+    const int64_t nck = (nsteps + m - 1) / m;
+    *bytes = state_bytes(g) * (size_t)(nck + (m - 1));
+    return ST_OK;
+}
+
+st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stream)
+{
+    if (!g || !ws) return fail(ST_ERR_ARG, "stencil_step_ckpt: NULL argument");
+    if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_step_ckpt: nsteps >= 0, ckpt_every >= 1");
+    if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_step_ckpt: one time level only");
+    if (((uintptr_t)ws & 15u) != 0) return fail(ST_ERR_ARG, "stencil_step_ckpt: workspace not 16-byte aligned");
+    st_status rc = check_ready(g, "stencil_step_ckpt");
+    if (rc != ST_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last = s;
+    rc = refresh_ghosts(g, s);
+    if (rc != ST_OK) return rc;
+    const size_t sb = state_bytes(g);
+    const size_t bytes = (size_t)g->g.elems * g->g.esize;
+    for (int t = 0; t < nsteps; t += m) {
+        ST_CUDA_TRY(cudaMemcpyAsync((char*)ws + (size_t)(t / m) * sb, g->buf[g->cur], bytes,
+                                    cudaMemcpyDeviceToDevice, s));
+        const int seg = std::min(m, nsteps - t);
+        rc = enqueue_steps(g, g->cur, g->step, seg, s);
+        if (rc != ST_OK) return rc;
+        if (seg & 1) g->cur = 1 - g->cur;
+        g->step += seg;
+    }
+    return ST_OK;
+}
+
+st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* lambda, void* lambda_tmp,
+                          double* grad, void* stream)
+{
+    if (!g || !ws || !lambda || !lambda_tmp) return fail(ST_ERR_ARG, "stencil_adjoint: NULL argument");
+    if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_adjoint: nsteps >= 0, ckpt_every >= 1");
+    if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: one time level only");
+    if (lambda == lambda_tmp) return fail(ST_ERR_ALIAS, "stencil_adjoint: lambda and lambda_tmp alias");
+    if (grad && !g->has_beta) return fail(ST_ERR_ARG, "stencil_adjoint: grad_coeff needs per-cell weights");
+    if (g->has_beta && !g->buf[ST_SLOT_COEFF]) return fail(ST_ERR_STATE, "stencil_adjoint: ST_SLOT_COEFF not bound");
+    st_status rc = ensure_scratch(g);
+    if (rc != ST_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last = s;
+    if (g->stale[ST_SLOT_COEFF] && g->buf[ST_SLOT_COEFF]) {
+        ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, g->buf[ST_SLOT_COEFF], g->g, 0.0, s));
+        g->stale[ST_SLOT_COEFF] = false;
+    }
+    ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, lambda, g->g, 0.0, s));
+    ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, lambda_tmp, g->g, 0.0, s));
+    if (nsteps == 0) return ST_OK;
+    const size_t sb = state_bytes(g);
+    const int64_t nck = (nsteps + m - 1) / m;
+    char* base = (char*)const_cast<void*>(ws);
+    char* seg = base + (size_t)nck * sb;
+    auto state = [&](int64_t c, int j) -> void* {
+        return j == 0 ? (void*)(base + (size_t)c * sb) : (void*)(seg + (size_t)(j - 1) * sb);
+    };
+    if (g->bc == ST_DIRICHLET)
+        for (int j = 1; j < m; ++j) ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, state(0, j), g->g, g->bc_value, s));
+    void* lin = lambda;
+    void* lout = lambda_tmp;
+    for (int64_t c = nck - 1; c >= 0; --c) {
+        const int64_t t0 = c * m;
+        const int L = (int)std::min<int64_t>(m, nsteps - t0);
+        for (int j = 1; j < L; ++j) {
+            SweepArgs a = sweep_args(g, state(c, j - 1), state(c, j), t0 + j - 1);
+            ST_CUDA_TRY(launch_family(g->fam, a, s));
+        }
+        for (int j = L - 1; j >= 0; --j) {
+            AdjointArgs a{};
+            a.u = state(c, j);
+            a.lam_in = lin;
+            a.lam_out = lout;
+            a.kappa = g->has_beta ? g->buf[ST_SLOT_COEFF] : nullptr;
+            a.gk = grad;
+            ST_CUDA_TRY(launch_family_adjoint(g->fam, a, s));
+            std::swap(lin, lout);
+        }
+    }
+    if (lin != lambda)
+        ST_CUDA_TRY(cudaMemcpyAsync(lambda, lin, (size_t)g->g.elems * g->g.esize, cudaMemcpyDeviceToDevice, s));
+    return ST_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched form
+// ---------------------------------------------------------------------------
+struct st_batch_s {
+    int ngrids = 0;
+    int npts = 0;
+    st_bc bc = ST_PERIODIC;
+    double bc_value = 0.0;
+    st_dtype dtype = ST_F32;
+    uint32_t flags = 0;
+    std::vector<int32_t> off;      // npts * 2
+    std::vector<double> weights;   // ngrids * npts
+    std::vector<Geom> geoms;
+    std::vector<void*> a, b;
+    bool bound = false;
+    int cur = 0;
+    BatchPlan plan;
+    cudaStream_t last = nullptr;
+    cudaStream_t cap = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;  // keyed by nsteps * 2 + cur
+    int* d_status = nullptr;
+};
+
+static void drop_batch_graphs(st_batch_t b)
+{
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+extern "C" {
+
+st_status stencil_batch_create(st_batch_t* out, int ngrids, const int64_t* dims, int npts, const int32_t* offsets,
+                               const double* weights, st_bc bc, double bc_value, st_dtype dtype, uint32_t flags)
+{
+    if (!out) return fail(ST_ERR_ARG, "stencil_batch_create: out is NULL");
+    *out = nullptr;
+    if (ngrids < 1 || !dims || !offsets || !weights) return fail(ST_ERR_ARG, "stencil_batch_create: bad arguments");
+    if (npts < 1 || npts > ST_MAX_POINTS) return fail(ST_ERR_ARG, "stencil_batch_create: npts out of range");
+    if (bc != ST_DIRICHLET && bc != ST_PERIODIC) return fail(ST_ERR_ARG, "stencil_batch_create: bad bc");
+    if (dtype != ST_F32 && dtype != ST_F64) return fail(ST_ERR_ARG, "stencil_batch_create: bad dtype");
+    if (flags & ~ST_FLAG_GENERIC) return fail(ST_ERR_ARG, "stencil_batch_create: unknown flags");
+    int r = 0;
+    for (int k = 0; k < 2 * npts; ++k) {
+        const int32_t o = offsets[k];
+        if (o < -ST_MAX_RADIUS || o > ST_MAX_RADIUS) return fail(ST_ERR_ARG, "stencil_batch_create: offset too large");
+        r = std::max(r, o < 0 ? -o : o);
+    }
+    st_batch_t b = new (std::nothrow) st_batch_s();
+    if (!b) return fail(ST_ERR_OOM, "stencil_batch_create: out of host memory");
+    b->ngrids = ngrids;
+    b->npts = npts;
+    b->bc = bc;
+    b->bc_value = bc_value;
+    b->dtype = dtype;
+    b->flags = flags;
+    b->off.assign(offsets, offsets + 2 * npts);
+    b->weights.assign(weights, weights + (size_t)ngrids * npts);
+    for (int i = 0; i < ngrids; ++i) {
+        const int64_t d[2] = {dims[2 * i], dims[2 * i + 1]};
+        if (d[0] < 1 || d[1] < 1 || d[0] > (1 << 24) || d[1] > (1 << 24)) {
+            delete b;
+            return fail(ST_ERR_ARG, "stencil_batch_create: grid extent out of range");
+        }
+        if (bc == ST_PERIODIC && (r >= d[0] || r >= d[1])) {
+            delete b;
+            return fail(ST_ERR_ARG, "stencil_batch_create: periodic offset not smaller than a grid extent");
+        }
+        b->geoms.push_back(make_geom(2, d, r, dtype == ST_F64 ? 8 : 4));
+    }
+    b->a.assign(ngrids, nullptr);
+    b->b.assign(ngrids, nullptr);
+    b->plan = make_batch_plan(b->geoms, b->npts, b->off.data(), b->weights.data(), bc == ST_PERIODIC, dtype,
+                              (flags & ST_FLAG_GENERIC) != 0);
+    *out = b;
+    return ST_OK;
+}
+
+st_status stencil_batch_destroy(st_batch_t b)
+{
+    if (!b) return ST_OK;
+    drop_batch_graphs(b);
+    free_batch_plan(b->plan);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->d_status) cudaFree(b->d_status);
+    delete b;
+    return ST_OK;
+}
+
+st_status stencil_batch_layout(st_batch_t b, int i, int64_t* padded_dims, int64_t* origin, int64_t* elems)
+{
+    if (!b) return fail(ST_ERR_ARG, "stencil_batch_layout: NULL handle");
+    if (i < 0 || i >= b->ngrids) return fail(ST_ERR_ARG, "stencil_batch_layout: grid index out of range");
+    const Geom& G = b->geoms[i];
+    if (padded_dims) {
+        padded_dims[0] = G.pny;
+        padded_dims[1] = G.pitch;
+    }
+    if (origin) {
+        origin[0] = G.r;
+        origin[1] = G.xl;
+    }
+    if (elems) *elems = G.elems;
+    return ST_OK;
+}
+
+st_status stencil_batch_bind(st_batch_t b, void* const* pa, void* const* pb)
+{
+    if (!b || !pa || !pb) return fail(ST_ERR_ARG, "stencil_batch_bind: NULL argument");
+    for (int i = 0; i < b->ngrids; ++i) {
+        if (!pa[i] || !pb[i]) return fail(ST_ERR_ARG, "stencil_batch_bind: NULL grid pointer");
+        if ((((uintptr_t)pa[i]) | ((uintptr_t)pb[i])) & 15u)
+            return fail(ST_ERR_ARG, "stencil_batch_bind: pointer not 16-byte aligned");
+        const size_t bytes = (size_t)b->geoms[i].elems * b->geoms[i].esize;
+        const uintptr_t l1 = (uintptr_t)pa[i], l2 = (uintptr_t)pb[i];
+        if (l1 < l2 + bytes && l2 < l1 + bytes) return fail(ST_ERR_ALIAS, "stencil_batch_bind: A and B overlap");
+    }
+    if (!b->cap) ST_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    if (!b->d_status) {
+        if (cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(ST_ERR_OOM, "stencil_batch_bind: scratch allocation failed");
+        }
+        ST_CUDA_TRY(cudaMemset(b->d_status, 0, sizeof(int)));
+    }
+    b->a.assign(pa, pa + b->ngrids);
+    b->b.assign(pb, pb + b->ngrids);
+    drop_batch_graphs(b);
+    st_status rc = bind_batch_plan(b->plan, b->geoms, b->a.data(), b->b.data(), b->d_status);
+    if (rc != ST_OK) return rc;
+    // Dirichlet ghosts of every grid
+    if (b->bc == ST_DIRICHLET)
+        for (int i = 0; i < b->ngrids; ++i) {
+            ST_CUDA_TRY(launch_fill_ghosts(b->geoms[i].esize, b->a[i], b->geoms[i], b->bc_value, nullptr));
+            ST_CUDA_TRY(launch_fill_ghosts(b->geoms[i].esize, b->b[i], b->geoms[i], b->bc_value, nullptr));
+        }
+    ST_CUDA_TRY(cudaStreamSynchronize(nullptr));
+    b->bound = true;
+    b->cur = 0;
+    return ST_OK;
+}
+
+static st_status batch_enqueue(st_batch_t b, int n, int cur, cudaStream_t s)
+{
+    return enqueue_batch_plan(b->plan, n, cur, s);
+}
+
+st_status stencil_batch_step(st_batch_t b, int nsteps, void* stream)
+{
+    if (!b) return fail(ST_ERR_ARG, "stencil_batch_step: NULL handle");
+    if (nsteps < 0) return fail(ST_ERR_ARG, "stencil_batch_step: negative step count");
+    if (!b->bound) return fail(ST_ERR_STATE, "stencil_batch_step: bind first");
+    cudaStream_t s = (cudaStream_t)stream;
+    b->last = s;
+    if (nsteps == 0) return ST_OK;
+    const int key = nsteps * 2 + b->cur;
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        ST_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        st_status erc = batch_enqueue(b, nsteps, b->cur, b->cap);
+        cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
+        if (erc != ST_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return erc;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+        it = b->graphs.emplace(key, exec).first;
+    }
+    ST_CUDA_TRY(cudaGraphLaunch(it->second, s));
+    if (nsteps & 1) b->cur = 1 - b->cur;
+    return ST_OK;
+}
+
+st_status stencil_batch_tune(st_batch_t b, int nsteps, void* stream)
+{
+    if (!b) return fail(ST_ERR_ARG, "stencil_batch_tune: NULL handle");
+    if (nsteps < 1) return fail(ST_ERR_ARG, "stencil_batch_tune: nsteps >= 1");
+    if (!b->bound) return fail(ST_ERR_STATE, "stencil_batch_tune: bind first");
+    cudaStream_t s = (cudaStream_t)stream;
+    b->last = s;
+    st_status rc = tune_batch_plan(b->plan, b->geoms, b->a.data(), b->b.data(), nsteps, b->cur, s);
+    drop_batch_graphs(b);
+    return rc;
+}
+
+st_status stencil_batch_config(st_batch_t b, int* cfg)
+{
+    if (!b || !cfg) return fail(ST_ERR_ARG, "stencil_batch_config: NULL argument");
+    batch_plan_config(b->plan, cfg);
+    return ST_OK;
+}
+
+st_status stencil_batch_current(st_batch_t b, int* slot)
+{
+    if (!b || !slot) return fail(ST_ERR_ARG, "stencil_batch_current: NULL argument");
+    *slot = b->cur;
+    return ST_OK;
+}
+
+st_status stencil_batch_sync(st_batch_t b)
+{
+    if (!b) return fail(ST_ERR_ARG, "stencil_batch_sync: NULL handle");
+    ST_CUDA_TRY(cudaStreamSynchronize(b->last));
+    if (!b->d_status) return ST_OK;
+    int code = 0;
+    ST_CUDA_TRY(cudaMemcpy(&code, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code != 0) {
+        ST_CUDA_TRY(cudaMemset(b->d_status, 0, sizeof(int)));
+        if (code == ST_ERR_DEVICE_TIMEOUT) return fail(ST_ERR_DEVICE_TIMEOUT, "device: bounded wait ran out");
+        return fail(ST_ERR_BOUNDS, "device: bounds check fired");
+    }
+    return ST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Internal declarations shared by the translation units of libstencil.
+// Not part of the public ABI (that is include/stencil.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/stencil.h"
+
+namespace st {
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local message behind stencil_last_error)
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+st_status fail(st_status code, const std::string& msg);
+st_status cuda_fail(cudaError_t e, const char* what);
+
+#define ST_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return ::st::cuda_fail(_e, #expr); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Padded-grid geometry.  2D grids are stored as one plane: nz = 1, no z ghosts.
+// ---------------------------------------------------------------------------
+struct Geom {
+    int ndim;        // 2 or 3
+    int r;           // ghost width (x and y, and z in 3D)
+    int rz;          // ghost width along z (0 in 2D)
+    int esize;       // bytes per element
+    int64_t nz, ny, nx;  // interior extents
+    int64_t xl;      // padded column of interior x = 0 (16-byte aligned)
+    int64_t pitch;   // padded row length in elements (multiple of 16 bytes)
+    int64_t pny;     // padded rows per plane
+    int64_t pnz;     // padded planes
+    int64_t plane;   // elements per padded plane
+    int64_t elems;   // elements per buffer
+    int64_t origin;  // linear index of interior (0, 0, 0)
+    int64_t npoints; // interior points
+};
+
+Geom make_geom(int ndim, const int64_t* dims, int r, int esize);
+
+// Parameters of the one-thread-per-point kernels (passed by value).
+struct GenParams {
+    int64_t nz, ny, nx;
+    int64_t pitch, plane, origin;
+    int npts;
+    int periodic;
+    int leapfrog;
+    int has_kappa;
+    int64_t src;           // linear padded index of the source point, -1: none
+    const double* src_amp; // device amplitudes
+    int64_t src_count;
+    int64_t step;          // step index of this launch (for the source)
+    int32_t dz[ST_MAX_POINTS], dy[ST_MAX_POINTS], dx[ST_MAX_POINTS];
+    int64_t lin[ST_MAX_POINTS];  // linear offset in the padded layout
+    double alpha[ST_MAX_POINTS], beta[ST_MAX_POINTS];
+};
+
+// Kernel launchers (k_generic.cu) -------------------------------------------
+cudaError_t launch_generic_sweep(int esize, const void* in, void* out, const void* prev,
+                                 const void* kappa, const GenParams& P, cudaStream_t s);
+cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_in, void* lam_out,
+                                   const void* kappa, double* gk, const GenParams& P,
+                                   cudaStream_t s);
+cudaError_t launch_fill_ghosts(int esize, void* buf, const Geom& g, double value, cudaStream_t s);
+cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g, double* partials,
+                          int nblocks, double* out, int mode, void* lam_out, cudaStream_t s);
+
+}  // namespace st

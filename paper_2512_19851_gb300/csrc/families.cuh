@@ -1,0 +1,114 @@
+// Kernel families: which kernel a grid handle dispatches to, and the
+// launch-argument structs shared by the step driver and the kernels.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace st {
+
+enum FamilyKind {
+    FAM_GENERIC = 0,    // one thread per point, any stencil (k_generic.cu)
+    FAM_STAR3D = 1,     // 3D star, z-streaming with bulk-copy staged planes (k_star3d.cu)
+    FAM_2D_TILE = 2,    // 2D tile kernel (k_2d.cu)
+};
+
+struct FamilyDesc {
+    Geom g;
+    int npts;
+    const int32_t* off;  // npts * 3 (dz, dy, dx)
+    const double* alpha;
+    const double* beta;
+    bool has_beta;
+    bool periodic;
+    int levels;
+    bool star;
+    bool force_generic;
+};
+
+// Star stencil coefficients in per-axis form: centre weight plus, for every
+// axis a (0 = z, 1 = y, 2 = x), side s (0: -j, 1: +j) and distance j (1..R),
+// the constant part ca and per-cell part cb of the weight.
+struct StarCoef {
+    int R;
+    double c_a, c_b;
+    double a[3][2][ST_MAX_RADIUS];
+    double b[3][2][ST_MAX_RADIUS];
+};
+
+struct Family {
+    FamilyKind kind;
+    const char* name;
+    GenParams gp;   // generic parameters (also used by the adjoint)
+    StarCoef sc;    // star families
+    Geom g;
+    bool periodic;
+    bool has_beta;
+    int levels;
+    int variant;    // family-specific launch variant
+};
+
+struct SweepArgs {
+    const void* in;
+    void* out;
+    const void* prev;   // u_{t-1} (leapfrog; equals out)
+    const void* kappa;
+    int64_t step;
+    int64_t src;
+    const double* src_amp;
+    int64_t src_count;
+    int* status;
+};
+
+struct AdjointArgs {
+    const void* u;
+    const void* lam_in;
+    void* lam_out;
+    const void* kappa;
+    double* gk;
+};
+
+Family select_family(const FamilyDesc& d);
+cudaError_t launch_family(const Family& f, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_family_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
+
+// Optimised kernels (return cudaErrorNotSupported when the case is not theirs)
+cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_star3d_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
+bool star3d_supports(const FamilyDesc& d, int* variant, const char** name);
+cudaError_t launch_tile2d(const Family& f, const SweepArgs& a, cudaStream_t s);
+bool tile2d_supports(const FamilyDesc& d, int* variant, const char** name);
+
+// ---------------------------------------------------------------------------
+// Batched plan (k_batch.cu)
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+    int ngrids = 0;
+    int npts = 0;
+    bool periodic = true;
+    int esize = 4;
+    bool generic = false;
+    std::vector<GenParams> gp;     // per-grid generic parameters
+    std::vector<void*> a, b;
+    // persistent-kernel tables (device)
+    void* d_desc = nullptr;        // per-grid descriptors
+    void* d_work = nullptr;        // work items
+    int nwork = 0;
+    int cfg[4] = {0, 0, 0, 0};     // tile x, tile y, threads, steps per pass
+    int* status = nullptr;
+    int nsm = 0;
+    std::vector<double> weights;
+    std::vector<int32_t> off;
+};
+
+BatchPlan make_batch_plan(const std::vector<Geom>& geoms, int npts, const int32_t* off2, const double* weights,
+                          bool periodic, st_dtype dtype, bool force_generic);
+st_status bind_batch_plan(BatchPlan& p, const std::vector<Geom>& geoms, void* const* a, void* const* b, int* status);
+st_status enqueue_batch_plan(BatchPlan& p, int nsteps, int cur, cudaStream_t s);
+st_status tune_batch_plan(BatchPlan& p, const std::vector<Geom>& geoms, void* const* a, void* const* b, int nsteps,
+                          int cur, cudaStream_t s);
+void batch_plan_config(const BatchPlan& p, int* cfg);
+void free_batch_plan(BatchPlan& p);
+
+}  // namespace st

@@ -1,0 +1,262 @@
+// One-thread-per-point kernels: the general form of the update (any offsets,
+// constant or per-cell weights, one or two time levels), its transpose, the
+// ghost fill of a Dirichlet boundary and the double-precision reductions.
+//
+// The sweep kernel has the shape of the kernels the paper's backend generates
+// (Sec. III-C "Code generation": each thread computes one element of the
+// output slice, the grid covers the whole slice).  It is the fallback for any
+// stencil the specialised families do not cover and the "plain launch"
+// baseline of the batched workload.
+#include "common.cuh"
+
+namespace st {
+
+namespace {
+
+__device__ __forceinline__ int64_t wrap1(int64_t i, int64_t n)
+{
+    // |offset| < n is validated on the host, so one correction suffices
+    i = (i < 0) ? i + n : i;
+    return (i >= n) ? i - n : i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sweep_generic(const T* __restrict__ in, T* out, const T* prev, const T* __restrict__ kappa,
+                const __grid_constant__ GenParams P)
+{
+    const int64_t x = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t y = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    const int64_t z = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    const int64_t p = P.origin + z * P.plane + y * P.pitch + x;
+    const T kap = P.has_kappa ? kappa[p] : T(0);
+    T acc = T(0);
+    for (int k = 0; k < P.npts; ++k) {
+        T v;
+        if (P.periodic) {
+            const int64_t zz = wrap1(z + P.dz[k], P.nz);
+            const int64_t yy = wrap1(y + P.dy[k], P.ny);
+            const int64_t xx = wrap1(x + P.dx[k], P.nx);
+            v = in[P.origin + zz * P.plane + yy * P.pitch + xx];
+        } else {
+            v = in[p + P.lin[k]];
+        }
+        T w = T(P.alpha[k]);
+        if (P.has_kappa) w = fma(T(P.beta[k]), kap, w);
+        acc = fma(w, v, acc);
+    }
+    if (P.leapfrog) acc = acc - prev[p];
+    if (p == P.src && P.step >= 0 && P.step < P.src_count) acc = acc + T(P.src_amp[P.step]);
+    out[p] = acc;
+}
+
+// Transpose step: lambda_t[q] = sum_k w_k(q - o_k) lambda_{t+1}[q - o_k], and the
+// coefficient gradient gk[q] += lambda_{t+1}[q] * sum_k beta_k u_t[q + o_k].
+// Dirichlet: q - o_k may be a ghost cell; lambda's ghosts are zero and the
+// coefficient field's ghosts finite, so those terms vanish.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adjoint_generic(const T* __restrict__ u, const T* __restrict__ lam, T* __restrict__ lout,
+                  const T* __restrict__ kappa, double* __restrict__ gk,
+                  const __grid_constant__ GenParams P)
+{
+    const int64_t x = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t y = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    const int64_t z = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    const int64_t q = P.origin + z * P.plane + y * P.pitch + x;
+    T acc = T(0);
+    T s = T(0);
+    for (int k = 0; k < P.npts; ++k) {
+        int64_t pm, pp;
+        if (P.periodic) {
+            pm = P.origin + wrap1(z - P.dz[k], P.nz) * P.plane + wrap1(y - P.dy[k], P.ny) * P.pitch +
+                 wrap1(x - P.dx[k], P.nx);
+            pp = P.origin + wrap1(z + P.dz[k], P.nz) * P.plane + wrap1(y + P.dy[k], P.ny) * P.pitch +
+                 wrap1(x + P.dx[k], P.nx);
+        } else {
+            pm = q - P.lin[k];
+            pp = q + P.lin[k];
+        }
+        T w = T(P.alpha[k]);
+        if (P.has_kappa) w = fma(T(P.beta[k]), kappa[pm], w);
+        acc = fma(w, lam[pm], acc);
+        if (gk) s = fma(T(P.beta[k]), u[pp], s);
+    }
+    lout[q] = acc;
+    if (gk) gk[q] += (double)lam[q] * (double)s;
+}
+
+// Write `value` into every cell of a padded buffer that is not interior.
+// One block per padded row.
+template <typename T>
+__global__ void k_fill_ghosts(T* __restrict__ buf, Geom g, T value)
+{
+    const int64_t rows = g.pnz * g.pny;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int64_t pz = row / g.pny;
+        const int64_t py = row - pz * g.pny;
+        T* rp = buf + pz * g.plane + py * g.pitch;
+        const bool ghost_row = (pz < g.rz) || (pz >= g.rz + g.nz) || (py < g.r) || (py >= g.r + g.ny);
+        if (ghost_row) {
+            for (int64_t x = threadIdx.x; x < g.pitch; x += blockDim.x) rp[x] = value;
+        } else {
+            for (int64_t x = threadIdx.x; x < g.xl; x += blockDim.x) rp[x] = value;
+            for (int64_t x = g.xl + g.nx + threadIdx.x; x < g.pitch; x += blockDim.x) rp[x] = value;
+        }
+    }
+}
+
+// Deterministic block reduction of (sum, sum of squares, max) in double.
+struct Red3 {
+    double s, q, m;
+};
+
+__device__ __forceinline__ Red3 warp_red(Red3 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.s += __shfl_down_sync(0xffffffffu, v.s, o);
+        v.q += __shfl_down_sync(0xffffffffu, v.q, o);
+        v.m = fmax(v.m, __shfl_down_sync(0xffffffffu, v.m, o));
+    }
+    return v;
+}
+
+__device__ Red3 block_red(Red3 v)
+{
+    __shared__ double sh[3][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_red(v);
+    if (lane == 0) {
+        sh[0][wid] = v.s;
+        sh[1][wid] = v.q;
+        sh[2][wid] = v.m;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    Red3 w{0.0, 0.0, 0.0};
+    if (wid == 0) {
+        if (lane < nw) w = Red3{sh[0][lane], sh[1][lane], sh[2][lane]};
+        w = warp_red(w);
+    }
+    __syncthreads();
+    return w;  // valid in thread 0
+}
+
+// mode 0: d = a - b (b may be null); mode 1: also lam_out = d on the interior.
+// One block handles whole interior rows; partials[3*block + {0,1,2}].
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b, Geom g, double* __restrict__ partials,
+                 int mode, T* __restrict__ lam_out)
+{
+    Red3 acc{0.0, 0.0, 0.0};
+    const int64_t rows = g.nz * g.ny;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int64_t z = row / g.ny;
+        const int64_t y = row - z * g.ny;
+        const int64_t base = g.origin + z * g.plane + y * g.pitch;
+        for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x) {
+            const T av = a[base + x];
+            const T bv = b ? b[base + x] : T(0);
+            const double d = (double)av - (double)bv;
+            if (mode == 1) lam_out[base + x] = av - bv;
+            acc.s += d;
+            acc.q += d * d;
+            acc.m = fmax(acc.m, fabs(d));
+        }
+    }
+    acc = block_red(acc);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x + 0] = acc.s;
+        partials[3 * blockIdx.x + 1] = acc.q;
+        partials[3 * blockIdx.x + 2] = acc.m;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_reduce_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out, int mode)
+{
+    Red3 acc{0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+        acc.s += partials[3 * i + 0];
+        acc.q += partials[3 * i + 1];
+        acc.m = fmax(acc.m, partials[3 * i + 2]);
+    }
+    acc = block_red(acc);
+    if (threadIdx.x == 0) {
+        if (mode == 1) {
+            out[0] = 0.5 * acc.q;
+        } else {
+            out[0] = acc.s;
+            out[1] = acc.q;
+            out[2] = acc.m;
+        }
+    }
+}
+
+dim3 point_grid(const GenParams& P)
+{
+    return dim3((unsigned)((P.nx + 31) / 32), (unsigned)((P.ny + 7) / 8), (unsigned)P.nz);
+}
+
+}  // namespace
+
+cudaError_t launch_generic_sweep(int esize, const void* in, void* out, const void* prev,
+                                 const void* kappa, const GenParams& P, cudaStream_t s)
+{
+    if (P.nz * P.ny * P.nx == 0) return cudaSuccess;
+    dim3 grid = point_grid(P), block(32, 8);
+    if (esize == 8)
+        k_sweep_generic<double><<<grid, block, 0, s>>>((const double*)in, (double*)out,
+                                                       (const double*)prev, (const double*)kappa, P);
+    else
+        k_sweep_generic<float><<<grid, block, 0, s>>>((const float*)in, (float*)out,
+                                                      (const float*)prev, (const float*)kappa, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_in, void* lam_out,
+                                   const void* kappa, double* gk, const GenParams& P,
+                                   cudaStream_t s)
+{
+    if (P.nz * P.ny * P.nx == 0) return cudaSuccess;
+    dim3 grid = point_grid(P), block(32, 8);
+    if (esize == 8)
+        k_adjoint_generic<double><<<grid, block, 0, s>>>((const double*)u_t, (const double*)lam_in,
+                                                         (double*)lam_out, (const double*)kappa, gk, P);
+    else
+        k_adjoint_generic<float><<<grid, block, 0, s>>>((const float*)u_t, (const float*)lam_in,
+                                                        (float*)lam_out, (const float*)kappa, gk, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_ghosts(int esize, void* buf, const Geom& g, double value, cudaStream_t s)
+{
+    const int64_t rows = g.pnz * g.pny;
+    const unsigned blocks = (unsigned)(rows < 65535 ? rows : 65535);
+    if (esize == 8)
+        k_fill_ghosts<double><<<blocks, 256, 0, s>>>((double*)buf, g, value);
+    else
+        k_fill_ghosts<float><<<blocks, 256, 0, s>>>((float*)buf, g, (float)value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g, double* partials,
+                          int nblocks, double* out, int mode, void* lam_out, cudaStream_t s)
+{
+    if (esize == 8)
+        k_reduce_partial<double><<<nblocks, 256, 0, s>>>((const double*)a, (const double*)b, g, partials,
+                                                         mode, (double*)lam_out);
+    else
+        k_reduce_partial<float><<<nblocks, 256, 0, s>>>((const float*)a, (const float*)b, g, partials,
+                                                        mode, (float*)lam_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, 256, 0, s>>>(partials, nblocks, out, mode);
+    return cudaGetLastError();
+}
+
+}  // namespace st

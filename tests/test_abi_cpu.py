@@ -1,0 +1,150 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/stencil.h; host-side validation and layout work without a GPU (no
+compute call is made here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2512_19851_gb300 import abi, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "stencil.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:st_status|const char\s*\*)\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("stencil_create", "stencil_step", "stencil_adjoint", "stencil_batch_create",
+                 "stencil_batch_step", "stencil_last_error"):
+        assert must in names
+    assert set(names) == set(abi.SIGNATURES), "binding and header disagree"
+
+
+def test_library_exports_every_symbol():
+    path = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(path)
+    for n in declared_functions():
+        assert getattr(lib, n) is not None
+
+
+def test_version_and_empty_error():
+    assert "sm_103a" in abi.stencil_version()
+    assert isinstance(abi.stencil_last_error(), str)
+
+
+def _create(**kw):
+    args = dict(ndim=3, dims=(8, 9, 10), radius=0, offsets=[(0, 0, 0), (0, 0, 1), (0, 0, -1)],
+                alpha=[0.5, 0.25, 0.25], beta=None, bc=abi.ST_DIRICHLET, bc_value=0.0, dtype=abi.ST_F32,
+                time_levels=1, flags=0)
+    args.update(kw)
+    return abi.stencil_create(**args)
+
+
+def test_layout_rules():
+    for dtype, es in ((abi.ST_F32, 4), (abi.ST_F64, 8)):
+        for r in (1, 2, 4):
+            h = _create(dtype=dtype, radius=r, dims=(5, 7, 13))
+            pd, org, n = abi.stencil_layout(h, 3)
+            assert org[0] == r and org[1] == r
+            assert org[2] >= r and (org[2] * es) % 16 == 0
+            assert (pd[2] * es) % 16 == 0 and pd[2] >= org[2] + 13 + r
+            assert pd[0] == 5 + 2 * r and pd[1] == 7 + 2 * r
+            assert n == pd[0] * pd[1] * pd[2]
+            abi.stencil_destroy(h)
+    h = abi.stencil_create(2, (6, 11), 0, [(0, 0), (1, 0), (-1, 0)], [1, 0, 0], dtype=abi.ST_F64)
+    pd, org, n = abi.stencil_layout(h, 2)
+    assert pd[0] == 8 and org == (1, 2) and n == pd[0] * pd[1]
+    abi.stencil_destroy(h)
+
+
+def test_radius_is_derived_from_offsets():
+    h = _create(offsets=[(0, 0, 0), (0, 3, 0), (-2, 0, 0)], alpha=[1, 0, 0])
+    assert abi.stencil_info(h)[0] == 3
+    abi.stencil_destroy(h)
+    h = _create(radius=5)
+    assert abi.stencil_info(h)[0] == 5
+    abi.stencil_destroy(h)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(ndim=4), abi.ST_ERR_ARG),
+    (dict(dims=(0, 4, 4)), abi.ST_ERR_ARG),
+    (dict(radius=1, offsets=[(0, 0, 2)], alpha=[1.0]), abi.ST_ERR_ARG),
+    (dict(offsets=[(0, 0, 9)], alpha=[1.0]), abi.ST_ERR_ARG),
+    (dict(bc=abi.ST_PERIODIC, dims=(8, 9, 2), offsets=[(0, 0, 2)], alpha=[1.0]), abi.ST_ERR_ARG),
+    (dict(dtype=7), abi.ST_ERR_ARG),
+    (dict(time_levels=3), abi.ST_ERR_ARG),
+    (dict(flags=8), abi.ST_ERR_ARG),
+    (dict(alpha=[float("nan"), 0.25, 0.25]), abi.ST_ERR_ARG),
+])
+def test_create_rejects_bad_arguments(kw, code):
+    with pytest.raises(abi.StencilError) as e:
+        _create(**kw)
+    assert e.value.code == code
+    assert abi.stencil_last_error()
+
+
+def test_calls_before_bind_are_state_errors():
+    h = _create()
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_step(h, 1)
+    assert e.value.code == abi.ST_ERR_STATE
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_step(h, -1)
+    assert e.value.code == abi.ST_ERR_ARG
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_bind(h, 3, 256)
+    assert e.value.code == abi.ST_ERR_ARG
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_bind(h, 0, 257)  # misaligned
+    assert e.value.code == abi.ST_ERR_ARG
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_set_current(h, 2)
+    assert e.value.code == abi.ST_ERR_ARG
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_set_source(h, (1, 1, 1), [1.0])   # one time level: no source
+    assert e.value.code == abi.ST_ERR_UNSUPPORTED
+    assert abi.stencil_current(h) == 0
+    abi.stencil_destroy(h)
+
+
+def test_adjoint_workspace_size():
+    h = _create(dims=(16, 16, 16))
+    _, _, n = abi.stencil_layout(h, 3)
+    per = (n * 4 + 255) // 256 * 256
+    assert abi.stencil_adjoint_workspace(h, 200, 20) == per * (10 + 19)
+    assert abi.stencil_adjoint_workspace(h, 7, 3) == per * (3 + 2)
+    with pytest.raises(abi.StencilError):
+        abi.stencil_adjoint_workspace(h, 10, 0)
+    abi.stencil_destroy(h)
+
+
+def test_batch_create_validation_and_layout():
+    dims = np.array([[64, 80], [3, 100], [37, 41]])
+    w = np.full((3, 9), 1.0 / 9)
+    from paper_2512_19851_gb300 import inputs
+    h = abi.stencil_batch_create(dims, inputs.OFFSETS_BOX9, w, abi.ST_PERIODIC, 0.0, abi.ST_F32)
+    for i, (ny, nx) in enumerate(dims):
+        pd, org, n = abi.stencil_batch_layout(h, i)
+        assert pd[0] == ny + 2 and org == (1, 4) and pd[1] * 4 % 16 == 0 and n == pd[0] * pd[1]
+    with pytest.raises(abi.StencilError):
+        abi.stencil_batch_layout(h, 3)
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_batch_step(h, 1)
+    assert e.value.code == abi.ST_ERR_STATE
+    abi.stencil_batch_destroy(h)
+    with pytest.raises(abi.StencilError):
+        abi.stencil_batch_create([[1, 10]], inputs.OFFSETS_BOX9, np.ones((1, 9)), abi.ST_PERIODIC, 0.0, abi.ST_F32)

@@ -1,0 +1,181 @@
+"""GPU parity of the per-cell 7-point diffusion, its transpose (adjoint) and
+the coefficient gradient with checkpoint-every-m recomputation.
+
+Tolerances: FP64 <= 1e-12 normwise against the FP64 oracle; FP32 forward
+<= 1e-5 (diffusion); FP32 gradients <= 1e-3 normwise against the FP64
+oracle.  The gradient bound follows from the arithmetic: dL/dkappa sums
+lambda * (Laplacian of u_t) over 200 steps, and the FP32 Laplacian of a
+smoothed field cancels most of its digits (|sum of neighbours - 6u| is ~1e-2
+of |u|), so its relative rounding error is ~100x FP32 epsilon before the sum.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import rel_err, require_cuda, torch
+from paper_2512_19851_gb300 import abi, inputs
+from paper_2512_19851_gb300.grid import Grid, StencilFn, VarCoefProblem
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32_FWD = 1e-5
+TOL32_GRAD = 1e-3
+ALPHA = [1.0] + [0.0] * 6
+BETA = [-6.0] + [1.0] * 6
+
+
+def setup_module(_):
+    require_cuda()
+
+
+def make(shape, dtype, periodic=False, bc=0.0, generic=False):
+    return Grid(shape, inputs.OFFSETS_7PT, ALPHA, BETA, periodic=periodic, bc_value=bc, dtype=dtype,
+                generic=generic)
+
+
+def gpu_grad(v, steps, m, dtype, periodic=False, bc=0.0, generic=False):
+    g = make(v.u0.shape, dtype, periodic, bc, generic)
+    prob = VarCoefProblem(g, steps, m)
+    uT = prob.forward(v.u0, v.kappa).double().cpu().numpy()
+    lam0, gk, loss = prob.backward_from(target=v.target)
+    g.sync()
+    out = (uT, lam0.double().cpu().numpy(), gk.cpu().numpy(), float(loss.cpu()[0]), g.kernel)
+    g.close()
+    return out
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_forward_full_size(dtype):
+    """256^3, 200 steps, Dirichlet 0: the benchmark's forward."""
+    v = inputs.varcoef3d(n=256)
+    ref = oracle.varcoef7_forward(v.u0, v.kappa, False, 0.0, 200)
+    g = make(v.u0.shape, dtype)
+    g.set_field(v.u0)
+    g.set_coeff(v.kappa)
+    g.step(200)
+    g.sync()
+    got = g.current().double().cpu().numpy()
+    assert rel_err(got, ref) <= (TOL64 if dtype == torch.float64 else TOL32_FWD), g.kernel
+    g.close()
+
+
+@pytest.mark.parametrize("periodic,bc", [(False, 0.0), (False, 0.3), (True, 0.0)])
+@pytest.mark.parametrize("generic", [False, True])
+def test_gradient_fp64_matches_oracle(periodic, bc, generic):
+    v = inputs.varcoef3d(shape=(30, 27, 45))
+    steps, m = 40, 7
+    loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, bc, steps, m)
+    uT, lam0, gk, loss, kern = gpu_grad(v, steps, m, torch.float64, periodic, bc, generic)
+    assert rel_err(uT, uT_r) <= TOL64, kern
+    assert abs(loss - loss_r) <= TOL64 * loss_r
+    assert rel_err(lam0, lam_r) <= TOL64, kern
+    assert rel_err(gk, gk_r) <= TOL64, kern
+
+
+def test_gradient_fp32_matches_fp64_oracle():
+    v = inputs.varcoef3d(n=64)
+    steps, m = 200, 20
+    loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, False, 0.0, steps, m)
+    uT, lam0, gk, loss, kern = gpu_grad(v, steps, m, torch.float32)
+    assert rel_err(uT, uT_r) <= TOL32_FWD, kern
+    assert abs(loss - loss_r) <= TOL32_FWD * loss_r
+    assert rel_err(lam0, lam_r) <= TOL32_GRAD, kern
+    assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
+
+
+def test_checkpoint_interval_does_not_change_gradient():
+    """Recomputation is deterministic: m = 1, 7 and 20 give bitwise equal results."""
+    v = inputs.varcoef3d(shape=(20, 24, 32))
+    base = gpu_grad(v, 20, 20, torch.float64)
+    for m in (1, 7):
+        other = gpu_grad(v, 20, m, torch.float64)
+        assert np.array_equal(base[1], other[1]) and np.array_equal(base[2], other[2])
+
+
+def test_dot_product_identity_gpu():
+    """<S x, y> = <x, S^T y> with the GPU forward and the GPU transpose."""
+    shape = (24, 20, 28)
+    v = inputs.varcoef3d(shape=shape)
+    rng = np.random.default_rng(4)
+    x, y = rng.standard_normal(shape), rng.standard_normal(shape)
+    g = make(shape, torch.float64)
+    prob = VarCoefProblem(g, 15, 4)
+    sx = prob.forward(x, v.kappa).cpu().numpy().copy()
+    lam0, _, _ = prob.backward_from(lam_T=y)
+    st = lam0.cpu().numpy()
+    lhs, rhs = float(np.vdot(sx, y)), float(np.vdot(x, st))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.abs(sx).sum())
+    g.close()
+
+
+def test_finite_differences_32cube():
+    """Central differences of the GPU loss (FP64, 32^3 instance of the adjoint
+    workload, 200 steps) against the GPU gradient: 8 random directions and 16
+    single coordinates of kappa, 4 directions of u0.  The loss is exactly
+    quadratic in u0 and smooth in kappa, so with eps = 1e-5 the truncation
+    error is far below the FP64 rounding of the loss (~1e-13 of ~1e3 over
+    2 eps), which sets the absolute floor of 1e-7."""
+    v = inputs.varcoef3d(n=32)
+    steps, m = 200, 20
+    _, g_u, g_k, _, _ = gpu_grad(v, steps, m, torch.float64)
+    grid = make(v.u0.shape, torch.float64)
+    prob = VarCoefProblem(grid, steps, m)
+    tgt = torch.as_tensor(v.target, device=grid.device)
+
+    def L(u0, kappa):
+        uT = prob.forward(u0, kappa)
+        return 0.5 * float(((uT - tgt) ** 2).sum())
+
+    rng = np.random.default_rng(0)
+    eps = 1e-5
+    for i in range(8):
+        d = rng.standard_normal(v.kappa.shape)
+        d /= np.linalg.norm(d)
+        fd = (L(v.u0, v.kappa + eps * d) - L(v.u0, v.kappa - eps * d)) / (2 * eps)
+        assert abs(fd - float(np.sum(g_k * d))) <= 1e-6 * abs(fd) + 1e-7
+    for i in range(4):
+        d = rng.standard_normal(v.u0.shape)
+        d /= np.linalg.norm(d)
+        fd = (L(v.u0 + eps * d, v.kappa) - L(v.u0 - eps * d, v.kappa)) / (2 * eps)
+        assert abs(fd - float(np.sum(g_u * d))) <= 1e-6 * abs(fd) + 1e-7
+    for j in range(16):
+        p = tuple(int(c) for c in rng.integers(0, 32, size=3))
+        e = np.zeros(v.kappa.shape)
+        e[p] = 1.0
+        fd = (L(v.u0, v.kappa + eps * e) - L(v.u0, v.kappa - eps * e)) / (2 * eps)
+        assert abs(fd - g_k[p]) <= 1e-6 * abs(fd) + 1e-7
+    grid.close()
+
+
+def test_autograd_function():
+    shape = (16, 18, 20)
+    v = inputs.varcoef3d(shape=shape)
+    steps, m = 12, 5
+    loss_r, _, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, False, 0.0, steps, m)
+    g = make(shape, torch.float64)
+    prob = VarCoefProblem(g, steps, m)
+    u0 = torch.tensor(v.u0, device="cuda", requires_grad=True)
+    kappa = torch.tensor(v.kappa, device="cuda", requires_grad=True)
+    uT = StencilFn.apply(u0, kappa, prob)
+    loss = 0.5 * ((uT - torch.as_tensor(v.target, device="cuda")) ** 2).sum()
+    loss.backward()
+    assert abs(float(loss) - loss_r) <= 1e-12 * loss_r
+    assert rel_err(u0.grad.cpu().numpy(), lam_r) <= TOL64
+    assert rel_err(kappa.grad.cpu().numpy(), gk_r) <= TOL64
+    g.close()
+
+
+def test_adjoint_argument_errors():
+    g = make((8, 8, 8), torch.float32)
+    prob = VarCoefProblem(g, 4, 2)
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_adjoint(g.h, 4, 2, prob.ws.data_ptr(), prob.lam.data_ptr(), prob.lam.data_ptr(), 0)
+    assert e.value.code == abi.ST_ERR_ALIAS
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_step_ckpt(g.h, 4, 0, prob.ws.data_ptr())
+    assert e.value.code == abi.ST_ERR_ARG
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_bind(g.h, abi.ST_SLOT_B, g.bufs[0].data_ptr())
+    assert e.value.code == abi.ST_ERR_ALIAS
+    g.close()

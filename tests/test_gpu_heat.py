@@ -1,0 +1,211 @@
+"""GPU parity of the constant-weight sweeps against the CPU oracle:
+2D 5-point Jacobi heat (FP64, Dirichlet 0) and 3D 7-point heat (periodic,
+FP64 and FP32).  Tolerances (normwise max relative error, max|x-ref|/max|ref|):
+FP64 <= 1e-12 after all steps; FP32 <= 1e-5 against the FP64 oracle for
+diffusion.  Both are the bounds stated for this path."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import (closed_form_heat3d, cone_box, five_point, rel_err, require_cuda, run_const,
+                         seven_point, torch)
+from paper_2512_19851_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+def setup_module(_):
+    require_cuda()
+
+
+# ---------------------------------------------------------------- 2D 5-point (configs: heat2d)
+@pytest.mark.parametrize("shape", [(256, 256), (37, 300), (1, 65), (130, 3)])
+@pytest.mark.parametrize("generic", [False, True])
+def test_heat2d_matches_oracle(shape, generic):
+    u0 = inputs.heat2d(shape=shape)
+    offs, w = five_point(0.2)
+    ref = oracle.sweep_const(u0, offs, w, False, 0.0, 100)
+    got, _ = run_const(u0, offs, w, False, 0.0, 100, torch.float64, generic=generic)
+    assert rel_err(got, ref) <= TOL64
+
+
+@pytest.mark.parametrize("steps,chunks", [(0, [0]), (1, [1]), (2, [2]), (7, [7]), (7, [3, 1, 3]), (100, [51, 49])])
+def test_heat2d_step_counts_and_chunks(steps, chunks):
+    u0 = inputs.heat2d(shape=(61, 77))
+    offs, w = five_point(0.2)
+    ref = oracle.sweep_const(u0, offs, w, False, 0.0, steps)
+    got, _ = run_const(u0, offs, w, False, 0.0, steps, torch.float64, chunks=chunks)
+    assert rel_err(got, ref) <= TOL64
+
+
+def test_heat2d_paper_example_boundary_one():
+    """Example 1's program shape: boundary ring 1, weights 1/4 on N,S,W,E,
+    interior 0; all values dyadic, so the GPU matches the oracle bitwise."""
+    offs = [(-1, 0), (1, 0), (0, -1), (0, 1)]
+    u0 = np.zeros((40, 33))
+    ref = oracle.sweep_const(u0, offs, [0.25] * 4, False, 1.0, 10)
+    got, _ = run_const(u0, offs, [0.25] * 4, False, 1.0, 10, torch.float64)
+    assert np.array_equal(got, ref)
+
+
+def test_heat2d_dirichlet_sine_decay_closed_form():
+    n, a, steps = 256, 0.2, 100
+    i = np.arange(1, n + 1)
+    u0 = np.sin(np.pi * 1 * i / (n + 1))[:, None] * np.sin(np.pi * 2 * i / (n + 1))[None, :]
+    lam = 1 - 4 * a * (np.sin(np.pi * 1 / (2 * (n + 1))) ** 2 + np.sin(np.pi * 2 / (2 * (n + 1))) ** 2)
+    offs, w = five_point(a)
+    got, _ = run_const(u0, offs, w, False, 0.0, steps, torch.float64)
+    assert rel_err(got, lam ** steps * u0) <= TOL64
+
+
+# ---------------------------------------------------------------- 3D 7-point (configs: heat3d)
+@pytest.mark.parametrize("shape", [(40, 36, 52), (17, 23, 129), (3, 64, 8), (64, 64, 512)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_heat3d_matches_oracle(shape, dtype):
+    h = inputs.heat3d(shape=shape)
+    offs, w = seven_point(0.1)
+    ref = oracle.sweep_const(h.u0, offs, w, True, 0.0, 100)
+    got, _ = run_const(h.u0, offs, w, True, 0.0, 100, dtype)
+    assert rel_err(got, ref) <= (TOL64 if dtype == torch.float64 else TOL32)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_heat3d_dirichlet_and_generic(dtype):
+    h = inputs.heat3d(shape=(21, 30, 44))
+    offs, w = seven_point(0.1)
+    ref = oracle.sweep_const(h.u0, offs, w, False, 0.5, 33)
+    for generic in (False, True):
+        got, _ = run_const(h.u0, offs, w, False, 0.5, 33, dtype, generic=generic)
+        assert rel_err(got, ref) <= (TOL64 if dtype == torch.float64 else TOL32)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_heat3d_full_size_closed_form(dtype):
+    """512^3, 100 steps, noise off: each sine mode decays by its eigenvalue."""
+    shape = (512, 512, 512)
+    h = inputs.heat3d(shape=shape, noise=False)
+    offs, w = seven_point(0.1)
+    got, kern = run_const(h.u0, offs, w, True, 0.0, 100, dtype)
+    ref = closed_form_heat3d(h, 0.1, 100, shape)
+    assert rel_err(got, ref) <= (TOL64 if dtype == torch.float64 else TOL32), kern
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_heat3d_full_size_with_noise(dtype):
+    """512^3 with noise, in the benchmark's launch configuration: every point
+    against the oracle after 6 steps, and after all 100 steps at sampled
+    points, each computed by the oracle on its periodic domain of dependence
+    (a 201^3 box; the centre is exact after 100 radius-1 steps)."""
+    shape = (512, 512, 512)
+    h = inputs.heat3d(shape=shape)
+    offs, w = seven_point(0.1)
+    tol = TOL64 if dtype == torch.float64 else TOL32
+    got6, _ = run_const(h.u0, offs, w, True, 0.0, 6, dtype)
+    ref6 = oracle.sweep_const(h.u0, offs, w, True, 0.0, 6)
+    assert rel_err(got6, ref6) <= tol
+    del got6, ref6
+    got, _ = run_const(h.u0, offs, w, True, 0.0, 100, dtype)
+    scale = float(np.max(np.abs(got)))
+    for c in [(0, 0, 0), (511, 3, 256), (200, 511, 17)]:
+        box = cone_box(h.u0, c, 100)
+        ref = oracle.sweep_const(box, offs, w, True, 0.0, 100)[100, 100, 100]
+        assert abs(got[c] - ref) <= tol * scale, c
+
+
+def test_heat3d_sum_conserved_and_constant_invariant():
+    shape = (48, 40, 64)
+    h = inputs.heat3d(shape=shape)
+    offs, w = seven_point(0.1)
+    got, _ = run_const(h.u0, offs, w, True, 0.0, 50, torch.float64)
+    assert abs(got.sum() - h.u0.sum()) < 1e-10 * np.abs(h.u0).sum()
+    c = np.full(shape, 0.375)
+    got, _ = run_const(c, offs, w, True, 0.0, 9, torch.float64)
+    assert np.allclose(got, 0.375, rtol=0, atol=1e-15)
+
+
+def test_heat3d_translation_equivariance_bitwise():
+    """Periodic: shifting the input shifts the output, bit for bit."""
+    shape = (32, 24, 40)
+    h = inputs.heat3d(shape=shape)
+    offs, w = seven_point(0.1)
+    a, _ = run_const(h.u0, offs, w, True, 0.0, 20, torch.float32)
+    s = (5, 7, 11)
+    b, _ = run_const(np.roll(h.u0, s, axis=(0, 1, 2)), offs, w, True, 0.0, 20, torch.float32)
+    assert np.array_equal(np.roll(a, s, axis=(0, 1, 2)), b)
+
+
+def test_deterministic_repeat():
+    h = inputs.heat3d(shape=(30, 31, 70))
+    offs, w = seven_point(0.1)
+    a, _ = run_const(h.u0, offs, w, True, 0.0, 17, torch.float32)
+    b, _ = run_const(h.u0, offs, w, True, 0.0, 17, torch.float32)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_general_offsets_radius2(periodic):
+    """Asymmetric offsets up to radius 2, unequal weights (generic family)."""
+    rng = np.random.default_rng(5)
+    offs = [(0, 0, 0), (0, 0, 2), (0, -1, 1), (-2, 0, 0), (1, 1, 0), (0, 2, -2)]
+    w = list(rng.uniform(-0.2, 0.3, size=len(offs)))
+    u0 = rng.standard_normal((9, 14, 21))
+    ref = oracle.sweep_const(u0, offs, w, periodic, 0.3, 5)
+    got, kern = run_const(u0, offs, w, periodic, 0.3, 5, torch.float64)
+    assert rel_err(got, ref) <= TOL64, kern
+
+
+def test_dirichlet_ghosts_hold_boundary_value():
+    from paper_2512_19851_gb300.grid import Grid
+    offs, w = five_point(0.2)
+    g = Grid((20, 30), offs, w, periodic=False, bc_value=0.75, dtype=torch.float64)
+    g.set_field(np.zeros((20, 30)))
+    g.step(5)
+    g.sync()
+    for buf in g.bufs:
+        b = buf.cpu().numpy()
+        r, xl = g.origin
+        assert np.all(b[:r, :] == 0.75) and np.all(b[r + 20:, :] == 0.75)
+        assert np.all(b[:, :xl] == 0.75) and np.all(b[:, xl + 30:] == 0.75)
+    g.close()
+
+
+def test_reductions_match_oracle():
+    from paper_2512_19851_gb300.grid import Grid
+    offs, w = seven_point(0.1)
+    rng = np.random.default_rng(3)
+    for dtype in (torch.float64, torch.float32):
+        g = Grid((13, 50, 77), offs, w, periodic=True, dtype=dtype)
+        a = rng.standard_normal((13, 50, 77))
+        b = rng.standard_normal((13, 50, 77))
+        g.set_field(a, 0)
+        g.set_field(b, 1)
+        out = g.reduce(g.bufs[0], g.bufs[1]).cpu().numpy()
+        ref = oracle.reduce(a.astype(np.float32 if dtype == torch.float32 else np.float64),
+                            b.astype(np.float32 if dtype == torch.float32 else np.float64))
+        assert abs(out[0] - ref[0]) <= 1e-12 * np.abs(a - b).sum()
+        assert abs(out[1] - ref[1]) <= 1e-12 * ref[1]
+        assert out[2] == ref[2]
+        out1 = g.reduce(g.bufs[0]).cpu().numpy()
+        ref1 = oracle.reduce(g.interior(g.bufs[0]).cpu().numpy())
+        assert abs(out1[1] - ref1[1]) <= 1e-12 * ref1[1] and out1[2] == ref1[2]
+        g.close()
+
+
+def test_run_host_end_to_end():
+    from paper_2512_19851_gb300 import abi
+    from paper_2512_19851_gb300.grid import Grid
+    shape = (20, 33, 64)
+    h = inputs.heat3d(shape=shape)
+    offs, w = seven_point(0.1)
+    for dtype, npdt in ((torch.float32, np.float32), (torch.float64, np.float64)):
+        g = Grid(shape, offs, w, periodic=True, dtype=dtype)
+        src = torch.from_numpy(h.u0.astype(npdt)).pin_memory()
+        dst = torch.empty(shape, dtype=dtype).pin_memory()
+        abi.stencil_run_host(g.h, 12, src.data_ptr(), dst.data_ptr(), torch.cuda.current_stream())
+        g.sync()
+        ref = oracle.sweep_const(h.u0, offs, w, True, 0.0, 12)
+        assert rel_err(dst.numpy(), ref) <= (TOL64 if dtype == torch.float64 else TOL32)
+        g.close()

@@ -1,0 +1,128 @@
+"""GPU parity of the radius-4 leapfrog wave update against the CPU oracle.
+
+Tolerances: FP64 <= 1e-12 normwise; FP32 <= 1e-3 normwise against the FP64
+oracle.  The FP32 bound comes from the arithmetic: the leapfrog scheme is not
+dissipative, so rounding errors are not damped; the oracle's own FP32 build of
+the same definition drifts 2.2e-5 from FP64 at 64^3 over 1000 steps, and the
+bound leaves a factor ~45 for the longer 512^3 runs and a different rounding
+order."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import rel_err, require_cuda, torch
+from paper_2512_19851_gb300 import inputs, stencils
+from paper_2512_19851_gb300.grid import Grid
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32_WAVE = 1e-3
+
+
+def setup_module(_):
+    require_cuda()
+
+
+def a8():
+    """Coefficients for the oracle side, from its own Taylor solve."""
+    return [float(x) for x in oracle.taylor_second_derivative_coeffs(4)]
+
+
+def run_wave(w, n, steps, dtype, generic=False, chunks=None, u_now=None, u_prev=None):
+    offs, alpha, beta = stencils.wave25()
+    g = Grid((n, n, n), offs, alpha, beta, periodic=False, bc_value=0.0, dtype=dtype, time_levels=2,
+             generic=generic)
+    g.set_coeff(w.m)
+    z = np.zeros((n, n, n))
+    g.set_levels(z if u_now is None else u_now, z if u_prev is None else u_prev)
+    g.set_source(w.src, w.amps)
+    for c in (chunks or [steps]):
+        g.step(c)
+    g.sync()
+    cur = g.current().double().cpu().numpy()
+    prev = g.previous().double().cpu().numpy()
+    kern = g.kernel
+    g.close()
+    return cur, prev, kern
+
+
+@pytest.mark.parametrize("n,steps", [(48, 300), (40, 57)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_wave_matches_oracle(n, steps, dtype):
+    w = inputs.wave3d(n=n, steps=steps)
+    z = np.zeros((n, n, n))
+    ref, ref_prev = oracle.wave25(z, z, w.m, a8(), w.src, w.amps, False, 0.0, steps)
+    cur, prev, kern = run_wave(w, n, steps, dtype)
+    tol = TOL64 if dtype == torch.float64 else TOL32_WAVE
+    assert rel_err(cur, ref) <= tol, kern
+    assert rel_err(prev, ref_prev) <= tol, kern
+
+
+def test_wave_generic_and_chunked_agree():
+    n, steps = 36, 41
+    w = inputs.wave3d(n=n, steps=steps)
+    rng = np.random.default_rng(1)
+    u1, u0 = rng.standard_normal((n, n, n)), rng.standard_normal((n, n, n))
+    ref, _ = oracle.wave25(u1, u0, w.m, a8(), w.src, w.amps, False, 0.0, steps)
+    for generic, chunks in ((True, None), (False, [10, 1, 30])):
+        cur, _, kern = run_wave(w, n, steps, torch.float64, generic=generic, chunks=chunks, u_now=u1, u_prev=u0)
+        assert rel_err(cur, ref) <= TOL64, kern
+
+
+def test_wave_full_size_sampled():
+    """520^3 layout (512^3 interior + 4 ghosts), benchmark launch
+    configuration: all points after 8 steps against the oracle, from a
+    random state so every point is exercised."""
+    n, steps = 512, 8
+    w = inputs.wave3d(n=n, steps=steps)
+    rng = np.random.default_rng(6)
+    u1 = rng.standard_normal((n, n, n))
+    u0 = u1 + 0.01 * rng.standard_normal((n, n, n))
+    ref, _ = oracle.wave25(u1, u0, w.m, a8(), w.src, w.amps, False, 0.0, steps)
+    cur, _, kern = run_wave(w, n, steps, torch.float32, u_now=u1, u_prev=u0)
+    assert rel_err(cur, ref) <= 1e-5, kern
+
+
+def test_wave_full_run_energy_and_symmetry():
+    """All 1000 steps at 512^3 in FP32: once the Ricker source has decayed
+    (t > t0 + 6/(pi f)) the discrete leapfrog energy is constant, and the
+    field is symmetric under exchanging x and y (layers vary along z only,
+    source at the centre, cubic grid)."""
+    n, steps = 512, 1000
+    w = inputs.wave3d(n=n, steps=steps)
+    offs, alpha, beta = stencils.wave25()
+    g = Grid((n, n, n), offs, alpha, beta, periodic=False, bc_value=0.0, dtype=torch.float32, time_levels=2)
+    g.set_coeff(w.m)
+    z = np.zeros((n, n, n))
+    g.set_levels(z, z)
+    g.set_source(w.src, w.amps)
+    g.step(900)
+    m = torch.as_tensor(w.m, device=g.device)
+    a = a8()
+
+    def lap(u):
+        up = torch.nn.functional.pad(u, (4, 4, 4, 4, 4, 4))
+        out = 3 * a[0] * u
+        for j in range(1, 5):
+            out = out + a[j] * (up[4 + j:4 + j + n, 4:4 + n, 4:4 + n] + up[4 - j:4 - j + n, 4:4 + n, 4:4 + n] +
+                                up[4:4 + n, 4 + j:4 + j + n, 4:4 + n] + up[4:4 + n, 4 - j:4 - j + n, 4:4 + n] +
+                                up[4:4 + n, 4:4 + n, 4 + j:4 + j + n] + up[4:4 + n, 4:4 + n, 4 - j:4 - j + n])
+        return out
+
+    def energy():
+        u1 = g.current().double()
+        u0 = g.previous().double()
+        d = u1 - u0
+        return float((d * d / m).sum() - (u1 * lap(u0)).sum())
+
+    e900 = energy()
+    g.step(100)
+    g.sync()
+    e1000 = energy()
+    assert abs(e1000 - e900) <= 1e-3 * abs(e900)
+    cur = g.current()
+    asym = float((cur - cur.transpose(1, 2)).abs().max())
+    assert asym <= TOL32_WAVE * float(cur.abs().max())
+    assert float(cur.abs().max()) > 0
+    g.close()
