@@ -268,10 +268,23 @@ st_status stencil_batch_tune(st_batch_t b, int nsteps, void* stream);
  * cfg[3] steps per pass. */
 st_status stencil_batch_config(st_batch_t b, int* cfg);
 
-/* Advance every grid nsteps steps. */
+/* Advance every grid nsteps steps.  With temporal blocking the result may end
+ * in either slot: stencil_batch_current() tells which. */
 st_status stencil_batch_step(st_batch_t b, int nsteps, void* stream);
 st_status stencil_batch_current(st_batch_t b, int* slot);
 st_status stencil_batch_sync(st_batch_t b);
+
+/*
+ * Failure-detection hook (no counterpart in the paper, whose runtime detects
+ * no device failures): advances every grid one step with the persistent
+ * kernel and then enters a grid-wide barrier that waits for one CTA more than
+ * were launched.  The barrier's bounded wait runs out after timeout_ns
+ * (1 ms .. 5 s), the kernel records ST_ERR_DEVICE_TIMEOUT in the status word
+ * and returns; stencil_batch_sync() then reports ST_ERR_DEVICE_TIMEOUT and the
+ * context stays usable.  ST_ERR_UNSUPPORTED for plans without the persistent
+ * kernel (ST_FLAG_GENERIC or offsets beyond the 3x3 neighbourhood).
+ */
+st_status stencil_batch_selftest_barrier(st_batch_t b, uint64_t timeout_ns, void* stream);
 
 #ifdef __cplusplus
 }

@@ -72,6 +72,7 @@ SIGNATURES = {
     "stencil_batch_step": (_I, [_VP, _I, _VP]),
     "stencil_batch_current": (_I, [_VP, _PI]),
     "stencil_batch_sync": (_I, [_VP]),
+    "stencil_batch_selftest_barrier": (_I, [_VP, ctypes.c_uint64, _VP]),
 }
 
 _lib = None
@@ -284,3 +285,8 @@ def stencil_batch_current(h) -> int:
 
 def stencil_batch_sync(h) -> None:
     _check(lib().stencil_batch_sync(h), "stencil_batch_sync")
+
+
+def stencil_batch_selftest_barrier(h, timeout_ns, stream=None) -> None:
+    _check(lib().stencil_batch_selftest_barrier(h, int(timeout_ns), ctypes.c_void_p(_stream(stream))),
+           "stencil_batch_selftest_barrier")

@@ -686,6 +686,7 @@ st_status stencil_batch_create(st_batch_t* out, int ngrids, const int64_t* dims,
     b->b.assign(ngrids, nullptr);
     b->plan = make_batch_plan(b->geoms, b->npts, b->off.data(), b->weights.data(), bc == ST_PERIODIC, dtype,
                               (flags & ST_FLAG_GENERIC) != 0);
+    b->plan.bc = bc_value;
     *out = b;
     return ST_OK;
 }
@@ -767,26 +768,34 @@ st_status stencil_batch_step(st_batch_t b, int nsteps, void* stream)
     cudaStream_t s = (cudaStream_t)stream;
     b->last = s;
     if (nsteps == 0) return ST_OK;
+    bool moved = false;
+    st_status rc = reserve_batch_steps(b->plan, nsteps, &moved);
+    if (rc != ST_OK) return rc;
+    if (moved) drop_batch_graphs(b);  // graphs captured earlier point at the old counters
     const int key = nsteps * 2 + b->cur;
     auto it = b->graphs.find(key);
-    if (it == b->graphs.end()) {
+    for (int attempt = 0; it == b->graphs.end() && attempt < 2; ++attempt) {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         ST_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
         st_status erc = batch_enqueue(b, nsteps, b->cur, b->cap);
         cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
-        if (erc != ST_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return erc;
+        if (erc == ST_OK && ce == cudaSuccess) {
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce == cudaSuccess) {
+                it = b->graphs.emplace(key, exec).first;
+                break;
+            }
+        } else if (graph) {
+            cudaGraphDestroy(graph);
         }
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-        ce = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
-        it = b->graphs.emplace(key, exec).first;
+        (void)cudaGetLastError();
+        if (attempt == 1) return erc != ST_OK ? erc : cuda_fail(ce, "batch graph capture");
+        batch_disable_coop(b->plan);  // retry with one launch per pass
     }
     ST_CUDA_TRY(cudaGraphLaunch(it->second, s));
-    if (nsteps & 1) b->cur = 1 - b->cur;
+    b->cur = batch_final_slot(b->plan, nsteps, b->cur);
     return ST_OK;
 }
 
@@ -800,6 +809,20 @@ st_status stencil_batch_tune(st_batch_t b, int nsteps, void* stream)
     st_status rc = tune_batch_plan(b->plan, b->geoms, b->a.data(), b->b.data(), nsteps, b->cur, s);
     drop_batch_graphs(b);
     return rc;
+}
+
+st_status stencil_batch_selftest_barrier(st_batch_t b, uint64_t timeout_ns, void* stream)
+{
+    if (!b) return fail(ST_ERR_ARG, "stencil_batch_selftest_barrier: NULL handle");
+    if (!b->bound) return fail(ST_ERR_STATE, "stencil_batch_selftest_barrier: bind first");
+    if (timeout_ns < 1000000ull || timeout_ns > 5000000000ull)
+        return fail(ST_ERR_ARG, "stencil_batch_selftest_barrier: timeout must be 1 ms .. 5 s");
+    cudaStream_t s = (cudaStream_t)stream;
+    b->last = s;
+    st_status rc = batch_barrier_selftest(b->plan, b->cur, s, timeout_ns);
+    if (rc != ST_OK) return rc;
+    b->cur = 1 - b->cur;  // the pass before the barrier advanced one step
+    return ST_OK;
 }
 
 st_status stencil_batch_config(st_batch_t b, int* cfg)

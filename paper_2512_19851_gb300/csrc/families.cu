@@ -46,10 +46,11 @@ Family select_family(const FamilyDesc& d)
     if (d.force_generic) return f;
     int variant = 0;
     const char* name = nullptr;
-    if (d.g.ndim == 3 && d.star && star3d_supports(d, &variant, &name)) {
-        f.kind = FAM_STAR3D;
+    const bool wave = d.g.ndim == 3 && d.star && wave_supports(d);
+    if (wave || (d.g.ndim == 3 && d.star && star3d_supports(d, &variant, &name))) {
+        f.kind = wave ? FAM_WAVE : FAM_STAR3D;
         f.variant = variant;
-        f.name = name;
+        f.name = wave ? "wave3d_r4_bulk_zqueue" : name;
         // per-axis coefficients
         StarCoef& c = f.sc;
         int R = 0;
@@ -84,6 +85,8 @@ cudaError_t launch_family(const Family& f, const SweepArgs& a, cudaStream_t s)
         return launch_star3d(f, a, s);
     case FAM_2D_TILE:
         return launch_tile2d(f, a, s);
+    case FAM_WAVE:
+        return launch_wave(f, a, s);
     default: {
         GenParams P = f.gp;
         P.src = a.src;

@@ -12,6 +12,7 @@ enum FamilyKind {
     FAM_GENERIC = 0,    // one thread per point, any stencil (k_generic.cu)
     FAM_STAR3D = 1,     // 3D star, z-streaming with bulk-copy staged planes (k_star3d.cu)
     FAM_2D_TILE = 2,    // 2D tile kernel (k_2d.cu)
+    FAM_WAVE = 3,       // 3D radius-4 leapfrog star (k_wave.cu)
 };
 
 struct FamilyDesc {
@@ -78,6 +79,8 @@ cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_star3d_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
 bool star3d_supports(const FamilyDesc& d, int* variant, const char** name);
 cudaError_t launch_tile2d(const Family& f, const SweepArgs& a, cudaStream_t s);
+bool wave_supports(const FamilyDesc& d);
+cudaError_t launch_wave(const Family& f, const SweepArgs& a, cudaStream_t s);
 bool tile2d_supports(const FamilyDesc& d, int* variant, const char** name);
 
 // ---------------------------------------------------------------------------
@@ -100,6 +103,7 @@ struct BatchPlan {
     int nsm = 0;
     std::vector<double> weights;
     std::vector<int32_t> off;
+    double bc = 0.0;
 };
 
 BatchPlan make_batch_plan(const std::vector<Geom>& geoms, int npts, const int32_t* off2, const double* weights,
@@ -110,5 +114,15 @@ st_status tune_batch_plan(BatchPlan& p, const std::vector<Geom>& geoms, void* co
                           int cur, cudaStream_t s);
 void batch_plan_config(const BatchPlan& p, int* cfg);
 void free_batch_plan(BatchPlan& p);
+// Slot holding the result after nsteps from slot cur (temporal blocking writes once per pass).
+int batch_final_slot(const BatchPlan& p, int nsteps, int cur);
+// Allocate per-pass counters for calls of up to nsteps (before any graph
+// capture); *moved tells that an existing table was replaced.
+st_status reserve_batch_steps(BatchPlan& p, int nsteps, bool* moved);
+// Use one launch per pass from now on (cooperative launch unavailable).
+void batch_disable_coop(BatchPlan& p);
+// Failure-detection hook: one pass, then a grid barrier that waits for one
+// CTA more than launched, so its bounded wait must run out.
+st_status batch_barrier_selftest(BatchPlan& p, int cur, cudaStream_t s, unsigned long long timeout_ns);
 
 }  // namespace st

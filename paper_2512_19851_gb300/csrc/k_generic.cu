@@ -145,27 +145,87 @@ __device__ Red3 block_red(Red3 v)
     return w;  // valid in thread 0
 }
 
+// Compensated single-precision accumulator (hi + lo carries ~48 bits): the
+// per-element work of an FP32 reduction stays on the FP32 pipe, because the
+// FP64 rate of this GPU is 1/64 of FP32.  Error-free transformations:
+// TwoSum (Knuth) for additions, fma for the exact product error.
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void f2_add(F2& acc, float x, float xlo)
+{
+    float s, e;
+    two_sum(acc.hi, x, s, e);
+    acc.hi = s;
+    acc.lo += e + xlo;
+}
+
 // mode 0: d = a - b (b may be null); mode 1: also lam_out = d on the interior.
-// One block handles whole interior rows; partials[3*block + {0,1,2}].
+// One warp handles whole interior rows; partials[3*block + {0,1,2}].
+__device__ __forceinline__ void red_elem(double av, double bv, Red3& acc)
+{
+    const double d = av - bv;
+    acc.s += d;
+    acc.q = fma(d, d, acc.q);
+    acc.m = fmax(acc.m, fabs(d));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b, Geom g, double* __restrict__ partials,
                  int mode, T* __restrict__ lam_out)
 {
-    Red3 acc{0.0, 0.0, 0.0};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t rows = g.nz * g.ny;
-    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int64_t z = row / g.ny;
-        const int64_t y = row - z * g.ny;
-        const int64_t base = g.origin + z * g.plane + y * g.pitch;
-        for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x) {
-            const T av = a[base + x];
-            const T bv = b ? b[base + x] : T(0);
-            const double d = (double)av - (double)bv;
-            if (mode == 1) lam_out[base + x] = av - bv;
-            acc.s += d;
-            acc.q += d * d;
-            acc.m = fmax(acc.m, fabs(d));
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    Red3 acc{0.0, 0.0, 0.0};
+    if constexpr (sizeof(T) == 4) {
+        F2 S{0.f, 0.f}, Q{0.f, 0.f};
+        float mh = 0.f;
+        double dmax = 0.0;
+        for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < rows; row += wstride) {
+            const int64_t z = row / g.ny;
+            const int64_t y = row - z * g.ny;
+            const int64_t base = g.origin + z * g.plane + y * g.pitch;
+            for (int64_t x = lane; x < g.nx; x += 32) {
+                const float av = a[base + x];
+                const float bv = b ? b[base + x] : 0.f;
+                float dh, dl;
+                two_sum(av, -bv, dh, dl);  // d = dh + dl exactly
+                if (mode == 1) lam_out[base + x] = dh;
+                f2_add(S, dh, dl);
+                const float p = dh * dh;
+                const float pe = fmaf(dh, dh, -p);  // dh^2 = p + pe exactly
+                f2_add(Q, p, pe + 2.f * dh * dl);
+                const float ad = fabsf(dh);
+                if (ad >= mh) {  // a new maximum is rare: resolve it in double
+                    mh = ad;
+                    dmax = fmax(dmax, fabs((double)dh + (double)dl));
+                }
+            }
+        }
+        acc.s = (double)S.hi + (double)S.lo;
+        acc.q = (double)Q.hi + (double)Q.lo;
+        acc.m = dmax;
+    } else {
+        for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < rows; row += wstride) {
+            const int64_t z = row / g.ny;
+            const int64_t y = row - z * g.ny;
+            const int64_t base = g.origin + z * g.plane + y * g.pitch;
+            for (int64_t x = lane; x < g.nx; x += 32) {
+                const double av = a[base + x];
+                const double bv = b ? (double)b[base + x] : 0.0;
+                if (mode == 1) lam_out[base + x] = av - bv;
+                red_elem(av, bv, acc);
+            }
         }
     }
     acc = block_red(acc);

@@ -1,0 +1,472 @@
+// 3D radius-1 star sweep (7-point), constant or per-cell weights, one time
+// level: the 3D heat workloads and the variable-coefficient diffusion.
+//
+// Design (one GPU, HBM-bound):
+//  * A CTA owns a tile of TY full rows (all of x) and streams it through a
+//    chunk of ZC planes.  Plane tiles (TY + 2 rows, halo included; the
+//    coefficient tile without halo) are staged in shared memory by 1D bulk
+//    copies (the TMA engine, cp.async.bulk) into a ring of NS stages, each
+//    completing on its own mbarrier; a dedicated producer warp issues them, so
+//    several planes are in flight per SM while 8 consumer warps compute.
+//  * Full rows make the x halo free: x-1/x+1 come from the same shared row
+//    (wrapped inside the row for a periodic boundary, the ghost columns for a
+//    Dirichlet one).  The y halo rows and the z planes are copied with wrapped
+//    row/plane indices when periodic, so ghost cells are never needed there.
+//  * CTAs are persistent (one per SM) and walk (y-tile, z-chunk) units with y
+//    fastest, so tiles that share halo rows run at the same time and the halo
+//    re-reads hit L2.
+//  * Consumers load 16-byte vectors from shared memory and store 16-byte
+//    vectors straight to global memory (coalesced, one write per point).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "families.cuh"
+#include "ptx.cuh"
+
+namespace st {
+
+namespace {
+
+constexpr int CONSUMER_WARPS = 16;
+constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
+
+struct Star1Params {
+    int64_t nz, ny, nx, pitch, plane, origin;
+    int rz, r, xl;
+    int TY, ZC, NS;
+    int nyt, nzc, units;
+    uint32_t stage_elems;  // per stage: u tile then coefficient tile
+    uint32_t u_elems;      // (TY + 2) * pitch
+    double wc, wxm, wxp, wym, wyp, wzm, wzp;  // constant parts (alpha)
+    double bc, bxm, bxp, bym, byp, bzm, bzp;  // per-cell parts (beta)
+    int* status;
+};
+
+template <typename T>
+struct V;
+template <>
+struct V<float> {
+    static constexpr int N = 4;
+    typedef float4 type;
+};
+template <>
+struct V<double> {
+    static constexpr int N = 2;
+    typedef double2 type;
+};
+
+template <typename T>
+__device__ __forceinline__ void ldv(const T* p, T (&v)[V<T>::N])
+{
+    typename V<T>::type t = *reinterpret_cast<const typename V<T>::type*>(p);
+    if constexpr (V<T>::N == 4) {
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    } else {
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void stv(T* p, const T (&v)[V<T>::N])
+{
+    typename V<T>::type t;
+    if constexpr (V<T>::N == 4) {
+        t.x = v[0];
+        t.y = v[1];
+        t.z = v[2];
+        t.w = v[3];
+    } else {
+        t.x = v[0];
+        t.y = v[1];
+    }
+    *reinterpret_cast<typename V<T>::type*>(p) = t;
+}
+
+__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ int64_t wrapi(int64_t i, int64_t n)
+{
+    i = i < 0 ? i + n : i;
+    return i >= n ? i - n : i;
+}
+
+// One output point from its centre, six neighbours and (optionally) kappa.
+template <typename T, bool KAPPA, bool SYM>
+__device__ __forceinline__ T point(const Star1Params& P, T c, T xm, T xp, T ym, T yp, T zm, T zp, T k)
+{
+    if constexpr (SYM) {
+        const T nb = ((((xm + xp) + ym) + yp) + zm) + zp;
+        if constexpr (KAPPA) {
+            const T wc = fma(T(P.bc), k, T(P.wc));
+            const T wn = fma(T(P.bxm), k, T(P.wxm));
+            return fma(wc, c, wn * nb);
+        } else {
+            return fma(T(P.wc), c, T(P.wxm) * nb);
+        }
+    } else {
+        T wc = T(P.wc), a = T(P.wxm), b = T(P.wxp), d = T(P.wym), e = T(P.wyp), f = T(P.wzm), g = T(P.wzp);
+        if constexpr (KAPPA) {
+            wc = fma(T(P.bc), k, wc);
+            a = fma(T(P.bxm), k, a);
+            b = fma(T(P.bxp), k, b);
+            d = fma(T(P.bym), k, d);
+            e = fma(T(P.byp), k, e);
+            f = fma(T(P.bzm), k, f);
+            g = fma(T(P.bzp), k, g);
+        }
+        T acc = wc * c;
+        acc = fma(a, xm, acc);
+        acc = fma(b, xp, acc);
+        acc = fma(d, ym, acc);
+        acc = fma(e, yp, acc);
+        acc = fma(f, zm, acc);
+        acc = fma(g, zp, acc);
+        return acc;
+    }
+}
+
+__device__ __forceinline__ void set_timeout(int* status)
+{
+    if (status) atomicCAS(status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
+}
+
+template <typename T, bool KAPPA, bool SYM, bool PERIODIC, int G>
+__global__ void __launch_bounds__(THREADS, 1)
+k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kappa, const __grid_constant__ Star1Params P)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* ring = reinterpret_cast<T*>(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)P.NS * P.stage_elems * sizeof(T));
+    uint64_t* empty = full + P.NS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int VN = V<T>::N;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.NS; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], CONSUMER_WARPS);
+        }
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+
+    const uint32_t rowb = (uint32_t)(P.pitch * sizeof(T));
+
+    if (warp == CONSUMER_WARPS) {
+        // ------------------------------------------------------------ producer
+        if (lane != 0) return;
+        uint32_t gq = 0;
+        for (int u = blockIdx.x; u < P.units; u += gridDim.x) {
+            const int yt = u % P.nyt, zc = u / P.nyt;
+            const int64_t y0 = (int64_t)yt * P.TY, z0 = (int64_t)zc * P.ZC;
+            const int tye = (int)imin64(P.TY, P.ny - y0);
+            const int zce = (int)imin64(P.ZC, P.nz - z0);
+            for (int q = 0; q < zce + 2; ++q, ++gq) {
+                const uint32_t s = gq % P.NS, k = gq / P.NS;
+                if (k > 0 && !ptx::mbar_wait(&empty[s], (k - 1) & 1)) {
+                    set_timeout(P.status);
+                    return;
+                }
+                const int64_t zi = z0 - 1 + q;
+                const bool need_k = KAPPA && q >= 1 && q <= zce;
+                const uint32_t bytes = (uint32_t)(tye + 2) * rowb + (need_k ? (uint32_t)tye * rowb : 0u);
+                T* dst = ring + (size_t)s * P.stage_elems;
+                ptx::mbar_arrive_expect_tx(&full[s], bytes);
+                if (!PERIODIC) {
+                    const T* src = in + (zi + P.rz) * P.plane + (y0 - 1 + P.r) * P.pitch;
+                    ptx::bulk_g2s(dst, src, (uint32_t)(tye + 2) * rowb, &full[s]);
+                } else {
+                    const T* pl = in + (wrapi(zi, P.nz) + P.rz) * P.plane + (int64_t)P.r * P.pitch;
+                    int j = 0;
+                    while (j < tye + 2) {
+                        int64_t row = y0 - 1 + j;
+                        row = ((row % P.ny) + P.ny) % P.ny;
+                        const int run = (int)imin64(tye + 2 - j, P.ny - row);
+                        ptx::bulk_g2s(dst + (size_t)j * P.pitch, pl + row * P.pitch, (uint32_t)run * rowb, &full[s]);
+                        j += run;
+                    }
+                }
+                if (need_k) {
+                    const T* ks = kappa + (zi + P.rz) * P.plane + (y0 + P.r) * P.pitch;
+                    ptx::bulk_g2s(dst + P.u_elems, ks, (uint32_t)tye * rowb, &full[s]);
+                }
+            }
+        }
+        // drain: wait until every issued copy has landed before leaving
+        for (uint32_t d = 0; d < (uint32_t)P.NS && d < gq; ++d) {
+            const uint32_t g = gq - 1 - d;
+            if (!ptx::mbar_wait(&full[g % P.NS], (g / P.NS) & 1)) set_timeout(P.status);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumers
+    // Each thread owns G column tasks per unit: a pair of rows (2 rp, 2 rp + 1)
+    // at one VN-wide x group.  It keeps the two rows of the planes below, at
+    // and above the output plane in registers (z reuse), and the pair shares
+    // its inner y neighbours (y reuse); only the plane above, the pair's outer
+    // y neighbours and the x edges are read from shared memory.
+    const int ct = threadIdx.x;
+    const int NC = CONSUMER_WARPS * 32;
+    const int ngx = (int)((P.nx + VN - 1) / VN);
+    const unsigned FULLM = 0xffffffffu;
+    uint32_t gq = 0;
+    for (int u = blockIdx.x; u < P.units; u += gridDim.x) {
+        const int yt = u % P.nyt, zc = u / P.nyt;
+        const int64_t y0 = (int64_t)yt * P.TY, z0 = (int64_t)zc * P.ZC;
+        const int tye = (int)imin64(P.TY, P.ny - y0);
+        const int zce = (int)imin64(P.ZC, P.nz - z0);
+        const uint32_t base = gq;
+        const int ntasks = ((tye + 1) / 2) * ngx;
+        int trow[G], tgx[G];
+        bool tact[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int t = ct + g * NC;
+            tact[g] = t < ntasks;
+            const int rp = tact[g] ? t / ngx : 0;
+            trow[g] = 2 * rp;
+            tgx[g] = tact[g] ? t - rp * ngx : 0;
+        }
+        auto stage = [&](int q) -> const T* {
+            return ring + (size_t)((base + q) % P.NS) * P.stage_elems + P.xl;
+        };
+        auto wait_q = [&](int q) -> bool {
+            const uint32_t gg = base + q;
+            return ptx::mbar_wait(&full[gg % P.NS], (gg / P.NS) & 1);
+        };
+        auto release = [&](int q) {
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&empty[(base + q) % P.NS]);
+        };
+        T bel[G][2][VN], cen[G][2][VN], abv[G][2][VN];
+        if (!wait_q(0) || !wait_q(1)) {
+            set_timeout(P.status);
+            return;
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int off = (trow[g] + r + 1) * (int)P.pitch + tgx[g] * VN;
+                ldv(stage(0) + off, bel[g][r]);
+                ldv(stage(1) + off, cen[g][r]);
+            }
+        release(0);
+        for (int i = 0; i < zce; ++i) {
+            if (!wait_q(i + 2)) {
+                set_timeout(P.status);
+                return;
+            }
+            const T* sa = stage(i + 2);
+            const T* sc = stage(i + 1);
+            const T* sk = sc + P.u_elems;
+            T* oplane = out + P.origin + (z0 + i) * P.plane + y0 * P.pitch;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int x = tgx[g] * VN;
+                const int rbase = trow[g] * (int)P.pitch + x;  // smem offset of row trow - 1
+                T up[VN], dn[VN], kv[2][VN];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) ldv(sa + rbase + (r + 1) * (int)P.pitch, abv[g][r]);
+                ldv(sc + rbase, up);
+                ldv(sc + rbase + 3 * (int)P.pitch, dn);
+                if constexpr (KAPPA) {
+                    ldv(sk + rbase, kv[0]);
+                    ldv(sk + rbase + (int)P.pitch, kv[1]);
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const T* crow = sc + rbase + (r + 1) * (int)P.pitch - x;  // centre row, x = 0
+                    // x edges from the neighbouring lanes, or shared memory at row/warp ends
+                    T left = __shfl_up_sync(FULLM, cen[g][r][VN - 1], 1);
+                    T right = __shfl_down_sync(FULLM, cen[g][r][0], 1);
+                    if (lane == 0 || tgx[g] == 0) left = (PERIODIC && x == 0) ? crow[P.nx - 1] : crow[x - 1];
+                    if (lane == 31 || tgx[g] == ngx - 1) right = (PERIODIC && x + VN >= P.nx) ? crow[0] : crow[x + VN];
+                    const T* yl = r == 0 ? up : cen[g][0];
+                    const T* yh = r == 0 ? cen[g][1] : dn;
+                    T o[VN];
+#pragma unroll
+                    for (int j = 0; j < VN; ++j) {
+                        const T xm = j == 0 ? left : cen[g][r][j - 1];
+                        T xp = j == VN - 1 ? right : cen[g][r][j + 1];
+                        if (PERIODIC && x + j + 1 == P.nx) xp = crow[0];
+                        o[j] = point<T, KAPPA, SYM>(P, cen[g][r][j], xm, xp, yl[j], yh[j], bel[g][r][j], abv[g][r][j],
+                                                    KAPPA ? kv[r][j] : T(0));
+                    }
+                    if (tact[g] && trow[g] + r < tye) {
+                        T* op = oplane + (int64_t)(trow[g] + r) * P.pitch + x;
+                        if (x + VN <= P.nx) {
+                            stv(op, o);
+                        } else {
+                            for (int j = 0; j < VN && x + j < P.nx; ++j) op[j] = o[j];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int j = 0; j < VN; ++j) {
+                        bel[g][r][j] = cen[g][r][j];
+                        cen[g][r][j] = abv[g][r][j];
+                    }
+            }
+            release(i + 1);
+            if (i == zce - 1) release(i + 2);
+        }
+        gq = base + zce + 2;
+    }
+}
+
+struct Cfg {
+    int TY, ZC, NS, G;
+};
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
+constexpr size_t SMEM_BUDGET = 200 * 1024;
+
+size_t stage_bytes(const Geom& g, int TY, bool kappa)
+{
+    size_t e = (size_t)(TY + 2) * g.pitch + (kappa ? (size_t)TY * g.pitch : 0);
+    e = (e * g.esize + 127) / 128 * 128;
+    return e;
+}
+
+// Tile rows TY (even), z-chunk ZC, ring stages NS, tasks per thread G.
+bool pick_cfg(const Geom& g, bool kappa, Cfg* c)
+{
+    const int VN = 16 / g.esize;
+    const int NC = CONSUMER_WARPS * 32;
+    const int ngx = (int)((g.nx + VN - 1) / VN);
+    int TY = 2 * std::max(1, (NC + ngx - 1) / ngx);  // row pairs x groups ~ one task per thread
+    TY = std::min(TY, 16);
+    TY = (int)std::min<int64_t>(TY, (g.ny + 1) / 2 * 2);
+    const char* env = std::getenv("ST_STAR1_CFG");  // "TY,ZC,NS" for tuning sweeps
+    int eTY = 0, eZC = 0, eNS = 0;
+    const bool use_env = env && std::sscanf(env, "%d,%d,%d", &eTY, &eZC, &eNS) == 3 && eTY >= 2 && eTY % 2 == 0 &&
+                         eZC > 0 && eNS >= 4;
+    if (use_env) TY = eTY;
+    while (TY > 2 && stage_bytes(g, TY, kappa) * 4 > SMEM_BUDGET) TY -= 2;
+    if (stage_bytes(g, TY, kappa) * 4 > SMEM_BUDGET) return false;
+    const int tasks = (TY / 2) * ngx;
+    const int G = (tasks + NC - 1) / NC;
+    if (G > 2) return false;
+    int NS = (int)std::min<size_t>(8, SMEM_BUDGET / stage_bytes(g, TY, kappa));
+    const int nyt = (int)((g.ny + TY - 1) / TY);
+    // z-chunk: about 7 units per CTA, at least 8 planes
+    const int64_t want_units = 7LL * sm_count();
+    int64_t nzc = std::max<int64_t>(1, want_units / nyt);
+    int ZC = (int)std::max<int64_t>(8, (g.nz + nzc - 1) / nzc);
+    ZC = (int)std::min<int64_t>(ZC, g.nz);
+    if (use_env) {
+        ZC = (int)std::min<int64_t>(eZC, g.nz);
+        NS = std::min(eNS, (int)(SMEM_BUDGET / stage_bytes(g, TY, kappa)));
+    }
+    *c = Cfg{TY, ZC, NS, G};
+    return true;
+}
+
+template <typename T, bool KAPPA, bool SYM, bool PERIODIC>
+cudaError_t launch_t(const Family& f, const SweepArgs& a, cudaStream_t s)
+{
+    const Geom& g = f.g;
+    Cfg c;
+    if (!pick_cfg(g, KAPPA, &c)) return cudaErrorNotSupported;
+    Star1Params P;
+    std::memset(&P, 0, sizeof(P));
+    P.nz = g.nz;
+    P.ny = g.ny;
+    P.nx = g.nx;
+    P.pitch = g.pitch;
+    P.plane = g.plane;
+    P.origin = g.origin;
+    P.rz = g.rz;
+    P.r = g.r;
+    P.xl = (int)g.xl;
+    P.TY = c.TY;
+    P.ZC = c.ZC;
+    P.NS = c.NS;
+    P.nyt = (int)((g.ny + c.TY - 1) / c.TY);
+    P.nzc = (int)((g.nz + c.ZC - 1) / c.ZC);
+    P.units = P.nyt * P.nzc;
+    P.u_elems = (uint32_t)((c.TY + 2) * g.pitch);
+    P.stage_elems = (uint32_t)(stage_bytes(g, c.TY, KAPPA) / sizeof(T));
+    const StarCoef& k = f.sc;
+    P.wc = k.c_a;
+    P.bc = k.c_b;
+    P.wzm = k.a[0][0][0];
+    P.wzp = k.a[0][1][0];
+    P.wym = k.a[1][0][0];
+    P.wyp = k.a[1][1][0];
+    P.wxm = k.a[2][0][0];
+    P.wxp = k.a[2][1][0];
+    P.bzm = k.b[0][0][0];
+    P.bzp = k.b[0][1][0];
+    P.bym = k.b[1][0][0];
+    P.byp = k.b[1][1][0];
+    P.bxm = k.b[2][0][0];
+    P.bxp = k.b[2][1][0];
+    P.status = a.status;
+    const size_t smem = (size_t)c.NS * P.stage_elems * sizeof(T) + 2 * sizeof(uint64_t) * c.NS;
+    static bool attr_set[2] = {false, false};
+    auto fn = c.G == 1 ? k_star1<T, KAPPA, SYM, PERIODIC, 1> : k_star1<T, KAPPA, SYM, PERIODIC, 2>;
+    if (!attr_set[c.G - 1]) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set[c.G - 1] = true;
+    }
+    const int grid = (int)std::min<int64_t>(P.units, sm_count());
+    fn<<<grid, THREADS, smem, s>>>((const T*)a.in, (T*)a.out, (const T*)a.kappa, P);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool star3d_supports(const FamilyDesc& d, int* variant, const char** name)
+{
+    if (d.g.ndim != 3 || d.levels != 1 || !d.star) return false;
+    for (int k = 0; k < d.npts; ++k)
+        for (int i = 0; i < 3; ++i)
+            if (d.off[3 * k + i] > 1 || d.off[3 * k + i] < -1) return false;
+    Cfg c;
+    if (!pick_cfg(d.g, d.has_beta, &c)) return false;
+    *variant = 1;
+    *name = d.has_beta ? "star3d_r1_bulk_kappa" : "star3d_r1_bulk";
+    return true;
+}
+
+cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s)
+{
+    const StarCoef& k = f.sc;
+    const bool sym = k.a[0][0][0] == k.a[0][1][0] && k.a[0][0][0] == k.a[1][0][0] && k.a[0][0][0] == k.a[1][1][0] &&
+                     k.a[0][0][0] == k.a[2][0][0] && k.a[0][0][0] == k.a[2][1][0] && k.b[0][0][0] == k.b[0][1][0] &&
+                     k.b[0][0][0] == k.b[1][0][0] && k.b[0][0][0] == k.b[1][1][0] && k.b[0][0][0] == k.b[2][0][0] &&
+                     k.b[0][0][0] == k.b[2][1][0];
+    const bool dbl = f.g.esize == 8;
+#define ST_DISPATCH(T, KA)                                                                                \
+    (sym ? (f.periodic ? launch_t<T, KA, true, true>(f, a, s) : launch_t<T, KA, true, false>(f, a, s))  \
+         : (f.periodic ? launch_t<T, KA, false, true>(f, a, s) : launch_t<T, KA, false, false>(f, a, s)))
+    if (dbl) return f.has_beta ? ST_DISPATCH(double, true) : ST_DISPATCH(double, false);
+    return f.has_beta ? ST_DISPATCH(float, true) : ST_DISPATCH(float, false);
+#undef ST_DISPATCH
+}
+
+cudaError_t launch_star3d_adjoint(const Family&, const AdjointArgs&, cudaStream_t) { return cudaErrorNotSupported; }
+
+}  // namespace st

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from gpu_helpers import rel_err, require_cuda, torch
-from paper_2512_19851_gb300 import inputs
+from paper_2512_19851_gb300 import abi, inputs
 from paper_2512_19851_gb300.grid import Batch, Grid
 
 pytestmark = pytest.mark.gpu
@@ -91,4 +91,36 @@ def test_full_batch_sampled_grids():
         s0 = float(np.sum(b.fields[i]))
         s1 = float(bt.current(i).double().sum())
         assert abs(s1 - s0) <= 5e-5 * abs(s0), i
+    bt.close()
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    """Failure detection without a GPU fault: the persistent kernel's grid
+    barrier is made to wait for one CTA more than launched; its bounded wait
+    (50 ms) runs out, the status word reports ST_ERR_DEVICE_TIMEOUT, and the
+    same handle then steps normally (one step was done before the barrier)."""
+    b = inputs.batch2d(ngrids=6, lo=16, hi=120)
+    bt = Batch(b.shapes, inputs.OFFSETS_BOX9, b.weights, periodic=True, dtype=torch.float32)
+    bt.set_fields(b.fields)
+    abi.stencil_batch_selftest_barrier(bt.h, 50_000_000)
+    with pytest.raises(abi.StencilError) as e:
+        bt.sync()
+    assert e.value.code == abi.ST_ERR_DEVICE_TIMEOUT
+    bt.step(4)
+    bt.sync()
+    for i in range(6):
+        ref = oracle.sweep_const(b.fields[i], inputs.OFFSETS_BOX9, b.weights[i], True, 0.0, 5)
+        assert rel_err(bt.current(i).double().cpu().numpy(), ref) <= TOL32
+    bt.close()
+
+
+def test_dirichlet_batch_matches_oracle():
+    b = inputs.batch2d(ngrids=8, lo=10, hi=150)
+    bt = Batch(b.shapes, inputs.OFFSETS_BOX9, b.weights, periodic=False, bc_value=0.25, dtype=torch.float32)
+    bt.set_fields(b.fields)
+    bt.step(13)
+    bt.sync()
+    for i in range(8):
+        ref = oracle.sweep_const(b.fields[i], inputs.OFFSETS_BOX9, b.weights[i], False, 0.25, 13)
+        assert rel_err(bt.current(i).double().cpu().numpy(), ref) <= TOL32
     bt.close()

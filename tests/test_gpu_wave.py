@@ -59,6 +59,31 @@ def test_wave_matches_oracle(n, steps, dtype):
     assert rel_err(prev, ref_prev) <= tol, kern
 
 
+@pytest.mark.parametrize("periodic", [False, True])
+def test_wave_ragged_shapes(periodic):
+    """Non-cubic interior with x not a multiple of the vector width, a
+    layered per-cell factor and a source off the centre."""
+    shape = (21, 30, 45)
+    rng = np.random.default_rng(3)
+    m = np.repeat(rng.uniform(0.02, 0.15, size=shape[0]), shape[1] * shape[2]).reshape(shape)
+    amps = rng.standard_normal(40)
+    src = (7, 11, 44)
+    u1, u0 = rng.standard_normal(shape), rng.standard_normal(shape)
+    ref, ref_prev = oracle.wave25(u1, u0, m, a8(), src, amps, periodic, 0.0, 40)
+    offs, alpha, beta = stencils.wave25()
+    for dtype, tol in ((torch.float64, TOL64), (torch.float32, TOL32_WAVE)):
+        g = Grid(shape, offs, alpha, beta, periodic=periodic, dtype=dtype, time_levels=2)
+        g.set_coeff(m)
+        g.set_levels(u1, u0)
+        g.set_source(src, amps)
+        g.step(17)
+        g.step(23)
+        g.sync()
+        assert rel_err(g.current().double().cpu().numpy(), ref) <= tol, g.kernel
+        assert rel_err(g.previous().double().cpu().numpy(), ref_prev) <= tol, g.kernel
+        g.close()
+
+
 def test_wave_generic_and_chunked_agree():
     n, steps = 36, 41
     w = inputs.wave3d(n=n, steps=steps)
