@@ -522,12 +522,17 @@ st_status stencil_residual(st_grid_t g, const void* u, const void* target, void*
 
 static size_t state_bytes(st_grid_t g) { return (size_t)((g->g.elems * g->g.esize + 255) / 256 * 256); }
 
+// FP32 grids on the fused adjoint accumulate the coefficient gradient in a
+// float-float scratch (two float fields) kept at the end of the workspace.
+static size_t ff_field_bytes(st_grid_t g) { return (size_t)((g->g.elems * 4 + 255) / 256 * 256); }
+static bool uses_ff(st_grid_t g) { return g->g.esize == 4 && g->has_beta && star3d_adjoint_fuse(g->fam) > 0; }
+
 st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* bytes)
 {
     if (!g || !bytes) return fail(ST_ERR_ARG, "stencil_adjoint_workspace: NULL argument");
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_adjoint_workspace: nsteps >= 0, ckpt_every >= 1");
     const int64_t nck = (nsteps + m - 1) / m;
-    *bytes = state_bytes(g) * (size_t)(nck + (m - 1));
+    *bytes = state_bytes(g) * (size_t)(nck + (m - 1)) + (uses_ff(g) ? 2 * ff_field_bytes(g) : 0);
     return ST_OK;
 }
 
@@ -586,6 +591,15 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     };
     if (g->bc == ST_DIRICHLET)
         for (int j = 1; j < m; ++j) ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, state(0, j), g->g, g->bc_value, s));
+    const int fuse = star3d_adjoint_fuse(g->fam);  // steps per optimised transpose launch (0: generic)
+    float* ghi = nullptr;
+    float* glo = nullptr;
+    const bool ff = grad && uses_ff(g);
+    if (ff) {
+        ghi = reinterpret_cast<float*>(base + (size_t)(nck + m - 1) * sb);
+        glo = reinterpret_cast<float*>(reinterpret_cast<char*>(ghi) + ff_field_bytes(g));
+        ST_CUDA_TRY(cudaMemsetAsync(ghi, 0, 2 * ff_field_bytes(g), s));
+    }
     void* lin = lambda;
     void* lout = lambda_tmp;
     for (int64_t c = nck - 1; c >= 0; --c) {
@@ -595,17 +609,26 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
             SweepArgs a = sweep_args(g, state(c, j - 1), state(c, j), t0 + j - 1);
             ST_CUDA_TRY(launch_family(g->fam, a, s));
         }
-        for (int j = L - 1; j >= 0; --j) {
+        int j = L - 1;
+        while (j >= 0) {
+            const int k = (fuse >= 2 && j >= 1) ? 2 : 1;
             AdjointArgs a{};
             a.u = state(c, j);
+            a.u2 = k == 2 ? state(c, j - 1) : nullptr;
             a.lam_in = lin;
             a.lam_out = lout;
             a.kappa = g->has_beta ? g->buf[ST_SLOT_COEFF] : nullptr;
-            a.gk = grad;
+            a.gk = ff ? nullptr : grad;
+            a.ghi = ghi;
+            a.glo = glo;
+            a.steps = k;
+            a.status = g->d_status;
             ST_CUDA_TRY(launch_family_adjoint(g->fam, a, s));
             std::swap(lin, lout);
+            j -= k;
         }
     }
+    if (ff) ST_CUDA_TRY(launch_fold_ff(ghi, glo, grad, g->g, s));
     if (lin != lambda)
         ST_CUDA_TRY(cudaMemcpyAsync(lambda, lin, (size_t)g->g.elems * g->g.esize, cudaMemcpyDeviceToDevice, s));
     return ST_OK;

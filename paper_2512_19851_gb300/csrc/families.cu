@@ -100,10 +100,8 @@ cudaError_t launch_family(const Family& f, const SweepArgs& a, cudaStream_t s)
 
 cudaError_t launch_family_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s)
 {
-    if (f.kind == FAM_STAR3D) {
-        cudaError_t e = launch_star3d_adjoint(f, a, s);
-        if (e != cudaErrorNotSupported) return e;
-    }
+    if (f.kind == FAM_STAR3D && star3d_adjoint_fuse(f) >= a.steps) return launch_star3d_adjoint(f, a, s);
+    if (a.steps != 1) return cudaErrorInvalidValue;  // callers fuse only what the family supports
     return launch_generic_adjoint(f.g.esize, a.u, a.lam_in, a.lam_out, a.kappa, a.gk, f.gp, s);
 }
 

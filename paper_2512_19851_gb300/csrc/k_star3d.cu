@@ -239,7 +239,7 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
         };
         auto wait_q = [&](int q) -> bool {
             const uint32_t gg = base + q;
-            return ptx::mbar_wait(&full[gg % P.NS], (gg / P.NS) & 1);
+            return ptx::mbar_wait_warp(&full[gg % P.NS], (gg / P.NS) & 1);
         };
         auto release = [&](int q) {
             __syncwarp();
@@ -467,6 +467,5 @@ cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s)
 #undef ST_DISPATCH
 }
 
-cudaError_t launch_star3d_adjoint(const Family&, const AdjointArgs&, cudaStream_t) { return cudaErrorNotSupported; }
 
 }  // namespace st

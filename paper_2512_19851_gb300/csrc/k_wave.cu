@@ -142,7 +142,7 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
         };
         auto wait_plane = [&](int qq) -> bool {
             const uint32_t g = base + qq;
-            return ptx::mbar_wait(&full[g % P.NS], (g / P.NS) & 1);
+            return ptx::mbar_wait_warp(&full[g % P.NS], (g / P.NS) & 1);
         };
         auto release = [&](int qq) {
             __syncwarp();
@@ -414,10 +414,7 @@ cudaError_t launch_wave(const Family& f, const SweepArgs& a, cudaStream_t s)
         P.sz = rel / g.plane;
         rel -= P.sz * g.plane;
         P.sy = rel / g.pitch;
-        P.sx = rel - P.sy * g.pitch;
-        P.sz -= g.rz;
-        P.sy -= g.r;
-        P.sx -= g.xl;
+        P.sx = rel - P.sy * g.pitch;  // rel is measured from the interior origin
         P.src_amp = a.src_amp;
         P.step = a.step;
     }

@@ -68,6 +68,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
     }
 }
 
+// Warp-uniform form: every lane of the warp calls it; it returns false on all
+// lanes if any lane's wait ran out, so a warp leaves a pipeline together and
+// no lane is left behind at a later warp-level synchronisation.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity)
+{
+    const bool ok = mbar_wait(bar, parity);
+    return __all_sync(0xffffffffu, ok);
+}
+
 // 1D bulk copy global -> shared completing on an mbarrier (transaction bytes).
 // dst, src 16-byte aligned; bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
