@@ -108,6 +108,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def aggregate_ms(ms: float, pg, device=None) -> float:
+    """Job time of a replicas-only run: the slowest rank's time (all-reduce
+    MAX over the process group; no data-path collective exists)."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(points_per_rank_step: float, steps: int, world: int, ms_total: float) -> float:
+    """Whole-job GLUP/s: the updates of all ranks divided by the job time."""
+    return world * points_per_rank_step * steps / (ms_total * 1e-3) / 1e9
+
+
 def source_sha(*names):
     h = hashlib.sha256()
     for n in names:
@@ -189,13 +205,10 @@ def run_ours(args):
     ms_total = t0.elapsed_time(t1)
     sweep_ms = [a.elapsed_time(b) for a, b, _ in ev]
     red_ms = [b.elapsed_time(c) for _, b, c in ev]
-    if pg:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = aggregate_ms(ms_total, pg, dev)
     ms_step = ms_total / args.steps
     pts = N3 ** 3 * SWEEPS
-    value = ws * pts * args.steps / (ms_total * 1e-3) / 1e9
+    value = job_value(pts, args.steps, ws, ms_total)
     per_sweep_s = statistics.mean(sweep_ms) * 1e-3 / SWEEPS
     achieved = 8.0 * N3 ** 3 / per_sweep_s / 1e9
     kname = g.kernel
@@ -218,12 +231,8 @@ def run_ours(args):
         abi.stencil_run_host(g.h, SWEEPS, src.data_ptr(), dst.data_ptr(), stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e_ms = e0.elapsed_time(e1) / e_steps
-    if pg:
-        t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e_ms = float(t.item())
-    e2e = {"value": ws * pts / (e_ms * 1e-3) / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": int(src.numel() * 4),
+    e_ms = aggregate_ms(e0.elapsed_time(e1) / e_steps, pg, dev)
+    e2e = {"value": job_value(pts, 1, ws, e_ms), "unit": "GLUP/s", "h2d_bytes_per_step": int(src.numel() * 4),
            "d2h_bytes_per_step": int(dst.numel() * 4), "ms_per_step": e_ms,
            "api": "stencil_run_host (pinned host in, 100 sweeps, pinned host out)"}
     g.close()

@@ -229,13 +229,17 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
                         S[j - 1][3] += yl.w + yh.w;
                     }
                     // x window: 4 left, the group, 4 right
+                    // vector loads only at multiples of 4 from the row start (16-byte
+                    // aligned); a periodic window that wraps is gathered element-wise
                     float4 L, R;
                     if (PERIODIC && x == 0)
-                        L = *reinterpret_cast<const float4*>(rc + P.nx - 4);
+                        L = make_float4(rc[wrapw(x - 4, P.nx)], rc[wrapw(x - 3, P.nx)], rc[wrapw(x - 2, P.nx)],
+                                        rc[wrapw(x - 1, P.nx)]);
                     else
                         L = *reinterpret_cast<const float4*>(rc + x - 4);
-                    if (PERIODIC && x + 4 == P.nx)
-                        R = *reinterpret_cast<const float4*>(rc);
+                    if (PERIODIC && x + 8 > P.nx)
+                        R = make_float4(rc[wrapw(x + 4, P.nx)], rc[wrapw(x + 5, P.nx)], rc[wrapw(x + 6, P.nx)],
+                                        rc[wrapw(x + 7, P.nx)]);
                     else
                         R = *reinterpret_cast<const float4*>(rc + x + 4);
                     const float w[12] = {L.x, L.y, L.z, L.w, c[0], c[1], c[2], c[3], R.x, R.y, R.z, R.w};

@@ -1,0 +1,114 @@
+"""Planted mistakes in the CPU oracle must be caught by its pins.
+
+Each mutant is a copy of oracle/stencil_oracle.c with one plausible slip (a
+dropped term, a wrong sign, a wrong index or axis, a transposed operand),
+compiled to a temporary library and swapped in for the double-precision
+oracle while a few pins from test_oracle_pins.py run.  At least one of them
+must fail.  Nothing here touches a GPU.
+"""
+import contextlib
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "stencil_oracle.c")
+
+MUTANTS = {
+    "sweep drops the last neighbour": (
+        "for (int k = 0; k < npts; ++k) {\n                        REAL v",
+        "for (int k = 0; k < npts - 1; ++k) {\n                        REAL v",
+        ["matrix", "golden", "decay"]),
+    "Dirichlet ghost ignores bc_value": (
+        "        return bc_value;", "        return (REAL)0;", ["matrix", "golden"]),
+    "sweep mixes up the z and x offsets": (
+        "orc_read(src, nz, ny, nx, z + off[3 * k], y + off[3 * k + 1],\n                                          x + off[3 * k + 2]",
+        "orc_read(src, nz, ny, nx, z + off[3 * k + 2], y + off[3 * k + 1],\n                                          x + off[3 * k]",
+        ["matrix"]),
+    "periodic wrap off by one": (
+        "    while (i < 0) i += n;", "    while (i < 0) i += n - 1;", ["matrix", "fourier", "conserve"]),
+    "variable diffusion centre weight 1 - 5 kappa": (
+        "dst[p] = ((REAL)1 - (REAL)6 * k) * src[p] + k * nb;",
+        "dst[p] = ((REAL)1 - (REAL)5 * k) * src[p] + k * nb;", ["varmatrix"]),
+    "variable diffusion drops the z+1 neighbour": (
+        "nb = nb + orc_read(src, nz, ny, nx, z + 1, y, x, periodic, bc);\n                    REAL k",
+        "REAL k", ["varmatrix"]),
+    "adjoint uses the receiver's kappa (transposed operand)": (
+        "lout[q] = lout[q] + k * lp;", "lout[q] = lout[q] + kappa[q] * lp;", ["transpose", "fd"]),
+    "gradient term has the wrong sign": (
+        "gk[p] = gk[p] + lp * (nb - (REAL)6 * ut[p]);", "gk[p] = gk[p] + lp * (nb + (REAL)6 * ut[p]);", ["fd"]),
+    "adjoint centre weight 1 - 6 kappa dropped to 1": (
+        "lout[p] = lout[p] + ((REAL)1 - (REAL)6 * k) * lp;", "lout[p] = lout[p] + lp;", ["transpose", "fd"]),
+    "leapfrog drops u^{n-1}": (
+        "REAL v = (REAL)2 * c - old[p] + m[p] * lap;", "REAL v = (REAL)2 * c + m[p] * lap;",
+        ["planewave", "energy", "shift"]),
+    "wave star reads z - j + 1": (
+        "orc_read(cur, nz, ny, nx, z - j, y, x, periodic, bc));",
+        "orc_read(cur, nz, ny, nx, z - j + 1, y, x, periodic, bc));", ["planewave", "shift"]),
+    "wave source added to the wrong step": (
+        "if (p == src) v = v + (REAL)s[st];", "if (p == src) v = v + (REAL)s[st + 1];", ["source"]),
+    "reduction sums |d| instead of d^2": (
+        "q = q + d * d;", "q = q + (d < 0 ? -d : d);", ["reduce"]),
+}
+
+PINS = {
+    "matrix": lambda: [pins.test_sweep_vs_assembled_matrix(s, p) for s in [(6, 7), (4, 5, 3)] for p in (False, True)],
+    "golden": pins.test_example1_golden_exact,
+    "decay": lambda: pins.test_dirichlet_sine_mode_decay((9, 13), (2, 3), 0.2, 17),
+    "fourier": pins.test_periodic_2d_fourier_decay,
+    "conserve": pins.test_periodic_sum_conserved,
+    "varmatrix": lambda: [pins.test_varcoef7_vs_assembled_matrix(p) for p in (False, True)],
+    "transpose": lambda: [pins.test_adjoint_equals_matrix_transpose(p) for p in (False, True)],
+    "fd": pins.test_gradient_central_differences,
+    "planewave": pins.test_wave_plane_wave_recurrence,
+    "energy": pins.test_wave_energy_conserved,
+    "shift": pins.test_wave_matches_shift_formula_dirichlet,
+    "source": pins.test_wave_source_injection,
+    "reduce": pins.test_reduce_matches_fsum,
+}
+
+
+@contextlib.contextmanager
+def mutant_oracle(old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "mut.c")
+        so = os.path.join(d, "mut.so")
+        open(c, "w").write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-DREAL=double", "-DORC_SUFFIX=_f64", c, "-o", so])
+        oracle.build()
+        saved = oracle._loaded.get(np.float64)
+        oracle._loaded[np.float64] = ctypes.CDLL(so)
+        try:
+            yield
+        finally:
+            if saved is None:
+                oracle._loaded.pop(np.float64, None)
+            else:
+                oracle._loaded[np.float64] = saved
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name):
+    old, new, which = MUTANTS[name]
+    caught = []
+    with mutant_oracle(old, new):
+        for key in which:
+            try:
+                PINS[key]()
+            except Exception as e:  # an assertion, or a numerical blow-up
+                caught.append((key, type(e).__name__))
+    assert caught, f"no pin caught the planted mistake: {name}"
+
+
+def test_unmutated_oracle_passes_the_same_pins():
+    for key, fn in PINS.items():
+        fn()
