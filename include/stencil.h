@@ -203,6 +203,32 @@ st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_
                          void* stream);
 
 /*
+ * Allocation-free form of stencil_reduce (the paper has no counterpart: its
+ * runtime allocates freely).  For callers that cannot allocate device
+ * memory at call time: an application whose device memory is entirely owned
+ * by another allocator (a framework's caching pool that has reserved the
+ * GPU), a latency-critical loop that cannot afford cudaMalloc's implicit
+ * device synchronisation, or code that must not fail with out-of-memory
+ * after start-up.  stencil_reduce takes its per-block partial sums from
+ * handle scratch that its first call allocates; this entry point takes them
+ * from a static device array instead and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   Same arguments and results as stencil_reduce (a, b: field-layout buffers
+ *   of the grid's dtype, b may be NULL; dev_out: 3 doubles in device memory).
+ *   Limit: at most 2^28 = 268435456 interior points (one partial per 65536
+ *   points, 4096 partials = 96 KB held by every GPU that loads the library
+ *   until the process exits); larger grids get ST_ERR_ARG and a message.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   All calls share the one array: every call overwrites the partials it
+ *   uses before reading them, so nothing needs clearing, but two calls whose
+ *   work overlaps on the GPU (different streams, no ordering) race on it.
+ *   Results agree with stencil_reduce up to summation order.
+ */
+st_status stencil_reduce_noalloc(st_grid_t g, const void* a, const void* b, double* dev_out, void* stream);
+
+/*
  * Loss residual: lambda = u - target on the interior (lambda's ghosts set to
  * 0) and dev_loss[0] = 0.5 * sum (u - target)^2 in double precision.
  */

@@ -60,6 +60,7 @@ SIGNATURES = {
     "stencil_sync": (_I, [_VP]),
     "stencil_reduce": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "stencil_residual": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "stencil_reduce_noalloc": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "stencil_adjoint_workspace": (_I, [_VP, _I, _I, _PSZ]),
     "stencil_step_ckpt": (_I, [_VP, _I, _I, _VP, _VP]),
     "stencil_adjoint": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP]),
@@ -207,6 +208,14 @@ def stencil_sync(h) -> None:
 def stencil_reduce(h, a_ptr, b_ptr, out_ptr, stream=None) -> None:
     _check(lib().stencil_reduce(h, ctypes.c_void_p(int(a_ptr)), ctypes.c_void_p(int(b_ptr) if b_ptr else None),
                                 ctypes.c_void_p(int(out_ptr)), ctypes.c_void_p(_stream(stream))), "stencil_reduce")
+
+
+def stencil_reduce_noalloc(h, a_ptr, b_ptr, out_ptr, stream=None) -> None:
+    """stencil_reduce without device allocation (static scratch, <= 2^28 points)."""
+    _check(lib().stencil_reduce_noalloc(h, ctypes.c_void_p(int(a_ptr)),
+                                        ctypes.c_void_p(int(b_ptr) if b_ptr else None),
+                                        ctypes.c_void_p(int(out_ptr)), ctypes.c_void_p(_stream(stream))),
+           "stencil_reduce_noalloc")
 
 
 def stencil_residual(h, u_ptr, target_ptr, lam_ptr, loss_ptr, stream=None) -> None:

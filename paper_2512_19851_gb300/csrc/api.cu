@@ -878,3 +878,9 @@ st_status stencil_batch_sync(st_batch_t b)
 }
 
 }  // extern "C"
+
+namespace st {
+// Accessors for translation units that do not see st_grid_s.
+const Geom* grid_geom(st_grid_t g) { return &g->g; }
+void grid_note_stream(st_grid_t g, cudaStream_t s) { g->last = s; }
+}  // namespace st
