@@ -37,6 +37,10 @@ sys.path.insert(0, ROOT)
 
 N3 = 512
 SWEEPS = 100
+# FP64 issue rate of the GB300 (nominal 1.25 TFLOP/s FP64, an FMA counting two
+# FLOPs): the bound of the FP64 sweeps, which need more DP instructions per
+# point than their bytes allow at HBM speed.
+FP64_INSTR_PER_S = 1.25e12 / 2
 WORKLOAD = "heat3d 7-point periodic 512^3, 100 sweeps per step, FP32 + FP64 reduction"
 
 
@@ -301,18 +305,22 @@ def extra_configs(dev, hbm_peak):
     del h
     t = _time(lambda: abi.stencil_step(g.h, SWEEPS, s), 2, s)
     per = t / SWEEPS
-    out["heat3d_f64"] = {"glups": N3 ** 3 * SWEEPS / t / 1e9, "us_per_sweep": per * 1e6,
+    glups = N3 ** 3 * SWEEPS / t / 1e9
+    out["heat3d_f64"] = {"glups": glups, "us_per_sweep": per * 1e6,
                          "hbm_gbs": 16 * N3 ** 3 / per / 1e9, "hbm_frac": 16 * N3 ** 3 / per / 1e9 / hbm_peak,
-                         "kernel": g.kernel}
+                         "bound": "alu", "alu_peak_glups": FP64_INSTR_PER_S / 7 / 1e9,
+                         "alu_frac": glups / (FP64_INSTR_PER_S / 7 / 1e9), "kernel": g.kernel}
     g.close()
     torch.cuda.empty_cache()
     # heat2d FP64 256^2 Dirichlet, 100 steps
     u0 = inputs.heat2d()
     g = Grid((256, 256), inputs.OFFSETS_5PT, [0.2] * 5, dtype=torch.float64, device=dev)
     g.set_field(u0)
+    cfg = g.tune(100)
     t = _time(lambda: abi.stencil_step(g.h, 100, s), 20, s)
     out["heat2d_f64"] = {"glups": 256 * 256 * 100 / t / 1e9, "us_per_step": t / 100 * 1e6,
-                         "us_per_run": t * 1e6, "kernel": g.kernel}
+                         "us_per_run": t * 1e6, "kernel": g.kernel, "config": list(cfg),
+                         "alu_bound_us_per_step": 256 * 256 * 5 / FP64_INSTR_PER_S * 1e6}
     g.close()
     # wave, radius-4 leapfrog FP32, 1000 steps
     wv = inputs.wave3d(n=N3, steps=1000)
@@ -459,8 +467,16 @@ def run_profile(case: str, launches: int = 3):
         offs, w, _ = stencils.heat3d()
         g = Grid(shape, offs, w, periodic=True, dtype=dt)
         g.set_field(inputs.heat3d(shape=shape).u0)
+        red = torch.empty(3, dtype=torch.float64, device="cuda")
         for _ in range(2 + launches):
             abi.stencil_step(g.h, 1, s)
+            abi.stencil_reduce(g.h, g.bufs[g.current_slot()].data_ptr(), 0, red.data_ptr(), s)
+    elif case == "heat2d":
+        offs, w, _ = stencils.heat2d()
+        g = Grid((256, 256), offs, w, dtype=torch.float64)
+        g.set_field(inputs.heat2d())
+        for _ in range(2 + launches):
+            abi.stencil_step(g.h, 100, s)
     elif case == "wave":
         n = 384
         wv = inputs.wave3d(n=n, steps=8)

@@ -179,6 +179,20 @@ st_status stencil_get_step_index(st_grid_t g, int64_t* t);
 st_status stencil_step(st_grid_t g, int nsteps, void* stream);
 
 /*
+ * Autotune the launch configuration of this grid for nsteps-step calls (2D
+ * grids on the persistent tile kernel: tile shape, threads per block, steps
+ * per shared-memory pass; other families have nothing to tune and return
+ * ST_OK).  Times the candidates on the bound data and restores it afterwards;
+ * synchronises `stream`.  With temporal blocking a call may leave the newest
+ * level in either slot: stencil_current() tells which.
+ */
+st_status stencil_tune(st_grid_t g, int nsteps, void* stream);
+
+/* The configuration in use (cfg[0] tile x, cfg[1] tile y, cfg[2] threads,
+ * cfg[3] steps per pass); zeros for families without one. */
+st_status stencil_tune_config(st_grid_t g, int* cfg);
+
+/*
  * End-to-end form of stencil_step for callers whose data is on the host:
  * copies host_u0 (dense interior, C order, the grid's dtype) into the current
  * level, runs nsteps, copies the newest level's interior to host_uT.  Both

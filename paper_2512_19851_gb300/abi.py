@@ -56,6 +56,8 @@ SIGNATURES = {
     "stencil_set_step_index": (_I, [_VP, _I64]),
     "stencil_get_step_index": (_I, [_VP, _PI64]),
     "stencil_step": (_I, [_VP, _I, _VP]),
+    "stencil_tune": (_I, [_VP, _I, _VP]),
+    "stencil_tune_config": (_I, [_VP, _PI]),
     "stencil_run_host": (_I, [_VP, _I, _VP, _VP, _VP]),
     "stencil_sync": (_I, [_VP]),
     "stencil_reduce": (_I, [_VP, _VP, _VP, _VP, _VP]),
@@ -193,6 +195,16 @@ def stencil_get_step_index(h) -> int:
 
 def stencil_step(h, nsteps, stream=None) -> None:
     _check(lib().stencil_step(h, int(nsteps), ctypes.c_void_p(_stream(stream))), "stencil_step")
+
+
+def stencil_tune(h, nsteps, stream=None) -> None:
+    _check(lib().stencil_tune(h, int(nsteps), ctypes.c_void_p(_stream(stream))), "stencil_tune")
+
+
+def stencil_tune_config(h):
+    cfg = (ctypes.c_int * 4)()
+    _check(lib().stencil_tune_config(h, cfg), "stencil_tune_config")
+    return tuple(cfg)
 
 
 def stencil_run_host(h, nsteps, host_u0_ptr, host_uT_ptr, stream=None) -> None:

@@ -94,6 +94,8 @@ struct st_grid_s {
     cudaStream_t cap = nullptr;
     cudaStream_t last = nullptr;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    BatchPlan* plan = nullptr;  // 2D grids on the persistent tile kernel (a batch of one)
+    bool plan_bound = false;
 };
 
 static void drop_graphs(st_grid_t g)
@@ -157,6 +159,8 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
         d3[3 - ndim + i] = dims[i];
     }
     if (d3[0] > 65535) return fail(ST_ERR_ARG, "stencil_create: nz > 65535");
+    if ((d3[0] + 2 * ST_MAX_RADIUS) * (d3[1] + 2 * ST_MAX_RADIUS) >= ((int64_t)1 << 32))
+        return fail(ST_ERR_ARG, "stencil_create: nz * ny beyond 2^32 rows");
     std::vector<int32_t> off(3 * npts, 0);
     int derived = 0;
     for (int k = 0; k < npts; ++k) {
@@ -208,6 +212,26 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     d.star = is_star(g->off, npts, ndim);
     d.force_generic = (flags & ST_FLAG_GENERIC) != 0;
     g->fam = select_family(d);
+    if (g->fam.kind == FAM_2D_TILE) {
+        std::vector<int32_t> off2(2 * npts);
+        for (int k = 0; k < npts; ++k) {
+            off2[2 * k] = g->off[3 * k + 1];
+            off2[2 * k + 1] = g->off[3 * k + 2];
+        }
+        g->plan = new (std::nothrow) BatchPlan(make_batch_plan(std::vector<Geom>{g->g}, npts, off2.data(),
+                                                               g->alpha.data(), bc == ST_PERIODIC, dtype, false));
+        if (!g->plan) {
+            delete g;
+            return fail(ST_ERR_OOM, "stencil_create: out of host memory");
+        }
+        g->plan->bc = bc_value;
+        // one grid: small tiles so that every SM gets work; FP64 is bound by
+        // the FP64 pipe, so no redundant halo work by default (k = 1)
+        g->plan->cfg[0] = 32;
+        g->plan->cfg[1] = 8;
+        g->plan->cfg[2] = 128;
+        g->plan->cfg[3] = dtype == ST_F64 ? 1 : 4;
+    }
     *out = g;
     return ST_OK;
 }
@@ -220,6 +244,10 @@ st_status stencil_destroy(st_grid_t g)
     if (g->d_status) cudaFree(g->d_status);
     if (g->d_partials) cudaFree(g->d_partials);
     if (g->d_src) cudaFree(g->d_src);
+    if (g->plan) {
+        free_batch_plan(*g->plan);
+        delete g->plan;
+    }
     delete g;
     return ST_OK;
 }
@@ -284,6 +312,16 @@ st_status stencil_bind(st_grid_t g, int slot, void* ptr)
     g->stale[slot] = true;
     if (slot == ST_SLOT_A) g->cur = ST_SLOT_A;
     drop_graphs(g);
+    if (g->plan && g->buf[ST_SLOT_A] && g->buf[ST_SLOT_B]) {
+        void* a = g->buf[ST_SLOT_A];
+        void* b = g->buf[ST_SLOT_B];
+        rc = bind_batch_plan(*g->plan, std::vector<Geom>{g->g}, &a, &b, g->d_status);
+        if (rc != ST_OK) return rc;
+        bool moved = false;
+        rc = reserve_batch_steps(*g->plan, 1024, &moved);
+        if (rc != ST_OK) return rc;
+        g->plan_bound = true;
+    }
     return ST_OK;
 }
 
@@ -420,6 +458,39 @@ st_status stencil_step(st_grid_t g, int nsteps, void* stream)
     rc = refresh_ghosts(g, s);
     if (rc != ST_OK) return rc;
     if (nsteps == 0 || g->g.npoints == 0) return ST_OK;
+    if (g->plan && g->plan_bound) {
+        // 2D grid on the persistent tile kernel: one captured launch for all steps
+        bool moved = false;
+        rc = reserve_batch_steps(*g->plan, nsteps, &moved);
+        if (rc != ST_OK) return rc;
+        if (moved) drop_graphs(g);
+        auto key = std::make_pair(nsteps, g->cur);
+        auto it = g->graphs.find(key);
+        for (int attempt = 0; it == g->graphs.end() && attempt < 2; ++attempt) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            ST_CUDA_TRY(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+            st_status erc = enqueue_batch_plan(*g->plan, nsteps, g->cur, g->cap);
+            cudaError_t ce = cudaStreamEndCapture(g->cap, &graph);
+            if (erc == ST_OK && ce == cudaSuccess) {
+                ce = cudaGraphInstantiate(&exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ce == cudaSuccess) {
+                    it = g->graphs.emplace(key, exec).first;
+                    break;
+                }
+            } else if (graph) {
+                cudaGraphDestroy(graph);
+            }
+            (void)cudaGetLastError();
+            if (attempt == 1) return erc != ST_OK ? erc : cuda_fail(ce, "tile graph capture");
+            batch_disable_coop(*g->plan);
+        }
+        ST_CUDA_TRY(cudaGraphLaunch(it->second, s));
+        g->cur = batch_final_slot(*g->plan, nsteps, g->cur);
+        g->step += nsteps;
+        return ST_OK;
+    }
     // Sources change per step (step index is a launch parameter): launch directly.
     const bool use_graph = (g->src < 0) && nsteps >= 2;
     if (!use_graph) {
@@ -448,6 +519,38 @@ st_status stencil_step(st_grid_t g, int nsteps, void* stream)
     }
     if (nsteps & 1) g->cur = 1 - g->cur;
     g->step += nsteps;
+    return ST_OK;
+}
+
+st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_tune: NULL handle");
+    if (nsteps < 1) return fail(ST_ERR_ARG, "stencil_tune: nsteps >= 1");
+    st_status rc = check_ready(g, "stencil_tune");
+    if (rc != ST_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last = s;
+    rc = refresh_ghosts(g, s);
+    if (rc != ST_OK) return rc;
+    if (!g->plan || !g->plan_bound) {
+        ST_CUDA_TRY(cudaStreamSynchronize(s));
+        return ST_OK;  // this family has nothing to tune
+    }
+    void* a = g->buf[ST_SLOT_A];
+    void* b = g->buf[ST_SLOT_B];
+    rc = tune_batch_plan(*g->plan, std::vector<Geom>{g->g}, &a, &b, nsteps, g->cur, s);
+    drop_graphs(g);
+    return rc;
+}
+
+st_status stencil_tune_config(st_grid_t g, int* cfg)
+{
+    if (!g || !cfg) return fail(ST_ERR_ARG, "stencil_tune_config: NULL argument");
+    if (!g->plan) {
+        cfg[0] = cfg[1] = cfg[2] = cfg[3] = 0;
+        return ST_OK;
+    }
+    batch_plan_config(*g->plan, cfg);
     return ST_OK;
 }
 

@@ -111,6 +111,7 @@ struct BatchPlan {
     std::vector<double> weights;
     std::vector<int32_t> off;
     double bc = 0.0;
+    int shape = 0;                 // 0: 3x3 box, 1: five-point star
 };
 
 BatchPlan make_batch_plan(const std::vector<Geom>& geoms, int npts, const int32_t* off2, const double* weights,

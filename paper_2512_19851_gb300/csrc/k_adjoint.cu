@@ -41,6 +41,11 @@ constexpr int A_CW = 8;  // consumer warps
 constexpr int A_THREADS = (A_CW + 1) * 32;
 constexpr int A_NC = A_CW * 32;
 constexpr int A_KMAX = 2;
+// Slots per intermediate ring: level s+1 reads planes pq-1..pq+1 of level s
+// while the next iteration's level s writes plane pq+2; with four slots those
+// never share a slot, so one consumer barrier per iteration (between the
+// levels) suffices.
+constexpr int LSLOTS = 4;
 
 struct AdjParams {
     int64_t nz, ny, nx, pitch, plane, origin;
@@ -49,6 +54,7 @@ struct AdjParams {
     int nyt, nzc, units;
     uint32_t stage_elems;                 // per staged plane
     uint32_t lam_off, kap_off, u_off[A_KMAX];  // element offsets inside a stage
+    uint32_t g_off;                       // gradient accumulator tile (owned planes only)
     uint32_t ring_elems;                  // one plane of an intermediate level ring
     double ac, bc, an, bn;
     int* status;
@@ -131,8 +137,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
     constexpr int VN = AV<T>::N;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* ring = reinterpret_cast<T*>(smem_raw);
-    T* lvl = ring + (size_t)P.NS * P.stage_elems;  // (K-1) rings of 3 planes
-    uint64_t* full = reinterpret_cast<uint64_t*>(lvl + (size_t)(K - 1) * 3 * P.ring_elems);
+    T* lvl = ring + (size_t)P.NS * P.stage_elems;  // (K-1) rings of LSLOTS planes
+    uint64_t* full = reinterpret_cast<uint64_t*>(lvl + (size_t)(K - 1) * LSLOTS * P.ring_elems);
     uint64_t* empty = full + P.NS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -144,7 +150,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
         ptx::fence_barrier_init();
     }
     // zero the intermediate rings once (their ghost columns stay 0)
-    for (size_t i = threadIdx.x; i < (size_t)(K - 1) * 3 * P.ring_elems; i += blockDim.x) lvl[i] = T(0);
+    for (size_t i = threadIdx.x; i < (size_t)(K - 1) * LSLOTS * P.ring_elems; i += blockDim.x) lvl[i] = T(0);
     __syncthreads();
     const uint32_t rowb = (uint32_t)(P.pitch * sizeof(T));
 
@@ -176,6 +182,9 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                     }
                 };
                 uint32_t bytes = 0;
+                // the gradient accumulators of the planes this unit owns
+                const bool gtile = (g64 != nullptr || ghi != nullptr) && q >= K && q < zce + K;
+                const uint32_t growb = (uint32_t)(P.pitch * 8);  // one double or two floats per point
                 if (zin) {
                     int64_t lo, hi;
                     rows_of(K, lo, hi);
@@ -183,7 +192,18 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                     rows_of(1, lo, hi);
                     bytes += (uint32_t)K * (uint32_t)(hi - lo) * rowb;
                 }
+                if (gtile) bytes += (uint32_t)tye * growb;
                 ptx::mbar_arrive_expect_tx(&full[s], bytes);
+                if (gtile) {
+                    const int64_t goff = P.origin + zi * P.plane + y0 * P.pitch - P.xl;  // row start
+                    if (sizeof(T) == 8) {
+                        ptx::bulk_g2s(dst + P.g_off, g64 + goff, (uint32_t)tye * growb / 1, &full[s]);
+                    } else {
+                        float* gd = reinterpret_cast<float*>(dst + P.g_off);
+                        ptx::bulk_g2s(gd, ghi + goff, (uint32_t)tye * rowb, &full[s]);
+                        ptx::bulk_g2s(gd + (size_t)P.TY * P.pitch, glo + goff, (uint32_t)tye * rowb, &full[s]);
+                    }
+                }
                 if (!zin) continue;
                 auto copy = [&](const T* a, T* d, int h) {
                     int64_t lo, hi;
@@ -246,15 +266,50 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 #pragma unroll
                 for (int e = 0; e < VN; ++e) dl[s][d][e] = T(0);
 
-        auto stage = [&](int q) -> const T* { return ring + (size_t)((base + q) % P.NS) * P.stage_elems; };
+        // running slot and parity of staged plane j (no modulo per lookup);
+        // stage(q) for a plane q <= j counts back from it
+        uint32_t sj = base % P.NS, pj = (base / P.NS) & 1;
+        int jcur = 0;
+        auto slot_of = [&](int q) -> uint32_t {
+            int sl = (int)sj - (jcur - q);
+            while (sl < 0) sl += P.NS;
+            return (uint32_t)sl;
+        };
+        auto stage = [&](int q) -> const T* { return ring + (size_t)slot_of(q) * P.stage_elems; };
         const int nq = zce + 2 * K;
+        // task -> (row, x group) per level, fixed for the unit; tasks below
+        // tye*ngx are the interior rows (same owner at every level, for the
+        // gradient delay lines), the rest the level's halo rows
+        int trr[K][2], tgx[K][2];
+        bool tval[K][2];
+#pragma unroll
+        for (int s = 1; s <= K; ++s) {
+            const int hs = K - s, rows_s = tye + 2 * hs;
+#pragma unroll
+            for (int ti = 0; ti < 2; ++ti) {
+                const int t = ct + ti * A_NC;
+                int rr = 0, gx = 0;
+                tval[s - 1][ti] = t < rows_s * ngx;
+                if (t < tye * ngx) {
+                    rr = t / ngx;
+                    gx = t - rr * ngx;
+                } else if (tval[s - 1][ti]) {
+                    const int h = t - tye * ngx;
+                    const int hr = h / ngx;  // 0 .. 2hs-1
+                    gx = h - hr * ngx;
+                    rr = hr < hs ? -hs + hr : tye + (hr - hs);
+                }
+                trr[s - 1][ti] = rr;
+                tgx[s - 1][ti] = gx;
+            }
+        }
         for (int j = 0; j < nq; ++j) {
+            jcur = j;
             // A wait that runs out is recorded, and the warp carries on without
             // waiting: every consumer warp must keep reaching the named
             // barriers below, which have no time limit of their own.
             if (!dead) {
-                const uint32_t g = base + j;
-                if (!ptx::mbar_wait_warp(&full[g % P.NS], (g / P.NS) & 1)) {
+                if (!ptx::mbar_wait_warp(&full[sj], pj)) {
                     atimeout(P.status);
                     dead = true;
                 }
@@ -277,7 +332,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                 } else {
 #pragma unroll
                     for (int d = 0; d < 3; ++d)
-                        src[d] = lvl + (size_t)(s - 2) * 3 * P.ring_elems + (size_t)((pq - 1 + d) % 3) * P.ring_elems;
+                        src[d] = lvl + (size_t)(s - 2) * LSLOTS * P.ring_elems +
+                                 (size_t)((pq - 1 + d) % LSLOTS) * P.ring_elems;
                     src_h = K - s + 1;
                 }
                 const T* kap[3];
@@ -286,22 +342,14 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                 const T* us[3];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) us[d] = stage(pq - 1 + d) + P.u_off[s - 1];
-                T* dst = (s < K) ? lvl + (size_t)(s - 1) * 3 * P.ring_elems + (size_t)(pq % 3) * P.ring_elems
+                T* dst = (s < K) ? lvl + (size_t)(s - 1) * LSLOTS * P.ring_elems + (size_t)(pq % LSLOTS) * P.ring_elems
                                  : nullptr;
-                const int ntasks = rows_s * ngx;
-                for (int t = ct; t < ntasks; t += A_NC) {
-                    // tasks [0, tye*ngx) are the interior rows (fixed owner for the gradient ring)
-                    int rr, gx;
-                    if (t < tye * ngx) {
-                        rr = t / ngx;
-                        gx = t - rr * ngx;
-                    } else {
-                        const int h = t - tye * ngx;
-                        const int hr = h / ngx;  // 0 .. 2hs-1
-                        gx = h - hr * ngx;
-                        rr = hr < hs ? -hs + hr : tye + (hr - hs);
-                    }
-                    const int x = gx * VN;
+#pragma unroll
+                for (int ti = 0; ti < 2; ++ti) {
+                    if (!tval[s - 1][ti]) continue;
+                    const int t = ct + ti * A_NC;
+                    const int rr = trr[s - 1][ti];
+                    const int x = tgx[s - 1][ti] * VN;
                     const int64_t yabs = y0 + rr;
                     const bool outside = !PERIODIC && (zout || yabs < 0 || yabs >= P.ny);
                     T o[VN];
@@ -334,11 +382,12 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                         // x neighbours
                         T lxm[VN], lxp[VN], kxm[VN], kxp[VN];
 #pragma unroll
+                        const int nxi = (int)P.nx;
                         for (int e = 0; e < VN; ++e) {
-                            int64_t xm = x + e - 1, xp = x + e + 1;
+                            int xm = x + e - 1, xp = x + e + 1;
                             if (PERIODIC) {
-                                xm = xm < 0 ? xm + P.nx : xm;
-                                xp = xp >= P.nx ? xp - P.nx : xp;
+                                xm = xm < 0 ? xm + nxi : xm;
+                                xp = xp >= nxi ? xp - nxi : xp;
                             }
                             lxm[e] = e > 0 ? lc[e - 1] : lrow[xm];
                             kxm[e] = e > 0 ? kc[e - 1] : krow[xm];
@@ -368,10 +417,10 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                             const T* urow = us[1] + uo;
 #pragma unroll
                             for (int e = 0; e < VN; ++e) {
-                                int64_t xm = x + e - 1, xp = x + e + 1;
+                                int xm = x + e - 1, xp = x + e + 1;
                                 if (PERIODIC) {
-                                    xm = xm < 0 ? xm + P.nx : xm;
-                                    xp = xp >= P.nx ? xp - P.nx : xp;
+                                    xm = xm < 0 ? xm + nxi : xm;
+                                    xp = xp >= nxi ? xp - nxi : xp;
                                 }
                                 const T uxm = e > 0 ? uc[e - 1] : urow[xm];
                                 const T uxp = (e < VN - 1 && !(PERIODIC && x + e + 1 == P.nx)) ? uc[e + 1] : urow[xp];
@@ -406,7 +455,6 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                 }
                 if (s < K) consumer_bar();  // level s is read by level s + 1 below
             }
-            consumer_bar();  // ring slots are rewritten next iteration
             // plane j - K is complete for the owner: flush the K gradient terms once
             {
                 const int pq = j - K;
@@ -415,10 +463,12 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                     const int rr = ct / ngx;
                     const int x = (ct - rr * ngx) * VN;
                     const int64_t off = P.origin + zabs * P.plane + (y0 + rr) * P.pitch + x;
-                    // the K terms of plane pq, in step order (level 1 = the latest step)
+                    // the K terms of plane pq, in step order (level 1 = the latest step);
+                    // the old accumulator comes from the staged tile of plane pq
+                    const T* gst = stage(pq) + P.g_off + rr * (int)P.pitch + P.xl + x;
                     if constexpr (sizeof(T) == 8) {
                         if (x + VN <= P.nx) {
-                            double2 gv = *reinterpret_cast<const double2*>(g64 + off);
+                            double2 gv = *reinterpret_cast<const double2*>(gst);
 #pragma unroll
                             for (int s = 1; s <= K; ++s) {
                                 gv.x += (double)dl[s - 1][K - s][0];
@@ -427,16 +477,18 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                             *reinterpret_cast<double2*>(g64 + off) = gv;
                         } else {
                             for (int e = 0; e < VN && x + e < P.nx; ++e) {
-                                double gv = g64[off + e];
+                                double gv = gst[e];
 #pragma unroll
                                 for (int s = 1; s <= K; ++s) gv += (double)dl[s - 1][K - s][e];
                                 g64[off + e] = gv;
                             }
                         }
                     } else {
+                        const float* hs = reinterpret_cast<const float*>(gst);
+                        const float* ls = hs + (size_t)P.TY * P.pitch;
                         if (x + VN <= P.nx) {
-                            float4 h = *reinterpret_cast<const float4*>(ghi + off);
-                            float4 l = *reinterpret_cast<const float4*>(glo + off);
+                            float4 h = *reinterpret_cast<const float4*>(hs);
+                            float4 l = *reinterpret_cast<const float4*>(ls);
 #pragma unroll
                             for (int s = 1; s <= K; ++s) {
                                 ff_add(h.x, l.x, (float)dl[s - 1][K - s][0]);
@@ -448,7 +500,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                             *reinterpret_cast<float4*>(glo + off) = l;
                         } else {
                             for (int e = 0; e < VN && x + e < P.nx; ++e) {
-                                float h = ghi[off + e], l = glo[off + e];
+                                float h = hs[e], l = ls[e];
 #pragma unroll
                                 for (int s = 1; s <= K; ++s) ff_add(h, l, (float)dl[s - 1][K - s][e]);
                                 ghi[off + e] = h;
@@ -472,13 +524,18 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
             // staged plane j-K-1 is no longer needed
             if (j - K - 1 >= 0) {
                 __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(&empty[(base + j - K - 1) % P.NS]);
+                if (lane == 0) ptx::mbar_arrive(&empty[slot_of(j - K - 1)]);
+            }
+            if (++sj == (uint32_t)P.NS) {
+                sj = 0;
+                pj ^= 1u;
             }
         }
-        // release the planes still held
+        // release the planes still held (sj now belongs to plane nq)
+        jcur = nq;
         for (int q = (nq - K - 1 > 0 ? nq - K - 1 : 0); q < nq; ++q) {
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&empty[(base + q) % P.NS]);
+            if (lane == 0) ptx::mbar_arrive(&empty[slot_of(q)]);
         }
         gq = base + nq;
     }
@@ -489,7 +546,7 @@ __global__ void k_fold_ff(const float* __restrict__ hi, const float* __restrict_
 {
     const int64_t rows = g.nz * g.ny;
     for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int64_t z = row / g.ny, y = row - z * g.ny;
+        const int64_t z = (uint32_t)row / (uint32_t)g.ny, y = row - z * g.ny;  // 32-bit division
         const int64_t base = g.origin + z * g.plane + y * g.pitch;
         for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x)
             grad[base + x] += (double)hi[base + x] + (double)lo[base + x];
@@ -507,7 +564,7 @@ int adj_sm_count()
     return n;
 }
 
-constexpr size_t A_SMEM = 212 * 1024;
+constexpr size_t A_SMEM = 220 * 1024;
 
 struct AdjCfg {
     int K, TY, ZC, NS;
@@ -521,9 +578,11 @@ bool adj_cfg(const Geom& g, int kmax, AdjCfg* c)
     const int TY = (int)std::min<int64_t>(std::min(16, A_NC / std::max(1, ngx)), g.ny);
     if (TY < 1) return false;
     for (int K = kmax; K >= 1; --K) {
+        if ((TY + 2 * (K - 1)) * ngx > 2 * A_NC) continue;  // at most two tasks per thread and level
         const size_t rows = 2 * (size_t)(TY + 2 * K) + (size_t)K * (TY + 2);
-        const size_t sb = (rows * g.pitch * g.esize + 127) / 128 * 128;
-        const size_t rb = (K > 1) ? (size_t)(K - 1) * 3 * ((size_t)(TY + 2 * (K - 1)) * g.pitch * g.esize) : 0;
+        // + the gradient accumulator tile: TY rows of 8 bytes per point
+        const size_t sb = ((rows * g.pitch * g.esize + (size_t)TY * g.pitch * 8) + 127) / 128 * 128;
+        const size_t rb = (K > 1) ? (size_t)(K - 1) * LSLOTS * ((size_t)(TY + 2 * (K - 1)) * g.pitch * g.esize) : 0;
         if (rb + (size_t)(K + 3) * sb + 256 > A_SMEM) continue;  // K+2 resident planes + 1 in flight
         const int NS = (int)std::min<size_t>(8, (A_SMEM - rb - 256) / sb);
         const int nyt = (int)((g.ny + TY - 1) / TY);
@@ -563,6 +622,7 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
     P.kap_off = (uint32_t)((c.TY + 2 * K) * g.pitch);
     P.u_off[0] = 2 * P.kap_off;
     P.u_off[1] = P.u_off[0] + (uint32_t)((c.TY + 2) * g.pitch);
+    P.g_off = P.u_off[0] + (uint32_t)(K * (c.TY + 2) * g.pitch);
     P.ring_elems = (uint32_t)((c.TY + 2 * (K - 1)) * g.pitch);
     const StarCoef& k = f.sc;
     P.ac = k.c_a;

@@ -33,13 +33,15 @@ namespace st {
 namespace {
 
 constexpr int BMAXP = 9;
+constexpr int SHAPE_BOX9 = 0;   // any offsets in the 3x3 neighbourhood
+constexpr int SHAPE_STAR5 = 1;  // no diagonal offsets: 5 FMAs per point
 
 struct GridDesc {
     void* a;
     void* b;
     int64_t pitch, origin;
     int ny, nx;
-    double w[BMAXP];
+    double w[9];  // row-major 3x3 weight table over (dy, dx), absent offsets 0
 };
 
 struct TileDesc {
@@ -67,7 +69,10 @@ struct BatchParams {
 
 __device__ __forceinline__ int wrapn(int i, int n)
 {
-    i %= n;
+    if (i >= 0 && i < n) return i;
+    if (i < 0 && i >= -n) return i + n;
+    if (i >= n && i < 2 * n) return i - n;
+    i %= n;  // halos wider than the grid
     return i < 0 ? i + n : i;
 }
 
@@ -105,7 +110,15 @@ __device__ __forceinline__ T ld_cg(const T* p)
 }
 
 // One pass of kp steps over one tile.
-template <typename T>
+//
+// Load: tile + kp-wide halo into s0, rows by warps, columns by lanes (wrapped
+// for a periodic boundary, the boundary value outside a Dirichlet domain).
+// Each step: threads own column strips (64 columns per row band, blockDim/64
+// bands); a thread walks its strip top to bottom keeping the three rows of
+// its 3x3 window in registers, so each point costs three shared loads and
+// nine FMAs.  The weights sit in a row-major 3x3 table (absent offsets 0), so
+// the FMA order is row-major over (dy, dx): the order of the box offsets.
+template <typename T, int SHAPE, bool PERIODIC>
 __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int src_slot, T* s0, T* s1)
 {
     const GridDesc& G = P.grids[t.g];
@@ -114,43 +127,96 @@ __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int sr
     const int W = t.tw + 2 * kp, H = t.th + 2 * kp;
     const int RS = P.row_stride;
     const int nx = G.nx, ny = G.ny;
+    const int64_t pitch = G.pitch;
     const T bc = T(P.bc);
-    // load tile + halo
-    for (int idx = threadIdx.x; idx < W * H; idx += blockDim.x) {
-        const int ly = idx / W, lx = idx - ly * W;
-        int gy = t.y0 - kp + ly, gx = t.x0 - kp + lx;
-        T v;
-        if (P.periodic) {
-            gy = wrapn(gy, ny);
-            gx = wrapn(gx, nx);
-            v = ld_cg(src + (int64_t)gy * G.pitch + gx);
-        } else {
-            v = (gy < 0 || gy >= ny || gx < 0 || gx >= nx) ? bc : ld_cg(src + (int64_t)gy * G.pitch + gx);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int ly = warp; ly < H; ly += nwarps) {
+        int gy = t.y0 - kp + ly;
+        const bool yout = !PERIODIC && (gy < 0 || gy >= ny);
+        if (PERIODIC) gy = wrapn(gy, ny);
+        const T* srow = src + (int64_t)gy * pitch;
+        T* srow_s = s0 + ly * RS;
+        for (int lx = lane; lx < W; lx += 32) {
+            int gx = t.x0 - kp + lx;
+            T v;
+            if (PERIODIC) {
+                gx = wrapn(gx, nx);
+                v = ld_cg(srow + gx);
+            } else {
+                v = (yout || gx < 0 || gx >= nx) ? bc : ld_cg(srow + gx);
+            }
+            srow_s[lx] = v;
         }
-        s0[ly * RS + lx] = v;
     }
     __syncthreads();
-    T wk[BMAXP];
+    T w[9];
 #pragma unroll
-    for (int k = 0; k < BMAXP; ++k) wk[k] = k < P.npts ? T(G.w[k]) : T(0);
+    for (int i = 0; i < 9; ++i) w[i] = T(G.w[i]);
+    const int nb = blockDim.x >> 6;  // row bands
+    const int cx = threadIdx.x & 63, band = threadIdx.x >> 6;
     T* in = s0;
     T* out = s1;
     for (int j = 1; j <= kp; ++j) {
         const bool last = j == kp;
         const int rw = W - 2 * j, rh = H - 2 * j;
-        for (int idx = threadIdx.x; idx < rw * rh; idx += blockDim.x) {
-            const int ry = idx / rw, rx = idx - ry * rw;
-            const int ly = ry + j, lx = rx + j;
-            T acc = T(0);
-#pragma unroll
-            for (int k = 0; k < BMAXP; ++k)
-                if (k < P.npts) acc = fma(wk[k], in[(ly + P.dy[k]) * RS + lx + P.dx[k]], acc);
-            const int gy = t.y0 - kp + ly, gx = t.x0 - kp + lx;
-            if (!P.periodic && (gy < 0 || gy >= ny || gx < 0 || gx >= nx)) acc = bc;  // ghost stays fixed
-            if (last)
-                dst[(int64_t)gy * G.pitch + gx] = acc;  // last step: region == tile interior
-            else
-                out[ly * RS + lx] = acc;
+        const int bh = (rh + nb - 1) / nb;
+        const int r0 = j + band * bh, r1 = min(j + rh, r0 + bh);
+        for (int lx = j + cx; lx < j + rw; lx += 64) {
+            if (r0 >= r1) break;
+            const T* pin = in + (r0 - 1) * RS + lx;  // row above the first output row
+            T a0 = pin[-1], a1 = pin[0], a2 = pin[1];
+            pin += RS;
+            T b0 = pin[-1], b1 = pin[0], b2 = pin[1];
+            pin += RS;  // row below the current output row
+            const int gx = t.x0 - kp + lx;
+            const bool xout = !PERIODIC && (gx < 0 || gx >= nx);
+            auto point = [&](T c0, T c1, T c2) -> T {
+                T acc;
+                if constexpr (SHAPE == SHAPE_BOX9) {
+                    acc = fma(w[0], a0, T(0));
+                    acc = fma(w[1], a1, acc);
+                    acc = fma(w[2], a2, acc);
+                    acc = fma(w[3], b0, acc);
+                    acc = fma(w[4], b1, acc);
+                    acc = fma(w[5], b2, acc);
+                    acc = fma(w[6], c0, acc);
+                    acc = fma(w[7], c1, acc);
+                    acc = fma(w[8], c2, acc);
+                } else {  // five-point star: the corners carry no weight
+                    acc = fma(w[1], a1, T(0));
+                    acc = fma(w[3], b0, acc);
+                    acc = fma(w[4], b1, acc);
+                    acc = fma(w[5], b2, acc);
+                    acc = fma(w[7], c1, acc);
+                }
+                return acc;
+            };
+            if (!last) {
+                T* po = out + r0 * RS + lx;
+                for (int ly = r0; ly < r1; ++ly) {
+                    const T c0 = pin[-1], c1 = pin[0], c2 = pin[1];
+                    T acc = point(c0, c1, c2);
+                    if (!PERIODIC) {
+                        const int gy = t.y0 - kp + ly;
+                        if (xout || gy < 0 || gy >= ny) acc = bc;  // ghost stays fixed
+                    }
+                    *po = acc;
+                    po += RS;
+                    pin += RS;
+                    a0 = b0; a1 = b1; a2 = b2;
+                    b0 = c0; b1 = c1; b2 = c2;
+                }
+            } else {  // last step: the region is the tile interior, written to global memory
+                T* po = dst + (int64_t)(t.y0 - kp + r0) * pitch + gx;
+                for (int ly = r0; ly < r1; ++ly) {
+                    const T c0 = pin[-1], c1 = pin[0], c2 = pin[1];
+                    *po = point(c0, c1, c2);
+                    po += pitch;
+                    pin += RS;
+                    a0 = b0; a1 = b1; a2 = b2;
+                    b0 = c0; b1 = c1; b2 = c2;
+                }
+            }
         }
         __syncthreads();
         T* tmp = in;
@@ -159,7 +225,7 @@ __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int sr
     }
 }
 
-template <typename T>
+template <typename T, int SHAPE, bool PERIODIC>
 __global__ void k_batch(const __grid_constant__ BatchParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -177,7 +243,7 @@ __global__ void k_batch(const __grid_constant__ BatchParams P)
             const int ti = s_tile;
             if (ti >= P.ntiles) break;
             const TileDesc t = P.tiles[ti];
-            run_tile<T>(P, t, kp, src_slot, s0, s1);
+            run_tile<T, SHAPE, PERIODIC>(P, t, kp, src_slot, s0, s1);
         }
         if (p + 1 < P.pass1) {
             const unsigned expected = gridDim.x + (unsigned)P.barrier_extra;
@@ -217,17 +283,21 @@ void build_tiles(const BatchPlan& p, const std::vector<int>& ny, const std::vect
                  std::vector<TileDesc>& out)
 {
     out.clear();
-    for (int g = 0; g < p.ngrids; ++g)
-        for (int y0 = 0; y0 < ny[g]; y0 += TH)
-            for (int x0 = 0; x0 < nx[g]; x0 += TW) {
+    // equal tiles per grid (no thin slivers at the edges): each extent is
+    // split into ceil(n / T) nearly equal parts of at most T points
+    for (int g = 0; g < p.ngrids; ++g) {
+        const int cx = (nx[g] + TW - 1) / TW, cy = (ny[g] + TH - 1) / TH;
+        for (int iy = 0; iy < cy; ++iy)
+            for (int ix = 0; ix < cx; ++ix) {
                 TileDesc t{};
                 t.g = g;
-                t.x0 = x0;
-                t.y0 = y0;
-                t.tw = std::min(TW, nx[g] - x0);
-                t.th = std::min(TH, ny[g] - y0);
+                t.x0 = (int)((int64_t)nx[g] * ix / cx);
+                t.y0 = (int)((int64_t)ny[g] * iy / cy);
+                t.tw = (int)((int64_t)nx[g] * (ix + 1) / cx) - t.x0;
+                t.th = (int)((int64_t)ny[g] * (iy + 1) / cy) - t.y0;
                 out.push_back(t);
             }
+    }
     std::stable_sort(out.begin(), out.end(),
                      [](const TileDesc& a, const TileDesc& b) { return a.tw * a.th > b.tw * b.th; });
 }
@@ -259,6 +329,9 @@ BatchPlan make_batch_plan(const std::vector<Geom>& geoms, int npts, const int32_
     for (int k = 0; k < 2 * npts; ++k)
         if (off2[k] < -1 || off2[k] > 1) small = false;
     p.generic = force_generic || !small;
+    p.shape = SHAPE_STAR5;
+    for (int k = 0; k < npts; ++k)
+        if (off2[2 * k] != 0 && off2[2 * k + 1] != 0) p.shape = SHAPE_BOX9;
     for (int i = 0; i < p.ngrids; ++i) {
         const Geom& g = geoms[i];
         GenParams P;
@@ -333,7 +406,10 @@ st_status bind_batch_plan(BatchPlan& p, const std::vector<Geom>& geoms, void* co
         gd[i].origin = geoms[i].origin;
         gd[i].ny = (int)geoms[i].ny;
         gd[i].nx = (int)geoms[i].nx;
-        for (int k = 0; k < p.npts; ++k) gd[i].w[k] = p.weights[(size_t)i * p.npts + k];
+        for (int k = 0; k < p.npts; ++k) {
+            const int cell = (p.off[2 * k] + 1) * 3 + (p.off[2 * k + 1] + 1);
+            gd[i].w[cell] += p.weights[(size_t)i * p.npts + k];
+        }
     }
     if (d->grids) cudaFree(d->grids);
     d->grids = nullptr;
@@ -394,7 +470,14 @@ static st_status enqueue_tiled(BatchPlan& p, int nsteps, int cur, cudaStream_t s
     P.timeout_ns = timeout_ns;
     P.barrier_extra = barrier_extra;
     ST_CUDA_TRY(cudaMemsetAsync(d->counters, 0, sizeof(unsigned) * 2 * npasses, s));
-    const void* fn = p.esize == 8 ? (const void*)k_batch<double> : (const void*)k_batch<float>;
+    typedef void (*KFn)(const BatchParams);
+    static const KFn table[2][2][2] = {  // [double][star][periodic]
+        {{k_batch<float, SHAPE_BOX9, false>, k_batch<float, SHAPE_BOX9, true>},
+         {k_batch<float, SHAPE_STAR5, false>, k_batch<float, SHAPE_STAR5, true>}},
+        {{k_batch<double, SHAPE_BOX9, false>, k_batch<double, SHAPE_BOX9, true>},
+         {k_batch<double, SHAPE_STAR5, false>, k_batch<double, SHAPE_STAR5, true>}}};
+    const KFn kf = table[p.esize == 8][p.shape == SHAPE_STAR5][p.periodic ? 1 : 0];
+    const void* fn = (const void*)kf;
     ST_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (coop && d->coop_ok) {
         int per_sm = 0;
@@ -413,7 +496,7 @@ static st_status enqueue_tiled(BatchPlan& p, int nsteps, int cur, cudaStream_t s
         at[0].val.cooperative = 1;
         lc.attrs = at;
         lc.numAttrs = 1;
-        cudaError_t e = p.esize == 8 ? cudaLaunchKernelEx(&lc, k_batch<double>, P) : cudaLaunchKernelEx(&lc, k_batch<float>, P);
+        cudaError_t e = cudaLaunchKernelEx(&lc, kf, P);
         if (e == cudaSuccess) return ST_OK;
         return cuda_fail(e, "batch cooperative launch");
     }
@@ -423,10 +506,7 @@ static st_status enqueue_tiled(BatchPlan& p, int nsteps, int cur, cudaStream_t s
     for (int pass = 0; pass < npasses; ++pass) {
         P.pass0 = pass;
         P.pass1 = pass + 1;
-        if (p.esize == 8)
-            k_batch<double><<<grid, threads, smem, s>>>(P);
-        else
-            k_batch<float><<<grid, threads, smem, s>>>(P);
+        kf<<<grid, threads, smem, s>>>(P);
         ST_CUDA_TRY(cudaGetLastError());
     }
     return ST_OK;
@@ -523,11 +603,12 @@ st_status tune_batch_plan(BatchPlan& p, const std::vector<Geom>& geoms, void* co
         return rc;
     }
     std::vector<Candidate> cands;
-    const int tiles[][2] = {{64, 16}, {128, 16}, {128, 32}, {256, 16}, {256, 32}, {64, 64}};
-    const int ks[] = {1, 2, 4, 5, 8, 10};
+    // tile shapes from small (single grids, many SMs) to wide (big grids)
+    const int tiles[][2] = {{32, 8}, {32, 16}, {64, 16}, {128, 16}, {128, 32}, {256, 16}, {64, 64}};
+    const int ks[] = {1, 2, 4, 6, 10};
     for (auto& t : tiles)
         for (int k : ks)
-            for (int th : {256, 512}) {
+            for (int th : {128, 256}) {
                 int rs;
                 if (tile_smem(t[0], t[1], k, p.esize, &rs) > 200 * 1024) continue;
                 cands.push_back(Candidate{t[0], t[1], th, k});
@@ -566,9 +647,8 @@ st_status tune_batch_plan(BatchPlan& p, const std::vector<Geom>& geoms, void* co
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
             ms_best = std::min(ms_best, ms);
-            // each trial advanced the data: restore before the next one
-            rc = copy_all(false);
-            if (rc != ST_OK) break;
+            // trials advance the data; run time does not depend on the values,
+            // so the inputs are restored once, after the last trial
         }
         if (rc != ST_OK) break;
         if (ok && ms_best < best) {

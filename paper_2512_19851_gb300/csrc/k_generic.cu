@@ -95,7 +95,7 @@ __global__ void k_fill_ghosts(T* __restrict__ buf, Geom g, T value)
 {
     const int64_t rows = g.pnz * g.pny;
     for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int64_t pz = row / g.pny;
+        const int64_t pz = (uint32_t)row / (uint32_t)g.pny;  // 32-bit: rows < 2^32
         const int64_t py = row - pz * g.pny;
         T* rp = buf + pz * g.plane + py * g.pitch;
         const bool ghost_row = (pz < g.rz) || (pz >= g.rz + g.nz) || (py < g.r) || (py >= g.r + g.ny);
@@ -168,71 +168,122 @@ __device__ __forceinline__ void f2_add(F2& acc, float x, float xlo)
     acc.lo += e + xlo;
 }
 
-// mode 0: d = a - b (b may be null); mode 1: also lam_out = d on the interior.
-// One warp handles whole interior rows; partials[3*block + {0,1,2}].
-__device__ __forceinline__ void red_elem(double av, double bv, Red3& acc)
-{
-    const double d = av - bv;
-    acc.s += d;
-    acc.q = fma(d, d, acc.q);
-    acc.m = fmax(acc.m, fabs(d));
-}
+// Per-element accumulation: FP32 inputs use the compensated float pair,
+// FP64 inputs plain double.
+struct AccF {
+    F2 S{0.f, 0.f}, Q{0.f, 0.f};
+    // max |d| kept exactly in single precision: |d| = |dh| + sign(dh) dl with
+    // |dl| at most half the float spacing around dh, so ordering by |dh| first
+    // and sign(dh) dl second orders the exact |d| (a rounding interval never
+    // reaches past the gap to the next float)
+    float mA = 0.f, mS = 0.f;
+    __device__ __forceinline__ float add(float av, float bv)
+    {
+        float dh, dl;
+        two_sum(av, -bv, dh, dl);  // d = dh + dl exactly
+        f2_add(S, dh, dl);
+        const float p = dh * dh;
+        const float pe = fmaf(dh, dh, -p);  // dh^2 = p + pe exactly
+        f2_add(Q, p, pe + 2.f * dh * dl);
+        const float A = fabsf(dh);
+        const float sg = dh < 0.f ? -dl : dl;
+        const bool gt = A > mA || (A == mA && sg > mS);
+        mA = gt ? A : mA;
+        mS = gt ? sg : mS;
+        return dh;
+    }
+    __device__ __forceinline__ Red3 result() const
+    {
+        return Red3{(double)S.hi + (double)S.lo, (double)Q.hi + (double)Q.lo, (double)mA + (double)mS};
+    }
+};
 
+struct AccD {
+    Red3 r{0.0, 0.0, 0.0};
+    __device__ __forceinline__ double add(double av, double bv)
+    {
+        const double d = av - bv;
+        r.s += d;
+        r.q = fma(d, d, r.q);
+        r.m = fmax(r.m, fabs(d));
+        return d;
+    }
+    __device__ __forceinline__ Red3 result() const { return r; }
+};
+
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<float> {
+    typedef float4 V;
+    typedef AccF Acc;
+    static constexpr int N = 4;
+};
+template <>
+struct VecOf<double> {
+    typedef double2 V;
+    typedef AccD Acc;
+    static constexpr int N = 2;
+};
+
+// mode 0: d = a - b (b may be null); mode 1: also lam_out = d on the interior.
+// Each warp walks whole interior rows; each lane loads 16-byte vectors, four
+// per trip, so several loads are in flight (interior rows start 16-byte
+// aligned).  partials[3*block + {0,1,2}].
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b, Geom g, double* __restrict__ partials,
                  int mode, T* __restrict__ lam_out)
 {
+    typedef typename VecOf<T>::V V;
+    constexpr int N = VecOf<T>::N;
+    constexpr int U = 4;  // vectors per lane per trip
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t rows = g.nz * g.ny;
     const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
-    Red3 acc{0.0, 0.0, 0.0};
-    if constexpr (sizeof(T) == 4) {
-        F2 S{0.f, 0.f}, Q{0.f, 0.f};
-        float mh = 0.f;
-        double dmax = 0.0;
-        for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < rows; row += wstride) {
-            const int64_t z = row / g.ny;
-            const int64_t y = row - z * g.ny;
-            const int64_t base = g.origin + z * g.plane + y * g.pitch;
-            for (int64_t x = lane; x < g.nx; x += 32) {
-                const float av = a[base + x];
-                const float bv = b ? b[base + x] : 0.f;
-                float dh, dl;
-                two_sum(av, -bv, dh, dl);  // d = dh + dl exactly
-                if (mode == 1) lam_out[base + x] = dh;
-                f2_add(S, dh, dl);
-                const float p = dh * dh;
-                const float pe = fmaf(dh, dh, -p);  // dh^2 = p + pe exactly
-                f2_add(Q, p, pe + 2.f * dh * dl);
-                const float ad = fabsf(dh);
-                if (ad >= mh) {  // a new maximum is rare: resolve it in double
-                    mh = ad;
-                    dmax = fmax(dmax, fabs((double)dh + (double)dl));
+    const int64_t nxv = g.nx / N * N;  // vector part of a row
+    typename VecOf<T>::Acc acc;
+    // rows < 2^32 (nz <= 65535, ny <= 2^24 ... checked on the host): 32-bit
+    // division, which does not go through the FP64 pipe as 64-bit division does
+    const uint32_t ny32 = (uint32_t)g.ny;
+    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < rows; row += wstride) {
+        const uint32_t z = (uint32_t)row / ny32;
+        const uint32_t y = (uint32_t)row - z * ny32;
+        const int64_t base = g.origin + (int64_t)z * g.plane + (int64_t)y * g.pitch;
+        const T* ra = a + base;
+        const T* rb = b ? b + base : nullptr;
+        for (int64_t x0 = (int64_t)lane * N; x0 < nxv; x0 += (int64_t)32 * N * U) {
+            V va[U], vb[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t x = x0 + (int64_t)u * 32 * N;
+                if (x < nxv) {
+                    va[u] = *reinterpret_cast<const V*>(ra + x);
+                    if (rb) vb[u] = *reinterpret_cast<const V*>(rb + x);
                 }
             }
-        }
-        acc.s = (double)S.hi + (double)S.lo;
-        acc.q = (double)Q.hi + (double)Q.lo;
-        acc.m = dmax;
-    } else {
-        for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < rows; row += wstride) {
-            const int64_t z = row / g.ny;
-            const int64_t y = row - z * g.ny;
-            const int64_t base = g.origin + z * g.plane + y * g.pitch;
-            for (int64_t x = lane; x < g.nx; x += 32) {
-                const double av = a[base + x];
-                const double bv = b ? (double)b[base + x] : 0.0;
-                if (mode == 1) lam_out[base + x] = av - bv;
-                red_elem(av, bv, acc);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t x = x0 + (int64_t)u * 32 * N;
+                if (x >= nxv) break;
+                const T* pa = reinterpret_cast<const T*>(&va[u]);
+                const T* pb = reinterpret_cast<const T*>(&vb[u]);
+                T dv[N];
+#pragma unroll
+                for (int e = 0; e < N; ++e) dv[e] = acc.add(pa[e], rb ? pb[e] : T(0));
+                if (mode == 1) *reinterpret_cast<V*>(lam_out + base + x) = *reinterpret_cast<const V*>(dv);
             }
         }
+        for (int64_t x = nxv + lane; x < g.nx; x += 32) {  // ragged tail
+            const T d = acc.add(ra[x], rb ? rb[x] : T(0));
+            if (mode == 1) lam_out[base + x] = d;
+        }
     }
-    acc = block_red(acc);
+    Red3 r = block_red(acc.result());
     if (threadIdx.x == 0) {
-        partials[3 * blockIdx.x + 0] = acc.s;
-        partials[3 * blockIdx.x + 1] = acc.q;
-        partials[3 * blockIdx.x + 2] = acc.m;
+        partials[3 * blockIdx.x + 0] = r.s;
+        partials[3 * blockIdx.x + 1] = r.q;
+        partials[3 * blockIdx.x + 2] = r.m;
     }
 }
 

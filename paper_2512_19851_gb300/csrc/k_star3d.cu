@@ -259,18 +259,24 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                 ldv(stage(1) + off, cen[g][r]);
             }
         release(0);
+        // running ring slots of the centre plane (i + 1) and the plane above
+        // (i + 2), and the phase parity of the latter
+        uint32_t slot_c = (base + 1) % P.NS, slot_a = (base + 2) % P.NS;
+        uint32_t par_a = ((base + 2) / P.NS) & 1;
         for (int i = 0; i < zce; ++i) {
-            if (!wait_q(i + 2)) {
+            if (!ptx::mbar_wait_warp(&full[slot_a], par_a)) {
                 set_timeout(P.status);
                 return;
             }
-            const T* sa = stage(i + 2);
-            const T* sc = stage(i + 1);
+            const T* sa = ring + (size_t)slot_a * P.stage_elems + P.xl;
+            const T* sc = ring + (size_t)slot_c * P.stage_elems + P.xl;
             const T* sk = sc + P.u_elems;
             T* oplane = out + P.origin + (z0 + i) * P.plane + y0 * P.pitch;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 const int x = tgx[g] * VN;
+                // periodic only: the row end falls inside this group (ragged last group)
+                const bool wrap_in_group = PERIODIC && x + VN > P.nx;
                 const int rbase = trow[g] * (int)P.pitch + x;  // smem offset of row trow - 1
                 T up[VN], dn[VN], kv[2][VN];
 #pragma unroll
@@ -296,7 +302,7 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                     for (int j = 0; j < VN; ++j) {
                         const T xm = j == 0 ? left : cen[g][r][j - 1];
                         T xp = j == VN - 1 ? right : cen[g][r][j + 1];
-                        if (PERIODIC && x + j + 1 == P.nx) xp = crow[0];
+                        if (PERIODIC && wrap_in_group && x + j + 1 == P.nx) xp = crow[0];
                         o[j] = point<T, KAPPA, SYM>(P, cen[g][r][j], xm, xp, yl[j], yh[j], bel[g][r][j], abv[g][r][j],
                                                     KAPPA ? kv[r][j] : T(0));
                     }
@@ -317,8 +323,14 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                         cen[g][r][j] = abv[g][r][j];
                     }
             }
-            release(i + 1);
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&empty[slot_c]);  // plane i + 1
             if (i == zce - 1) release(i + 2);
+            slot_c = slot_a;
+            if (++slot_a == (uint32_t)P.NS) {
+                slot_a = 0;
+                par_a ^= 1u;
+            }
         }
         gq = base + zce + 2;
     }

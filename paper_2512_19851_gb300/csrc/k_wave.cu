@@ -12,9 +12,11 @@
 //    when it arrives (as z+4) and leaves it 9 planes later.  Only the centre
 //    plane's x and y neighbours are read from shared memory, so the ring must
 //    hold planes z..z+4 (5 stages) plus the ones in flight.
-//  * m and u^{n-1} are needed only at the point: they are loaded from global
-//    memory two planes ahead into registers.  u^{n+1} overwrites u^{n-1} in
-//    place (each point reads its own u^{n-1} before writing it).
+//  * m and u^{n-1} are needed only at the point: their plane tiles (TY rows,
+//    no halo) travel through a second, short bulk-copy ring with its own
+//    barriers, so no global load is ever waited on by the consumers.  u^{n+1}
+//    overwrites u^{n-1} in place (every point's u^{n-1} is staged before the
+//    point is written, and no other CTA reads it).
 #include <algorithm>
 #include <cstring>
 
@@ -33,9 +35,10 @@ constexpr int W_NC = W_CWARPS * 32;
 struct WaveParams {
     int64_t nz, ny, nx, pitch, plane, origin;
     int rz, r, xl;
-    int TY, ZC, NS;
+    int TY, ZC, NS, NSM;  // u-ring and (m, u^{n-1})-ring stages
     int nyt, nzc, units;
-    uint32_t stage_elems;
+    uint32_t stage_elems;    // u stage
+    uint32_t mstage_elems;   // (m, u^{n-1}) stage: m rows then u^{n-1} rows
     // coefficients: alpha/beta of the centre and of distance j (symmetric star)
     float ac, bc;
     float aj[WR], bj[WR];
@@ -59,19 +62,26 @@ __device__ __forceinline__ void timeout(int* status)
     if (status) atomicCAS(status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
 }
 
-template <bool PERIODIC>
+template <bool PERIODIC, bool ALPHA0>
 __global__ void __launch_bounds__(W_THREADS, 1)
 k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__ m, const __grid_constant__ WaveParams P)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* ring = reinterpret_cast<float*>(smem_raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)P.NS * P.stage_elems * sizeof(float));
+    float* mring = ring + (size_t)P.NS * P.stage_elems;
+    uint64_t* full = reinterpret_cast<uint64_t*>(mring + (size_t)P.NSM * P.mstage_elems);
     uint64_t* empty = full + P.NS;
+    uint64_t* mfull = empty + P.NS;
+    uint64_t* mempty = mfull + P.NSM;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.NS; ++s) {
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&empty[s], W_CWARPS);
+        }
+        for (int s = 0; s < P.NSM; ++s) {
+            ptx::mbar_init(&mfull[s], 1);
+            ptx::mbar_init(&mempty[s], W_CWARPS);
         }
         ptx::fence_barrier_init();
     }
@@ -80,19 +90,17 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
     const int H = 2 * WR;  // halo rows per tile
 
     if (warp == W_CWARPS) {
+        // ------------------------------------------------------------ producer
         if (lane != 0) return;
-        uint32_t gq = 0;
+        uint32_t gq = 0, gm = 0;
         for (int u = blockIdx.x; u < P.units; u += gridDim.x) {
             const int yt = u % P.nyt, zc = u / P.nyt;
             const int64_t y0 = (int64_t)yt * P.TY, z0 = (int64_t)zc * P.ZC;
             const int tye = (int)imin_w(P.TY, P.ny - y0);
             const int zce = (int)imin_w(P.ZC, P.nz - z0);
-            for (int q = 0; q < zce + 2 * WR; ++q, ++gq) {
+            auto issue_u = [&](int q) -> bool {  // u^n plane z0 - 4 + q with a 4-row halo
                 const uint32_t s = gq % P.NS, k = gq / P.NS;
-                if (k > 0 && !ptx::mbar_wait(&empty[s], (k - 1) & 1)) {
-                    timeout(P.status);
-                    return;
-                }
+                if (k > 0 && !ptx::mbar_wait(&empty[s], (k - 1) & 1)) return false;
                 const int64_t zi = z0 - WR + q;
                 float* dst = ring + (size_t)s * P.stage_elems;
                 ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)(tye + H) * rowb);
@@ -110,11 +118,35 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
                         j += run;
                     }
                 }
+                ++gq;
+                return true;
+            };
+            auto issue_m = [&](int i) -> bool {  // m and u^{n-1} of output plane z0 + i
+                const uint32_t s = gm % P.NSM, k = gm / P.NSM;
+                if (k > 0 && !ptx::mbar_wait(&mempty[s], (k - 1) & 1)) return false;
+                const int64_t off = (z0 + i + P.rz) * P.plane + (y0 + P.r) * P.pitch;
+                float* dst = mring + (size_t)s * P.mstage_elems;
+                ptx::mbar_arrive_expect_tx(&mfull[s], 2u * (uint32_t)tye * rowb);
+                ptx::bulk_g2s(dst, m + off, (uint32_t)tye * rowb, &mfull[s]);
+                ptx::bulk_g2s(dst + (size_t)P.TY * P.pitch, uprev_out + off, (uint32_t)tye * rowb, &mfull[s]);
+                ++gm;
+                return true;
+            };
+            bool ok = true;
+            for (int q = 0; q < 2 * WR && ok; ++q) ok = issue_u(q);
+            for (int i = 0; i < zce && ok; ++i) ok = issue_m(i) && issue_u(i + 2 * WR);
+            if (!ok) {
+                timeout(P.status);
+                return;
             }
         }
         for (uint32_t d = 0; d < (uint32_t)P.NS && d < gq; ++d) {
             const uint32_t g = gq - 1 - d;
             if (!ptx::mbar_wait(&full[g % P.NS], (g / P.NS) & 1)) timeout(P.status);
+        }
+        for (uint32_t d = 0; d < (uint32_t)P.NSM && d < gm; ++d) {
+            const uint32_t g = gm - 1 - d;
+            if (!ptx::mbar_wait(&mfull[g % P.NSM], (g / P.NSM) & 1)) timeout(P.status);
         }
         return;
     }
@@ -122,20 +154,21 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
     // ---------------------------------------------------------------- consumers
     const int ct = threadIdx.x;
     const int ngx = (int)((P.nx + 3) / 4);
-    uint32_t gq = 0;
+    const float bj[WR] = {P.bj[0], P.bj[1], P.bj[2], P.bj[3]};
+    const float aj[WR] = {P.aj[0], P.aj[1], P.aj[2], P.aj[3]};
+    uint32_t gq = 0, gm = 0;
     for (int u = blockIdx.x; u < P.units; u += gridDim.x) {
         const int yt = u % P.nyt, zc = u / P.nyt;
         const int64_t y0 = (int64_t)yt * P.TY, z0 = (int64_t)zc * P.ZC;
         const int tye = (int)imin_w(P.TY, P.ny - y0);
         const int zce = (int)imin_w(P.ZC, P.nz - z0);
-        const uint32_t base = gq;
+        const uint32_t base = gq, mbase = gm;
         const bool active = ct < tye * ngx;
         const int row = active ? ct / ngx : 0;
         const int x = active ? (ct - row * ngx) * 4 : 0;
         const bool full4 = x + 4 <= P.nx;
         const int64_t gofs = P.origin + (y0 + row) * P.pitch + x;  // + z * plane
         float4 q[2 * WR + 1];
-        float4 m0, m1, p0, p1;  // m and u^{n-1} of the next two output planes
 
         auto stage_of = [&](int qq) -> const float* {
             return ring + (size_t)((base + qq) % P.NS) * P.stage_elems + P.xl;
@@ -151,8 +184,7 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
         // plane q is a centre (output z0 + q - 4) for q in [4, zce + 4); all
         // other planes of the chunk only feed the z queues
         auto is_centre = [&](int qq) -> bool { return qq >= WR && qq < zce + WR; };
-        auto read_q = [&](int qq) -> float4 {
-            const float* rp = stage_of(qq) + (int64_t)(row + WR) * P.pitch;
+        auto read4 = [&](const float* rp) -> float4 {
             if (full4) return *reinterpret_cast<const float4*>(rp + x);
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (x + 0 < P.nx) v.x = rp[x + 0];
@@ -160,15 +192,7 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
             if (x + 2 < P.nx) v.z = rp[x + 2];
             return v;
         };
-        auto load_g = [&](const float* arr, int64_t zz) -> float4 {
-            const float* p = arr + gofs + zz * P.plane;
-            if (full4) return __ldg(reinterpret_cast<const float4*>(p));
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (x + 0 < P.nx) v.x = p[0];
-            if (x + 1 < P.nx) v.y = p[1];
-            if (x + 2 < P.nx) v.z = p[2];
-            return v;
-        };
+        auto read_q = [&](int qq) -> float4 { return read4(stage_of(qq) + (int64_t)(row + WR) * P.pitch); };
         // prime: queue planes z0-4 .. z0+3 (q = 0..7)
         for (int qq = 0; qq < 2 * WR; ++qq) {
             if (!wait_plane(qq)) {
@@ -178,59 +202,67 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
             q[qq + 1] = active ? read_q(qq) : make_float4(0.f, 0.f, 0.f, 0.f);
             if (!is_centre(qq)) release(qq);
         }
-        m0 = m1 = p0 = p1 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (active) {
-            m0 = load_g(m, z0);
-            p0 = load_g(uprev_out, z0);
-            if (zce > 1) {
-                m1 = load_g(m, z0 + 1);
-                p1 = load_g(uprev_out, z0 + 1);
-            }
-        }
+        // running ring slots (no modulo per plane): the centre plane i + 4,
+        // the incoming plane i + 8 with its phase parity, and the (m, u^{n-1})
+        // stage of output i with its parity
+        uint32_t s_c = (base + WR) % P.NS, s_n = (base + 2 * WR) % P.NS, p_n = ((base + 2 * WR) / P.NS) & 1;
+        uint32_t s_m = mbase % P.NSM, p_m = (mbase / P.NSM) & 1;
         for (int i = 0; i < zce; ++i) {
             // shift the queue and take plane z+4 (q = i + 8)
 #pragma unroll
             for (int d = 0; d < 2 * WR; ++d) q[d] = q[d + 1];
-            if (!wait_plane(i + 2 * WR)) {
+            if (!ptx::mbar_wait_warp(&full[s_n], p_n) || !ptx::mbar_wait_warp(&mfull[s_m], p_m)) {
                 timeout(P.status);
                 return;
             }
-            if (active) q[2 * WR] = read_q(i + 2 * WR);
-            if (!is_centre(i + 2 * WR)) release(i + 2 * WR);
-            const float4 mv = m0, pv = p0;
-            m0 = m1;
-            p0 = p1;
-            if (active && i + 2 < zce) {
-                m1 = load_g(m, z0 + i + 2);
-                p1 = load_g(uprev_out, z0 + i + 2);
+            if (active) q[2 * WR] = read4(ring + (size_t)s_n * P.stage_elems + P.xl + (int64_t)(row + WR) * P.pitch);
+            if (!is_centre(i + 2 * WR)) {
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&empty[s_n]);
             }
             if (active) {
-                const float* cp = stage_of(i + WR);  // centre plane, x origin applied
+                const float* ms = mring + (size_t)s_m * P.mstage_elems + P.xl + (int64_t)row * P.pitch;
+                const float4 mv = read4(ms);
+                const float4 pv = read4(ms + (size_t)P.TY * P.pitch);
+                const float* cp = ring + (size_t)s_c * P.stage_elems + P.xl;  // centre plane
                 const float* rc = cp + (int64_t)(row + WR) * P.pitch;
-                float c[4] = {q[WR].x, q[WR].y, q[WR].z, q[WR].w};
-                // distance sums S_j over the six neighbours at distance j
-                float S[WR][4];
+                const float c[4] = {q[WR].x, q[WR].y, q[WR].z, q[WR].w};
+                // running sums per point: lb = sum_k beta_k u_k, la = sum_{k != 0} alpha_k u_k
+                float lb[4], la[4];
 #pragma unroll
-                for (int j = 1; j <= WR; ++j) {
+                for (int e = 0; e < 4; ++e) {
+                    lb[e] = P.bc * c[e];
+                    la[e] = 0.f;
+                }
+                // coefficient of distance j by register selects (j may be a loop
+                // variable: indexing a local array with it would go to local memory)
+                auto cb = [&](int j) { return j == 1 ? bj[0] : (j == 2 ? bj[1] : (j == 3 ? bj[2] : bj[3])); };
+                auto ca = [&](int j) { return j == 1 ? aj[0] : (j == 2 ? aj[1] : (j == 3 ? aj[2] : aj[3])); };
+                auto add_pair = [&](int j, int e, float s2) {  // the two neighbours at distance j
+                    lb[e] = fmaf(cb(j), s2, lb[e]);
+                    if (!ALPHA0) la[e] = fmaf(ca(j), s2, la[e]);
+                };
+#pragma unroll
+                for (int j = 1; j <= WR; ++j) {  // z neighbours from the register queue
                     const float4 zl = q[WR - j], zh = q[WR + j];
-                    S[j - 1][0] = zl.x + zh.x;
-                    S[j - 1][1] = zl.y + zh.y;
-                    S[j - 1][2] = zl.z + zh.z;
-                    S[j - 1][3] = zl.w + zh.w;
+                    add_pair(j, 0, zl.x + zh.x);
+                    add_pair(j, 1, zl.y + zh.y);
+                    add_pair(j, 2, zl.z + zh.z);
+                    add_pair(j, 3, zl.w + zh.w);
                 }
                 if (full4) {
-#pragma unroll
-                    for (int j = 1; j <= WR; ++j) {
+#pragma unroll 2
+                    for (int j = 1; j <= WR; ++j) {  // y neighbours
                         const float4 yl = *reinterpret_cast<const float4*>(rc - j * P.pitch + x);
                         const float4 yh = *reinterpret_cast<const float4*>(rc + j * P.pitch + x);
-                        S[j - 1][0] += yl.x + yh.x;
-                        S[j - 1][1] += yl.y + yh.y;
-                        S[j - 1][2] += yl.z + yh.z;
-                        S[j - 1][3] += yl.w + yh.w;
+                        add_pair(j, 0, yl.x + yh.x);
+                        add_pair(j, 1, yl.y + yh.y);
+                        add_pair(j, 2, yl.z + yh.z);
+                        add_pair(j, 3, yl.w + yh.w);
                     }
-                    // x window: 4 left, the group, 4 right
-                    // vector loads only at multiples of 4 from the row start (16-byte
-                    // aligned); a periodic window that wraps is gathered element-wise
+                    // x window: 4 left, the group, 4 right.  Vector loads only
+                    // at multiples of 4 from the row start (16-byte aligned); a
+                    // periodic window that wraps is gathered element-wise.
                     float4 L, R;
                     if (PERIODIC && x == 0)
                         L = make_float4(rc[wrapw(x - 4, P.nx)], rc[wrapw(x - 3, P.nx)], rc[wrapw(x - 2, P.nx)],
@@ -246,8 +278,9 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
 #pragma unroll
                     for (int j = 1; j <= WR; ++j)
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) S[j - 1][e] += w[4 + e - j] + w[4 + e + j];
+                        for (int e = 0; e < 4; ++e) add_pair(j, e, w[4 + e - j] + w[4 + e + j]);
                 } else {
+#pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int64_t xe = x + e;
                         if (xe >= P.nx) break;
@@ -256,7 +289,8 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
                             const float yl = rc[xe - j * P.pitch], yh = rc[xe + j * P.pitch];
                             const int64_t xm = PERIODIC ? wrapw(xe - j, P.nx) : xe - j;
                             const int64_t xp = PERIODIC ? wrapw(xe + j, P.nx) : xe + j;
-                            S[j - 1][e] += yl + yh + rc[xm] + rc[xp];
+                            add_pair(j, e, yl + yh);
+                            add_pair(j, e, rc[xm] + rc[xp]);
                         }
                     }
                 }
@@ -264,20 +298,7 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
                 const float pp[4] = {pv.x, pv.y, pv.z, pv.w};
                 float o[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    float lap = P.bj[0] * S[0][e];
-                    lap = fmaf(P.bj[1], S[1][e], lap);
-                    lap = fmaf(P.bj[2], S[2][e], lap);
-                    lap = fmaf(P.bj[3], S[3][e], lap);
-                    lap = fmaf(P.bc, c[e], lap);                      // beta part: sum_k beta_k u_k
-                    float acc = fmaf(P.ac, c[e], -pp[e]);             // alpha part (centre only) - u^{n-1}
-                    float alo = P.aj[0] * S[0][e];
-                    alo = fmaf(P.aj[1], S[1][e], alo);
-                    alo = fmaf(P.aj[2], S[2][e], alo);
-                    alo = fmaf(P.aj[3], S[3][e], alo);
-                    acc += alo;
-                    o[e] = fmaf(mm[e], lap, acc);
-                }
+                for (int e = 0; e < 4; ++e) o[e] = fmaf(mm[e], lb[e], fmaf(P.ac, c[e], -pp[e]) + la[e]);
                 const int64_t z = z0 + i;
                 if (P.sz == z && P.sy == y0 + row && P.sx >= x && P.sx < x + 4) {
                     const float amp = (float)P.src_amp[P.step];
@@ -292,9 +313,23 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
                     for (int e = 0; e < 4 && x + e < P.nx; ++e) op[e] = o[e];
                 }
             }
-            release(i + WR);
+            __syncwarp();
+            if (lane == 0) {
+                ptx::mbar_arrive(&empty[s_c]);  // centre plane i + 4
+                ptx::mbar_arrive(&mempty[s_m]);
+            }
+            s_c = (s_c + 1 == (uint32_t)P.NS) ? 0 : s_c + 1;
+            if (++s_n == (uint32_t)P.NS) {
+                s_n = 0;
+                p_n ^= 1u;
+            }
+            if (++s_m == (uint32_t)P.NSM) {
+                s_m = 0;
+                p_m ^= 1u;
+            }
         }
         gq = base + zce + 2 * WR;
+        gm = mbase + zce;
     }
 }
 
@@ -311,18 +346,22 @@ int wave_sm_count()
 
 constexpr size_t W_SMEM = 210 * 1024;
 
-bool wave_cfg(const Geom& g, int* TY, int* ZC, int* NS, size_t* stage_bytes)
+bool wave_cfg(const Geom& g, int* TY, int* ZC, int* NS, int* NSM, size_t* stage_bytes, size_t* mstage_bytes)
 {
     if (g.esize != 4) return false;
     const int ngx = (int)((g.nx + 3) / 4);
-    int ty = std::min<int64_t>(g.ny, W_NC / std::max(1, ngx));
+    int ty = (int)std::min<int64_t>(g.ny, W_NC / std::max(1, ngx));
     if (ty < 1) return false;  // a row wider than 4 * 512 points
     for (; ty >= 1; --ty) {
         const size_t sb = ((size_t)(ty + 2 * WR) * g.pitch * 4 + 127) / 128 * 128;
-        if (sb * 8 + 128 <= W_SMEM) {
+        const size_t mb = ((size_t)2 * ty * g.pitch * 4 + 127) / 128 * 128;
+        // 5 u planes resident + 2 in flight; 2 (m, u^{n-1}) stages
+        if (sb * 7 + mb * 2 + 256 <= W_SMEM) {
             *TY = ty;
-            *NS = 8;
+            *NS = (int)std::min<size_t>(8, (W_SMEM - mb * 2 - 256) / sb);
+            *NSM = 2;
             *stage_bytes = sb;
+            *mstage_bytes = mb;
             break;
         }
     }
@@ -376,17 +415,17 @@ bool wave_supports(const FamilyDesc& d)
         if (d.alpha[k] != a[j] || (d.has_beta ? d.beta[k] : 0.0) != b[j]) return false;
     }
     if (!d.has_beta) return false;
-    int TY, ZC, NS;
-    size_t sb;
-    return wave_cfg(d.g, &TY, &ZC, &NS, &sb);
+    int TY, ZC, NS, NSM;
+    size_t sb, mb;
+    return wave_cfg(d.g, &TY, &ZC, &NS, &NSM, &sb, &mb);
 }
 
 cudaError_t launch_wave(const Family& f, const SweepArgs& a, cudaStream_t s)
 {
     const Geom& g = f.g;
-    int TY, ZC, NS;
-    size_t sb;
-    if (!wave_cfg(g, &TY, &ZC, &NS, &sb)) return cudaErrorNotSupported;
+    int TY, ZC, NS, NSM;
+    size_t sb, mb;
+    if (!wave_cfg(g, &TY, &ZC, &NS, &NSM, &sb, &mb)) return cudaErrorNotSupported;
     WaveParams P;
     std::memset(&P, 0, sizeof(P));
     P.nz = g.nz;
@@ -401,6 +440,8 @@ cudaError_t launch_wave(const Family& f, const SweepArgs& a, cudaStream_t s)
     P.TY = TY;
     P.ZC = ZC;
     P.NS = NS;
+    P.NSM = NSM;
+    P.mstage_elems = (uint32_t)(mb / 4);
     P.nyt = (int)((g.ny + TY - 1) / TY);
     P.nzc = (int)((g.nz + ZC - 1) / ZC);
     P.units = P.nyt * P.nzc;
@@ -423,20 +464,19 @@ cudaError_t launch_wave(const Family& f, const SweepArgs& a, cudaStream_t s)
         P.step = a.step;
     }
     P.status = a.status;
-    const size_t smem = (size_t)NS * sb + 2 * sizeof(uint64_t) * NS;
-    static bool attr[2] = {false, false};
-    const int pi = f.periodic ? 1 : 0;
-    if (!attr[pi]) {
-        cudaError_t e = cudaFuncSetAttribute(f.periodic ? k_wave<true> : k_wave<false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    const size_t smem = (size_t)NS * sb + (size_t)NSM * mb + 2 * sizeof(uint64_t) * (NS + NSM);
+    const bool alpha0 = P.aj[0] == 0.f && P.aj[1] == 0.f && P.aj[2] == 0.f && P.aj[3] == 0.f;
+    typedef void (*WFn)(const float*, float*, const float*, const WaveParams);
+    static const WFn table[2][2] = {{k_wave<false, false>, k_wave<false, true>}, {k_wave<true, false>, k_wave<true, true>}};
+    static bool attr[2][2] = {{false, false}, {false, false}};
+    const int pi = f.periodic ? 1 : 0, ai = alpha0 ? 1 : 0;
+    if (!attr[pi][ai]) {
+        cudaError_t e = cudaFuncSetAttribute(table[pi][ai], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
-        attr[pi] = true;
+        attr[pi][ai] = true;
     }
     const int grid = (int)std::min<int64_t>(P.units, wave_sm_count());
-    if (f.periodic)
-        k_wave<true><<<grid, W_THREADS, smem, s>>>((const float*)a.in, (float*)a.out, (const float*)a.kappa, P);
-    else
-        k_wave<false><<<grid, W_THREADS, smem, s>>>((const float*)a.in, (float*)a.out, (const float*)a.kappa, P);
+    table[pi][ai]<<<grid, W_THREADS, smem, s>>>((const float*)a.in, (float*)a.out, (const float*)a.kappa, P);
     return cudaGetLastError();
 }
 

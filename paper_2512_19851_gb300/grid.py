@@ -91,6 +91,12 @@ class Grid:
     def sync(self) -> None:
         abi.stencil_sync(self.h)
 
+    def tune(self, nsteps: int, stream=None) -> tuple:
+        """Autotune for nsteps-step calls (2D tile kernel); returns the configuration."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        abi.stencil_tune(self.h, nsteps, s)
+        return abi.stencil_tune_config(self.h)
+
     def reduce(self, a: torch.Tensor, b: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """(sum, sum of squares, max abs) of a - b over the interior, float64 on device."""
         out = torch.empty(3, dtype=torch.float64, device=self.device)

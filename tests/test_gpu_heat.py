@@ -209,3 +209,43 @@ def test_run_host_end_to_end():
         ref = oracle.sweep_const(h.u0, offs, w, True, 0.0, 12)
         assert rel_err(dst.numpy(), ref) <= (TOL64 if dtype == torch.float64 else TOL32)
         g.close()
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_2d_tile_kernel_fp32_temporal_blocking_and_tuning(periodic):
+    """2D grids run on the persistent tile kernel (k steps per shared-memory
+    pass for FP32): against the oracle, and the tuned configuration gives
+    bit-identical results to the default one (same FMA sequence per point)."""
+    from paper_2512_19851_gb300.grid import Grid
+    shape = (97, 203)
+    u0 = inputs.heat2d(shape=shape)
+    offs, w = five_point(0.2)
+    ref = oracle.sweep_const(u0, offs, w, periodic, 0.0, 37)
+    outs = []
+    for tune in (False, True):
+        g = Grid(shape, offs, w, periodic=periodic, dtype=torch.float32)
+        assert g.kernel == "tile2d_persistent"
+        g.set_field(u0)
+        if tune:
+            cfg = g.tune(37)
+            assert cfg[0] > 0 and cfg[3] >= 1
+        g.step(37)
+        g.sync()
+        outs.append(g.current().double().cpu().numpy())
+        g.close()
+    assert rel_err(outs[0], ref) <= TOL32
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_2d_box9_fp64_tuned_matches_oracle():
+    from paper_2512_19851_gb300.grid import Grid
+    b = inputs.batch2d(ngrids=1, lo=300, hi=400)
+    u0, wts = b.fields[0], b.weights[0]
+    ref = oracle.sweep_const(u0, inputs.OFFSETS_BOX9, wts, True, 0.0, 50)
+    g = Grid(u0.shape, inputs.OFFSETS_BOX9, wts, periodic=True, dtype=torch.float64)
+    g.set_field(u0)
+    g.tune(50)
+    g.step(50)
+    g.sync()
+    assert rel_err(g.current().cpu().numpy(), ref) <= TOL64
+    g.close()
