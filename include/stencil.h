@@ -35,7 +35,8 @@
  *   - Device buffers are BORROWED: the caller allocates and frees them and
  *     keeps them alive while a handle uses them.  The library allocates only
  *     its own scratch (status word, reduction partials, source table, batch
- *     tables, tuning copies) in create/bind/set/tune calls, never in a step.
+ *     tables, tuning copies) in bind/set/tune calls, and the host staging
+ *     buffer in the first stencil_run_host; never in a step.
  *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
  *     void*, NULL = legacy default stream) and is asynchronous, except
  *     stencil_sync() and the *_tune() calls, which synchronise that stream.
@@ -195,9 +196,12 @@ st_status stencil_tune_config(st_grid_t g, int* cfg);
 /*
  * End-to-end form of stencil_step for callers whose data is on the host:
  * copies host_u0 (dense interior, C order, the grid's dtype) into the current
- * level, runs nsteps, copies the newest level's interior to host_uT.  Both
- * copies are enqueued on `stream` (pinned host memory makes them
- * asynchronous); the call returns after enqueueing.  One time level only.
+ * level, runs nsteps, copies the newest level's interior to host_uT.  Each
+ * direction is one contiguous copy into a dense device staging buffer plus a
+ * device (un)pack kernel into the padded layout; the first call on a handle
+ * allocates that buffer (interior size), later calls reuse it.  Everything is
+ * enqueued on `stream` (pinned host memory makes the copies asynchronous);
+ * the call returns after enqueueing.  One time level only.
  */
 st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* host_uT,
                            void* stream);

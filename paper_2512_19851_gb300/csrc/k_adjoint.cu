@@ -37,7 +37,7 @@ namespace st {
 
 namespace {
 
-constexpr int A_CW = 8;  // consumer warps
+constexpr int A_CW = 16;  // consumer warps
 constexpr int A_THREADS = (A_CW + 1) * 32;
 constexpr int A_NC = A_CW * 32;
 constexpr int A_KMAX = 2;
@@ -64,8 +64,10 @@ template <typename T>
 struct AV;
 template <>
 struct AV<float> {
-    static constexpr int N = 4;
-    typedef float4 type;
+    // two points per thread: twice the threads of four-wide groups for the
+    // same tile, for latency hiding, at half the registers per thread
+    static constexpr int N = 2;
+    typedef float2 type;
 };
 template <>
 struct AV<double> {
@@ -77,30 +79,16 @@ template <typename T>
 __device__ __forceinline__ void ald(const T* p, T (&v)[AV<T>::N])
 {
     typename AV<T>::type t = *reinterpret_cast<const typename AV<T>::type*>(p);
-    if constexpr (AV<T>::N == 4) {
-        v[0] = t.x;
-        v[1] = t.y;
-        v[2] = t.z;
-        v[3] = t.w;
-    } else {
-        v[0] = t.x;
-        v[1] = t.y;
-    }
+    v[0] = t.x;
+    v[1] = t.y;
 }
 
 template <typename T>
 __device__ __forceinline__ void ast(T* p, const T (&v)[AV<T>::N])
 {
     typename AV<T>::type t;
-    if constexpr (AV<T>::N == 4) {
-        t.x = v[0];
-        t.y = v[1];
-        t.z = v[2];
-        t.w = v[3];
-    } else {
-        t.x = v[0];
-        t.y = v[1];
-    }
+    t.x = v[0];
+    t.y = v[1];
     *reinterpret_cast<typename AV<T>::type*>(p) = t;
 }
 
@@ -487,17 +475,15 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                         const float* hs = reinterpret_cast<const float*>(gst);
                         const float* ls = hs + (size_t)P.TY * P.pitch;
                         if (x + VN <= P.nx) {
-                            float4 h = *reinterpret_cast<const float4*>(hs);
-                            float4 l = *reinterpret_cast<const float4*>(ls);
+                            float2 h = *reinterpret_cast<const float2*>(hs);
+                            float2 l = *reinterpret_cast<const float2*>(ls);
 #pragma unroll
                             for (int s = 1; s <= K; ++s) {
                                 ff_add(h.x, l.x, (float)dl[s - 1][K - s][0]);
                                 ff_add(h.y, l.y, (float)dl[s - 1][K - s][1]);
-                                ff_add(h.z, l.z, (float)dl[s - 1][K - s][2]);
-                                ff_add(h.w, l.w, (float)dl[s - 1][K - s][3]);
                             }
-                            *reinterpret_cast<float4*>(ghi + off) = h;
-                            *reinterpret_cast<float4*>(glo + off) = l;
+                            *reinterpret_cast<float2*>(ghi + off) = h;
+                            *reinterpret_cast<float2*>(glo + off) = l;
                         } else {
                             for (int e = 0; e < VN && x + e < P.nx; ++e) {
                                 float h = hs[e], l = ls[e];
@@ -573,7 +559,7 @@ struct AdjCfg {
 
 bool adj_cfg(const Geom& g, int kmax, AdjCfg* c)
 {
-    const int VN = 16 / g.esize;
+    const int VN = 2;  // AV<T>::N for both types
     const int ngx = (int)((g.nx + VN - 1) / VN);
     const int TY = (int)std::min<int64_t>(std::min(16, A_NC / std::max(1, ngx)), g.ny);
     if (TY < 1) return false;

@@ -308,6 +308,24 @@ k_reduce_final(const double* __restrict__ partials, int nblocks, double* __restr
     }
 }
 
+// Dense interior <-> padded layout (dir 0: dense -> padded, 1: padded -> dense).
+// One block per interior row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pack(T* __restrict__ dense, T* __restrict__ padded, Geom g, int dir)
+{
+    const int64_t rows = g.nz * g.ny;
+    const uint32_t ny32 = (uint32_t)g.ny;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const uint32_t z = (uint32_t)row / ny32, y = (uint32_t)row - z * ny32;
+        T* pr = padded + g.origin + (int64_t)z * g.plane + (int64_t)y * g.pitch;
+        T* dr = dense + row * g.nx;
+        if (dir == 0)
+            for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x) pr[x] = dr[x];
+        else
+            for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x) dr[x] = pr[x];
+    }
+}
+
 dim3 point_grid(const GenParams& P)
 {
     return dim3((unsigned)((P.nx + 31) / 32), (unsigned)((P.ny + 7) / 8), (unsigned)P.nz);
@@ -341,6 +359,17 @@ cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_i
     else
         k_adjoint_generic<float><<<grid, block, 0, s>>>((const float*)u_t, (const float*)lam_in,
                                                         (float*)lam_out, (const float*)kappa, gk, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int dir, cudaStream_t s)
+{
+    const int64_t rows = g.nz * g.ny;
+    const unsigned blocks = (unsigned)(rows < 65535 * 8 ? rows : 65535 * 8);
+    if (esize == 8)
+        k_pack<double><<<blocks, 256, 0, s>>>((double*)dense, (double*)padded, g, dir);
+    else
+        k_pack<float><<<blocks, 256, 0, s>>>((float*)dense, (float*)padded, g, dir);
     return cudaGetLastError();
 }
 
