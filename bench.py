@@ -380,11 +380,29 @@ def extra_configs(dev, hbm_peak):
     bt = Batch(b.shapes, inputs.OFFSETS_BOX9, b.weights, periodic=True, dtype=torch.float32, device=dev)
     bt.set_fields(b.fields)
     npts = int((b.shapes[:, 0] * b.shapes[:, 1]).sum())
-    del b
     cfg = bt.tune(50, s)
     t = _time(lambda: bt.step(50, s), 3, s)
     out["batch2d_f32"] = {"glups": npts * 50 / t / 1e9, "ms_per_run": t * 1e3,
                           "nominal_hbm_frac": 8 * npts * 50 / t / 1e9 / hbm_peak, "config": list(cfg)}
+    # the comparison the workload asks for: 512 separate plain FP64 launches
+    # per step (one-thread-per-point kernel, 25,600 launches in one graph)
+    bp = Batch(b.shapes, inputs.OFFSETS_BOX9, b.weights, periodic=True, dtype=torch.float64, generic=True, device=dev)
+    bp.set_fields(b.fields)
+    t64 = _time(lambda: bp.step(50, s), 1, s)
+    # accuracy of one 50-step FP32 batched run against the FP64 plain run
+    bt.set_fields(b.fields)
+    bp.set_fields(b.fields)
+    bt.step(50, s)
+    bp.step(50, s)
+    torch.cuda.synchronize()
+    err = 0.0
+    for i in range(len(b.fields)):
+        a32 = bt.current(i).double()
+        a64 = bp.current(i)
+        err = max(err, float((a32 - a64).abs().max() / a64.abs().max()))
+    out["batch2d_f32"].update({"plain_f64_ms_per_run": t64 * 1e3, "speedup_vs_plain_f64": t64 / t,
+                               "max_normwise_err_vs_plain_f64": err})
+    bp.close()
     bt.close()
     torch.cuda.empty_cache()
     return out
@@ -489,7 +507,7 @@ def run_profile(case: str, launches: int = 3):
         for _ in range(2 + launches):
             abi.stencil_step(g.h, 1, s)
     elif case in ("varcoef_fwd", "varcoef_adj"):
-        n = 384
+        n = 256
         v = inputs.varcoef3d(n=n)
         offs, alpha, beta = stencils.varcoef7()
         g = Grid((n,) * 3, offs, alpha, beta, dtype=torch.float32)

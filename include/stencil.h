@@ -275,6 +275,8 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int ckpt_every, void* works
  *     lambda_t[q] = sum_k w_k(q - o_k) lambda_{t+1}[q - o_k],
  * over the points q - o_k that are interior (wrapped when periodic); ghost
  * cells are boundary data, not variables.  The current level is unchanged.
+ * workspace, lambda, lambda_tmp and grad_coeff are 16-byte aligned
+ * (ST_ERR_ARG otherwise).
  */
 st_status stencil_adjoint(st_grid_t g, int nsteps, int ckpt_every, const void* workspace,
                           void* lambda, void* lambda_tmp, double* grad_coeff, void* stream);

@@ -625,17 +625,13 @@ st_status stencil_residual(st_grid_t g, const void* u, const void* target, void*
 
 static size_t state_bytes(st_grid_t g) { return (size_t)((g->g.elems * g->g.esize + 255) / 256 * 256); }
 
-// FP32 grids on the fused adjoint accumulate the coefficient gradient in a
-// float-float scratch (two float fields) kept at the end of the workspace.
-static size_t ff_field_bytes(st_grid_t g) { return (size_t)((g->g.elems * 4 + 255) / 256 * 256); }
-static bool uses_ff(st_grid_t g) { return g->g.esize == 4 && g->has_beta && star3d_adjoint_fuse(g->fam) > 0; }
 
 st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* bytes)
 {
     if (!g || !bytes) return fail(ST_ERR_ARG, "stencil_adjoint_workspace: NULL argument");
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_adjoint_workspace: nsteps >= 0, ckpt_every >= 1");
     const int64_t nck = (nsteps + m - 1) / m;
-    *bytes = state_bytes(g) * (size_t)(nck + (m - 1)) + (uses_ff(g) ? 2 * ff_field_bytes(g) : 0);
+    *bytes = state_bytes(g) * (size_t)(nck + (m - 1));
     return ST_OK;
 }
 
@@ -672,6 +668,8 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_adjoint: nsteps >= 0, ckpt_every >= 1");
     if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: one time level only");
     if (lambda == lambda_tmp) return fail(ST_ERR_ALIAS, "stencil_adjoint: lambda and lambda_tmp alias");
+    if ((((uintptr_t)ws) | ((uintptr_t)lambda) | ((uintptr_t)lambda_tmp) | ((uintptr_t)grad)) & 15u)
+        return fail(ST_ERR_ARG, "stencil_adjoint: buffers must be 16-byte aligned");
     if (grad && !g->has_beta) return fail(ST_ERR_ARG, "stencil_adjoint: grad_coeff needs per-cell weights");
     if (g->has_beta && !g->buf[ST_SLOT_COEFF]) return fail(ST_ERR_STATE, "stencil_adjoint: ST_SLOT_COEFF not bound");
     st_status rc = ensure_scratch(g);
@@ -695,14 +693,6 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     if (g->bc == ST_DIRICHLET)
         for (int j = 1; j < m; ++j) ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, state(0, j), g->g, g->bc_value, s));
     const int fuse = star3d_adjoint_fuse(g->fam);  // steps per optimised transpose launch (0: generic)
-    float* ghi = nullptr;
-    float* glo = nullptr;
-    const bool ff = grad && uses_ff(g);
-    if (ff) {
-        ghi = reinterpret_cast<float*>(base + (size_t)(nck + m - 1) * sb);
-        glo = reinterpret_cast<float*>(reinterpret_cast<char*>(ghi) + ff_field_bytes(g));
-        ST_CUDA_TRY(cudaMemsetAsync(ghi, 0, 2 * ff_field_bytes(g), s));
-    }
     void* lin = lambda;
     void* lout = lambda_tmp;
     for (int64_t c = nck - 1; c >= 0; --c) {
@@ -721,9 +711,7 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
             a.lam_in = lin;
             a.lam_out = lout;
             a.kappa = g->has_beta ? g->buf[ST_SLOT_COEFF] : nullptr;
-            a.gk = ff ? nullptr : grad;
-            a.ghi = ghi;
-            a.glo = glo;
+            a.gk = grad;
             a.steps = k;
             a.status = g->d_status;
             ST_CUDA_TRY(launch_family_adjoint(g->fam, a, s));
@@ -731,7 +719,6 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
             j -= k;
         }
     }
-    if (ff) ST_CUDA_TRY(launch_fold_ff(ghi, glo, grad, g->g, s));
     if (lin != lambda)
         ST_CUDA_TRY(cudaMemcpyAsync(lambda, lin, (size_t)g->g.elems * g->g.esize, cudaMemcpyDeviceToDevice, s));
     return ST_OK;

@@ -68,9 +68,7 @@ struct AdjointArgs {
     const void* lam_in;  // lambda_{t+1}
     void* lam_out;       // lambda_{t+1-steps}
     const void* kappa;
-    double* gk;          // FP64 gradient (generic path and FP64 grids)
-    float* ghi;          // float-float gradient scratch (FP32 grids, optimised path)
-    float* glo;
+    double* gk;          // FP64 gradient accumulator (NULL: no gradient)
     int steps;           // transpose steps fused in this launch (1 or 2)
     int* status;
 };
@@ -83,7 +81,6 @@ cudaError_t launch_family_adjoint(const Family& f, const AdjointArgs& a, cudaStr
 cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_star3d_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
 int star3d_adjoint_fuse(const Family& f);
-cudaError_t launch_fold_ff(const float* hi, const float* lo, double* grad, const Geom& g, cudaStream_t s);
 bool star3d_supports(const FamilyDesc& d, int* variant, const char** name);
 cudaError_t launch_tile2d(const Family& f, const SweepArgs& a, cudaStream_t s);
 bool wave_supports(const FamilyDesc& d);

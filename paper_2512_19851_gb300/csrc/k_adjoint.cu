@@ -1,33 +1,44 @@
-// Transpose (adjoint) sweep of the per-cell 7-point operator with K steps
-// fused per pass, plus the coefficient gradient.
+// Transpose (adjoint) sweep of the per-cell 7-point operator with K = 1 or 2
+// steps fused per pass, plus the coefficient gradient (the backward pass of
+// the variable-coefficient diffusion, Sec. 4 of the paper's stencil model
+// differentiated by hand).
 //
 // Operator (symmetric star, one coefficient field):
-//   w_centre(p) = ac + bc kappa_p,  w_neighbour(p) = an + bn kappa_p
-// Transpose step (lambda_in = lambda_{t+1} -> lambda_out = lambda_t):
-//   lambda_out[q] = w_c(q) lambda_in[q] + sum_{p nbr of q} w_n(p) lambda_in[p]
-// Gradient term of that step:
-//   g[q] = lambda_in[q] * (bc u_t[q] + bn sum_{p nbr of q} u_t[p])
+//   w_c(p) = ac + bc kappa_p,  w_n(p) = an + bn kappa_p for all six neighbours.
+// With mu = w_n * lambda_in, one transposed step lambda_in -> lambda_out is
+//   lambda_out[q] = w_c(q) lambda_in[q] + sum over the six neighbours p of q of mu[p]
+// (a constant-weight 7-point sum of mu plus a pointwise centre term), and the
+// gradient term of that step is
+//   g[q] += lambda_in[q] * (bc u_t[q] + bn * sum over the neighbours of u_t).
 //
-// Design (HBM-bound; K levels per pass cut the lambda / kappa / gradient
-// traffic by K):
-//  * CTA tile = TY full rows, streamed through a chunk of z planes; staged per
-//    input plane by 1D bulk copies into an mbarrier ring: lambda_{t+1} and
-//    kappa with a K-row y halo, and the K states u_t .. u_{t-K+1} with a 1-row
-//    halo.  For a Dirichlet boundary the copies are clipped to the ghost shell:
-//    positions farther out are never read (see below).
-//  * Time-skewed pipeline: at iteration j staged plane j has arrived and level
-//    s (= lambda_{t+1-s}) is computed at plane j - s from level s-1 at planes
-//    j-s-1 .. j-s+1; intermediate levels live in 3-plane shared rings.  Level
-//    s is computed on TY + 2(K-s) rows (the shrinking halo).  Outside the
-//    interior (Dirichlet) every level is 0 without reading anything: ghosts
-//    are boundary data, not variables.  So no value more than one cell
-//    outside the interior is ever read.
-//  * The K gradient terms of a point arrive at K consecutive iterations; each
-//    thread owns fixed interior points and sums them in a register ring, then
-//    adds them to the gradient once per pass.  FP32 grids accumulate into a
-//    float-float (hi, lo) scratch with error-free additions (the FP64 pipe of
-//    this GPU runs at 1/64 of FP32); FP64 grids accumulate in FP64.
+// Design (HBM-bound; two fused steps halve the lambda, kappa and gradient
+// traffic per step):
+//  * A CTA owns TY full rows and streams them through a chunk of z planes.  A
+//    producer warp stages, per plane, lambda and kappa with a K-row y halo and
+//    the states u_t (and u_{t-1}, one plane behind) with a 1-row halo into a
+//    ring of NS stages by 1D bulk copies completing on mbarriers.  Only two
+//    stages are read at a time (the centre plane and the plane above); the
+//    rest are in flight.
+//  * Consumer threads own fixed tasks: a pair of rows at one 16-byte x group.
+//    The plane below lives in registers (z reuse), the pair shares its inner
+//    y neighbours, x edges come from the neighbouring lanes by shuffles (from
+//    shared memory at warp and row ends).
+//  * Time skew (K = 2): at iteration j stage j has arrived, level 1 computes
+//    the plane of stage j - 1 and level 2 the plane below it.  Level 1 runs on
+//    the tile rows plus one halo row on each side (computed by halo warps) and
+//    publishes its mu in a 3-plane shared ring; level 2 reads the ring for its
+//    outer y neighbours and keeps everything else in registers.
+//  * Outside the interior (Dirichlet) every level is 0 by selection, never by
+//    arithmetic on ghost data: ghosts are boundary data, not variables.
+//  * Each fused level evaluates exactly the expressions of a single-step pass
+//    in the same order and adds its gradient term to the FP64 gradient as
+//    soon as it is computed, by reductions performed at L2 (the SMs never wait
+//    on the accumulator).  Level 1 of a plane runs one iteration before level
+//    2 of the same plane, so every point sums its terms in step order and a
+//    fused pass rounds exactly like K single-step passes.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "families.cuh"
@@ -37,25 +48,21 @@ namespace st {
 
 namespace {
 
-constexpr int A_CW = 16;  // consumer warps
-constexpr int A_THREADS = (A_CW + 1) * 32;
-constexpr int A_NC = A_CW * 32;
-constexpr int A_KMAX = 2;
-// Slots per intermediate ring: level s+1 reads planes pq-1..pq+1 of level s
-// while the next iteration's level s writes plane pq+2; with four slots those
-// never share a slot, so one consumer barrier per iteration (between the
-// levels) suffices.
-constexpr int LSLOTS = 4;
+// At most 12 warps per block (3 per SM sub-partition) leave 168 registers a
+// thread for the carried planes.
+constexpr int A_MAXCW = 11;                     // consumer warps at most
+constexpr int A_BLOCK = (A_MAXCW + 1) * 32;     // + the producer warp
+constexpr int A_RING = 3;                       // planes in the level-1 mu ring
 
 struct AdjParams {
     int64_t nz, ny, nx, pitch, plane, origin;
     int rz, r, xl;
-    int TY, ZC, NS;
+    int TY, NS, CW;                 // rows per tile, stages, consumer warps
     int nyt, nzc, units;
-    uint32_t stage_elems;                 // per staged plane
-    uint32_t lam_off, kap_off, u_off[A_KMAX];  // element offsets inside a stage
-    uint32_t g_off;                       // gradient accumulator tile (owned planes only)
-    uint32_t ring_elems;                  // one plane of an intermediate level ring
+    int ngx, npair, pair_warps;     // row-pair tasks fill warps [0, pair_warps); halo row tasks the rest
+    uint32_t stage_elems, kap_off, ua_off, ub_off;  // lambda at offset 0 of a stage
+    uint32_t ring_elems;            // one plane of the mu ring: TY + 2 rows
+    int grad;                       // gradient requested
     double ac, bc, an, bn;
     int* status;
 };
@@ -64,10 +71,8 @@ template <typename T>
 struct AV;
 template <>
 struct AV<float> {
-    // two points per thread: twice the threads of four-wide groups for the
-    // same tile, for latency hiding, at half the registers per thread
-    static constexpr int N = 2;
-    typedef float2 type;
+    static constexpr int N = 4;
+    typedef float4 type;
 };
 template <>
 struct AV<double> {
@@ -76,19 +81,33 @@ struct AV<double> {
 };
 
 template <typename T>
-__device__ __forceinline__ void ald(const T* p, T (&v)[AV<T>::N])
+__device__ __forceinline__ void vld(const T* p, T (&v)[AV<T>::N])
 {
-    typename AV<T>::type t = *reinterpret_cast<const typename AV<T>::type*>(p);
-    v[0] = t.x;
-    v[1] = t.y;
+    const typename AV<T>::type t = *reinterpret_cast<const typename AV<T>::type*>(p);
+    if constexpr (AV<T>::N == 4) {
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    } else {
+        v[0] = t.x;
+        v[1] = t.y;
+    }
 }
 
 template <typename T>
-__device__ __forceinline__ void ast(T* p, const T (&v)[AV<T>::N])
+__device__ __forceinline__ void vst(T* p, const T (&v)[AV<T>::N])
 {
     typename AV<T>::type t;
-    t.x = v[0];
-    t.y = v[1];
+    if constexpr (AV<T>::N == 4) {
+        t.x = v[0];
+        t.y = v[1];
+        t.z = v[2];
+        t.w = v[3];
+    } else {
+        t.x = v[0];
+        t.y = v[1];
+    }
     *reinterpret_cast<typename AV<T>::type*>(p) = t;
 }
 
@@ -100,127 +119,169 @@ __device__ __forceinline__ void atimeout(int* status)
     if (status) atomicCAS(status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
 }
 
-// Barrier among the consumer warps only (the producer warp has left the
-// block's main loop, so __syncthreads would wait for it).
-__device__ __forceinline__ void consumer_bar()
+// Per-thread constants of the x group a task owns.
+struct XCtx {
+    int x;        // first column of the group
+    int cl, cr;   // columns of the left neighbour of element 0 and the right one of element VN-1
+    int nx;
+    bool fixl, fixr;  // that neighbour is not held by the adjacent lane
+    bool wig;         // periodic row end inside the group: element nx-1-x wraps to column 0
+    bool xfull;       // the whole group is interior
+};
+
+// Neighbour sum of one row of values v in the fixed order
+//   z-1, y-1, y+1, x-1, x+1, z+1
+// shared by every level and every pass.  `left`/`right` are the values at
+// columns X.cl / X.cr when X.fixl / X.fixr; otherwise they come from the
+// adjacent lanes.  All lanes of the warp must call it.
+template <typename T>
+__device__ __forceinline__ void nsum(const XCtx& X, const T (&zm)[AV<T>::N], const T (&ym)[AV<T>::N],
+                                     const T (&v)[AV<T>::N], const T (&yp)[AV<T>::N], const T (&zp)[AV<T>::N],
+                                     T left, T right, T (&s)[AV<T>::N])
 {
-    asm volatile("bar.sync 1, %0;" ::"r"(A_NC) : "memory");
+    constexpr int VN = AV<T>::N;
+    const T l = __shfl_up_sync(0xffffffffu, v[VN - 1], 1);
+    const T r = __shfl_down_sync(0xffffffffu, v[0], 1);
+    left = X.fixl ? left : l;
+    right = X.fixr ? right : r;
+#pragma unroll
+    for (int e = 0; e < VN; ++e) {
+        const T xm = e == 0 ? left : v[e - 1];
+        T xp = e == VN - 1 ? right : v[e + 1];
+        if (X.wig && X.x + e + 1 == X.nx) xp = right;
+        s[e] = ((((zm[e] + ym[e]) + yp[e]) + xm) + xp) + zp[e];
+    }
 }
 
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float x)
+// Add one step's gradient terms of a row group to the FP64 gradient.  The
+// additions are fire-and-forget reductions performed at L2 (the thread never
+// waits on them); a point's terms all come from one thread, in step order, and
+// same-thread atomics on one address take effect in program order, so every
+// point sums its terms in step order, whatever the pass structure.
+template <typename T>
+__device__ __forceinline__ void add_grad(const XCtx& X, int64_t off, double* __restrict__ g64, const T (&t)[AV<T>::N])
 {
-    const float s = hi + x;
-    const float bb = s - hi;
-    const float e = (hi - (s - bb)) + (x - bb);
-    hi = s;
-    lo += e;
+    constexpr int VN = AV<T>::N;
+#pragma unroll
+    for (int e = 0; e < VN; ++e)
+        if (X.xfull || X.x + e < X.nx) atomicAdd(g64 + off + e, (double)t[e]);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_row(const XCtx& X, T* p, const T (&v)[AV<T>::N])
+{
+    if (X.xfull) {
+        vst(p, v);
+    } else {
+        for (int e = 0; e < AV<T>::N && X.x + e < X.nx; ++e) p[e] = v[e];  // columns past nx stay untouched
+    }
 }
 
 template <typename T, int K, bool PERIODIC>
-__global__ void __launch_bounds__(A_THREADS, 1)
+__global__ void __launch_bounds__(A_BLOCK, 1)
 k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __restrict__ kappa,
-          const T* __restrict__ ua, const T* __restrict__ ub, double* __restrict__ g64, float* __restrict__ ghi,
-          float* __restrict__ glo, const __grid_constant__ AdjParams P)
+          const T* __restrict__ ua, const T* __restrict__ ub, double* __restrict__ g64,
+          const __grid_constant__ AdjParams P)
 {
     constexpr int VN = AV<T>::N;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T* ring = reinterpret_cast<T*>(smem_raw);
-    T* lvl = ring + (size_t)P.NS * P.stage_elems;  // (K-1) rings of LSLOTS planes
-    uint64_t* full = reinterpret_cast<uint64_t*>(lvl + (size_t)(K - 1) * LSLOTS * P.ring_elems);
+    T* stg = reinterpret_cast<T*>(smem_raw);
+    T* mring = stg + (size_t)P.NS * P.stage_elems;
+    uint64_t* full = reinterpret_cast<uint64_t*>(mring + (K == 2 ? (size_t)A_RING * P.ring_elems : 0));
     uint64_t* empty = full + P.NS;
+    uint64_t* rfull = empty + P.NS;    // K == 2: a ring plane is written (one arrival per consumer warp)
+    uint64_t* rempty = rfull + A_RING;  // K == 2: a ring plane is read
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.NS; ++s) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&empty[s], A_CW);
+            ptx::mbar_init(&empty[s], P.CW);
         }
+        if (K == 2)
+            for (int s = 0; s < A_RING; ++s) {
+                ptx::mbar_init(&rfull[s], P.CW);
+                ptx::mbar_init(&rempty[s], P.CW);
+            }
         ptx::fence_barrier_init();
     }
-    // zero the intermediate rings once (their ghost columns stay 0)
-    for (size_t i = threadIdx.x; i < (size_t)(K - 1) * LSLOTS * P.ring_elems; i += blockDim.x) lvl[i] = T(0);
+    // the ring's ghost columns stay 0 for good (only interior columns are written)
+    if (K == 2)
+        for (size_t i = threadIdx.x; i < (size_t)A_RING * P.ring_elems; i += blockDim.x) mring[i] = T(0);
     __syncthreads();
     const uint32_t rowb = (uint32_t)(P.pitch * sizeof(T));
+    const bool grad = P.grad != 0;
 
-    if (warp == A_CW) {
+    if (warp == P.CW) {
         // ------------------------------------------------------------ producer
         if (lane != 0) return;
         uint32_t gq = 0;
         for (int un = blockIdx.x; un < P.units; un += gridDim.x) {
             const int yt = un % P.nyt, zc = un / P.nyt;
-            const int64_t y0 = (int64_t)yt * P.TY, z0 = (int64_t)zc * P.ZC;
+            const int64_t y0 = (int64_t)yt * P.TY;
             const int tye = (int)amin(P.TY, P.ny - y0);
-            const int zce = (int)amin(P.ZC, P.nz - z0);
-            for (int q = 0; q < zce + 2 * K; ++q, ++gq) {
+            const int64_t z0 = (int64_t)zc * P.nz / P.nzc, z1 = (int64_t)(zc + 1) * P.nz / P.nzc;
+            const int nq = (int)(z1 - z0) + 2 * K;
+            // rows [y0 - h, y0 + tye + h): periodic wraps, Dirichlet clips to the ghost shell
+            auto rows_of = [&](int h, int64_t& lo, int64_t& hi) {
+                lo = y0 - h;
+                hi = y0 + tye + h;
+                if (!PERIODIC) {
+                    lo = amax(lo, -P.r);
+                    hi = amin(hi, P.ny + P.r);
+                }
+            };
+            auto plane_ok = [&](int64_t z) { return PERIODIC || (z >= -P.rz && z < P.nz + P.rz); };
+            auto nbytes = [&](int h) {
+                int64_t lo, hi;
+                rows_of(h, lo, hi);
+                return (uint32_t)(hi - lo) * rowb;
+            };
+            for (int q = 0; q < nq; ++q, ++gq) {
                 const uint32_t s = gq % P.NS, k = gq / P.NS;
                 if (k > 0 && !ptx::mbar_wait(&empty[s], (k - 1) & 1)) {
                     atimeout(P.status);
                     return;
                 }
-                const int64_t zi = z0 - K + q;  // interior plane index of this stage
-                T* dst = ring + (size_t)s * P.stage_elems;
-                // rows [y0 - h, y0 + tye + h): periodic wraps, Dirichlet clips to the ghost shell
-                const bool zin = PERIODIC || (zi >= -P.rz && zi < P.nz + P.rz);
-                auto rows_of = [&](int h, int64_t& lo, int64_t& hi) {
-                    lo = y0 - h;
-                    hi = y0 + tye + h;
-                    if (!PERIODIC) {
-                        lo = amax(lo, -P.r);
-                        hi = amin(hi, P.ny + P.r);
-                    }
-                };
+                const int64_t zi = z0 - K + q;  // plane of lambda, kappa, u_t in this stage
+                const bool okz = plane_ok(zi);
+                const bool okb = K == 2 && grad && plane_ok(zi - 1);  // u_{t-1} one plane behind
                 uint32_t bytes = 0;
-                // the gradient accumulators of the planes this unit owns
-                const bool gtile = (g64 != nullptr || ghi != nullptr) && q >= K && q < zce + K;
-                const uint32_t growb = (uint32_t)(P.pitch * 8);  // one double or two floats per point
-                if (zin) {
-                    int64_t lo, hi;
-                    rows_of(K, lo, hi);
-                    bytes += 2u * (uint32_t)(hi - lo) * rowb;
-                    rows_of(1, lo, hi);
-                    bytes += (uint32_t)K * (uint32_t)(hi - lo) * rowb;
-                }
-                if (gtile) bytes += (uint32_t)tye * growb;
+                if (okz) bytes += 2u * nbytes(K) + (grad ? nbytes(1) : 0u);
+                if (okb) bytes += nbytes(1);
                 ptx::mbar_arrive_expect_tx(&full[s], bytes);
-                if (gtile) {
-                    const int64_t goff = P.origin + zi * P.plane + y0 * P.pitch - P.xl;  // row start
-                    if (sizeof(T) == 8) {
-                        ptx::bulk_g2s(dst + P.g_off, g64 + goff, (uint32_t)tye * growb / 1, &full[s]);
-                    } else {
-                        float* gd = reinterpret_cast<float*>(dst + P.g_off);
-                        ptx::bulk_g2s(gd, ghi + goff, (uint32_t)tye * rowb, &full[s]);
-                        ptx::bulk_g2s(gd + (size_t)P.TY * P.pitch, glo + goff, (uint32_t)tye * rowb, &full[s]);
-                    }
-                }
-                if (!zin) continue;
-                auto copy = [&](const T* a, T* d, int h) {
+                T* dst = stg + (size_t)s * P.stage_elems;
+                auto copy = [&](const T* a, T* d, int h, int64_t z) {
                     int64_t lo, hi;
                     rows_of(h, lo, hi);
                     T* dd = d + (size_t)(lo - (y0 - h)) * P.pitch;
                     if (!PERIODIC) {
-                        const T* src = a + (zi + P.rz) * P.plane + (lo + P.r) * P.pitch;
+                        const T* src = a + (z + P.rz) * P.plane + (lo + P.r) * P.pitch;
                         ptx::bulk_g2s(dd, src, (uint32_t)(hi - lo) * rowb, &full[s]);
                     } else {
-                        const int64_t zw = ((zi % P.nz) + P.nz) % P.nz;
+                        const int64_t zw = ((z % P.nz) + P.nz) % P.nz;
                         const T* pl = a + (zw + P.rz) * P.plane + (int64_t)P.r * P.pitch;
-                        int j = 0;
                         const int nrows = (int)(hi - lo);
-                        while (j < nrows) {
-                            int64_t row = lo + j;
+                        int jr = 0;
+                        while (jr < nrows) {
+                            int64_t row = lo + jr;
                             row = ((row % P.ny) + P.ny) % P.ny;
-                            const int run = (int)amin(nrows - j, P.ny - row);
-                            ptx::bulk_g2s(dd + (size_t)j * P.pitch, pl + row * P.pitch, (uint32_t)run * rowb,
+                            const int run = (int)amin(nrows - jr, P.ny - row);
+                            ptx::bulk_g2s(dd + (size_t)jr * P.pitch, pl + row * P.pitch, (uint32_t)run * rowb,
                                           &full[s]);
-                            j += run;
+                            jr += run;
                         }
                     }
                 };
-                copy(lam_in, dst + P.lam_off, K);
-                copy(kappa, dst + P.kap_off, K);
-                copy(ua, dst + P.u_off[0], 1);
-                if (K > 1) copy(ub, dst + P.u_off[1], 1);
+                if (okz) {
+                    copy(lam_in, dst, K, zi);
+                    copy(kappa, dst + P.kap_off, K, zi);
+                    if (grad) copy(ua, dst + P.ua_off, 1, zi);
+                }
+                if (okb) copy(ub, dst + P.ub_off, 1, zi - 1);
             }
         }
+        // wait until every issued copy has landed before leaving
         for (uint32_t d = 0; d < (uint32_t)P.NS && d < gq; ++d) {
             const uint32_t g = gq - 1 - d;
             if (!ptx::mbar_wait(&full[g % P.NS], (g / P.NS) & 1)) atimeout(P.status);
@@ -229,313 +290,365 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
     }
 
     // ---------------------------------------------------------------- consumers
-    const int ct = threadIdx.x;
-    const int ngx = (int)((P.nx + VN - 1) / VN);
+    const int ngx = P.ngx, pitch = (int)P.pitch;
+    const bool pairw = warp < P.pair_warps;
+    int gx = 0, rp = 0;
+    bool act = false;
+    if (pairw) {
+        const int t = threadIdx.x;
+        act = t < P.npair;
+        if (act) {
+            rp = t / ngx;
+            gx = t - rp * ngx;
+        }
+    } else if (K == 2) {
+        // both halo rows (above and below the tile) of one x group
+        const int t = threadIdx.x - 32 * P.pair_warps;
+        act = t < ngx;
+        if (act) gx = t;
+    }
+    XCtx X;
+    X.nx = (int)P.nx;
+    X.x = gx * VN;
+    X.fixl = lane == 0 || gx == 0;
+    X.fixr = lane == 31 || gx == ngx - 1;
+    X.wig = PERIODIC && X.x + VN > X.nx;
+    X.cl = X.x > 0 ? X.x - 1 : (PERIODIC ? X.nx - 1 : -1);
+    // (a Dirichlet ragged group reads the ghost column instead: its last
+    // elements are not interior and their results are dropped)
+    X.cr = X.x + VN >= X.nx ? (PERIODIC ? 0 : X.nx) : X.x + VN;
+    X.xfull = X.x + VN <= X.nx;
+    const int x = X.x;
     const T ac = T(P.ac), bc = T(P.bc), an = T(P.an), bn = T(P.bn);
-    bool dead = false;  // a bounded wait ran out (warp-uniform)
-    uint32_t gq = 0;
+    // mu = w_n * lambda of a staged (lambda, kappa) pair
+    auto mu_of = [&](T l, T k) -> T { return fma(bn, k, an) * l; };
+
+    bool dead = false;
+    uint32_t gq = 0, gr = 0;
     for (int un = blockIdx.x; un < P.units; un += gridDim.x) {
         const int yt = un % P.nyt, zc = un / P.nyt;
-        const int64_t y0 = (int64_t)yt * P.TY, z0 = (int64_t)zc * P.ZC;
+        const int64_t y0 = (int64_t)yt * P.TY;
         const int tye = (int)amin(P.TY, P.ny - y0);
-        const int zce = (int)amin(P.ZC, P.nz - z0);
+        const int64_t z0 = (int64_t)zc * P.nz / P.nzc, z1 = (int64_t)(zc + 1) * P.nz / P.nzc;
+        const int nq = (int)(z1 - z0) + 2 * K;
         const uint32_t base = gq;
-        // this thread's owned interior task (gradient ring) when ct < tye * ngx
-        const bool own = ct < tye * ngx;
-        // delay lines: dl[s-1][d] holds the level-s gradient term computed d
-        // iterations ago (for plane j - s - d); plane j - K is flushed with the
-        // terms dl[s-1][K-s], s = 1..K, added one at a time in step order so a
-        // fused pass rounds exactly like K single-step passes
-        T dl[K][K][VN];
-#pragma unroll
-        for (int s = 0; s < K; ++s)
-#pragma unroll
-            for (int d = 0; d < K; ++d)
-#pragma unroll
-                for (int e = 0; e < VN; ++e) dl[s][d][e] = T(0);
+        uint32_t sj = base % P.NS, pj = (base / P.NS) & 1, sp = 0;
+        // Ring planes are numbered per CTA: iteration j >= 2 of this unit writes
+        // plane rbase + j - 2 into slot (number mod 3); level 2 of iteration
+        // j + 1 reads it.  Warps synchronise only through these barriers, so
+        // they may drift apart by an iteration.
+        const uint32_t rbase = gr;
 
-        // running slot and parity of staged plane j (no modulo per lookup);
-        // stage(q) for a plane q <= j counts back from it
-        uint32_t sj = base % P.NS, pj = (base / P.NS) & 1;
-        int jcur = 0;
-        auto slot_of = [&](int q) -> uint32_t {
-            int sl = (int)sj - (jcur - q);
-            while (sl < 0) sl += P.NS;
-            return (uint32_t)sl;
-        };
-        auto stage = [&](int q) -> const T* { return ring + (size_t)slot_of(q) * P.stage_elems; };
-        const int nq = zce + 2 * K;
-        // task -> (row, x group) per level, fixed for the unit; tasks below
-        // tye*ngx are the interior rows (same owner at every level, for the
-        // gradient delay lines), the rest the level's halo rows
-        int trr[K][2], tgx[K][2];
-        bool tval[K][2];
+        // first tile row of a row-pair task; halo tasks own rows -1 and tye
+        const int rr0 = 2 * rp;
+        // carried state (registers), per owned row: mu and u_t of the plane below the level-1 centre
+        T m0p[2][VN], uap[2][VN];
+        // level 2 (K == 2): mu_1 of the planes below and at its centre, lambda_1 and w_c at its
+        // centre, u_{t-1} below its centre
+        T m1a[2][VN], m1b[2][VN], l1p[2][VN], wcp[2][VN], ubp[2][VN];
+        // level-1 results of this iteration, handed to level 2
+        T l1n[2][VN], wcn[2][VN], m1n[2][VN], g1n[2][VN];  // g1n: this step's gradient term
 #pragma unroll
-        for (int s = 1; s <= K; ++s) {
-            const int hs = K - s, rows_s = tye + 2 * hs;
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int ti = 0; ti < 2; ++ti) {
-                const int t = ct + ti * A_NC;
-                int rr = 0, gx = 0;
-                tval[s - 1][ti] = t < rows_s * ngx;
-                if (t < tye * ngx) {
-                    rr = t / ngx;
-                    gx = t - rr * ngx;
-                } else if (tval[s - 1][ti]) {
-                    const int h = t - tye * ngx;
-                    const int hr = h / ngx;  // 0 .. 2hs-1
-                    gx = h - hr * ngx;
-                    rr = hr < hs ? -hs + hr : tye + (hr - hs);
-                }
-                trr[s - 1][ti] = rr;
-                tgx[s - 1][ti] = gx;
+            for (int e = 0; e < VN; ++e) {
+                m0p[i][e] = uap[i][e] = T(0);
+                m1a[i][e] = m1b[i][e] = l1p[i][e] = wcp[i][e] = ubp[i][e] = T(0);
+                l1n[i][e] = wcn[i][e] = m1n[i][e] = g1n[i][e] = T(0);
             }
-        }
+
         for (int j = 0; j < nq; ++j) {
-            jcur = j;
-            // A wait that runs out is recorded, and the warp carries on without
-            // waiting: every consumer warp must keep reaching the named
-            // barriers below, which have no time limit of their own.
-            if (!dead) {
-                if (!ptx::mbar_wait_warp(&full[sj], pj)) {
+            // A wait that runs out is recorded and the warp carries on without
+            // waiting: every consumer warp must keep reaching the named barrier.
+            if (!dead && !ptx::mbar_wait_warp(&full[sj], pj)) {
+                atimeout(P.status);
+                dead = true;
+            }
+            const T* S1 = stg + (size_t)sj * P.stage_elems + P.xl;  // plane above the level-1 centre (column 0)
+            const T* S0 = stg + (size_t)sp * P.stage_elems + P.xl;  // level-1 centre plane
+            const int64_t c1 = z0 - K - 1 + j;                       // level-1 centre plane (j >= 1)
+            const bool zout1 = !PERIODIC && (c1 < 0 || c1 >= P.nz);
+            const bool own1 = c1 >= z0 && c1 < z1;
+            // ring plane written by level 1 of this iteration (K == 2, j >= 2):
+            // its slot's previous plane must have been read by every warp
+            const uint32_t wn = rbase + (uint32_t)j - 2u, wslot = wn % A_RING;
+            if (K == 2 && j >= 2 && wn >= (uint32_t)A_RING && !dead &&
+                !ptx::mbar_wait_warp(&rempty[wslot], (wn / A_RING - 1u) & 1u)) {
+                atimeout(P.status);
+                dead = true;
+            }
+
+            if (pairw) {
+                // ------------------------------------------------ row pair, level 1
+                const T* L = S0 + (rr0 - 1 + K) * pitch;  // lambda row rr0 - 1
+                const T* Kp = L + P.kap_off;
+                const T* U = S0 + P.ua_off + rr0 * pitch;  // u_t row rr0 - 1
+                if (j == 1) {
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        T lv[VN], kv[VN];
+                        vld(L + (i + 1) * pitch + x, lv);
+                        vld(Kp + (i + 1) * pitch + x, kv);
+#pragma unroll
+                        for (int e = 0; e < VN; ++e) m0p[i][e] = mu_of(lv[e], kv[e]);
+                        if (grad) vld(U + (i + 1) * pitch + x, uap[i]);
+                    }
+                } else if (j >= 2) {
+                    T mv[4][VN], lc[2][VN], kc[2][VN], mz[2][VN];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        T lv[VN], kv[VN];
+                        vld(L + i * pitch + x, lv);
+                        vld(Kp + i * pitch + x, kv);
+#pragma unroll
+                        for (int e = 0; e < VN; ++e) {
+                            mv[i][e] = mu_of(lv[e], kv[e]);
+                            if (i == 1 || i == 2) {
+                                lc[i - 1][e] = lv[e];
+                                kc[i - 1][e] = kv[e];
+                            }
+                        }
+                    }
+                    {
+                        const T* L1 = S1 + (rr0 + K) * pitch;
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            T lv[VN], kv[VN];
+                            vld(L1 + i * pitch + x, lv);
+                            vld(L1 + P.kap_off + i * pitch + x, kv);
+#pragma unroll
+                            for (int e = 0; e < VN; ++e) mz[i][e] = mu_of(lv[e], kv[e]);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const T* Lr = L + (i + 1) * pitch;
+                        T left = T(0), right = T(0);
+                        if (X.fixl) left = mu_of(Lr[X.cl], Lr[P.kap_off + X.cl]);
+                        if (X.fixr) right = mu_of(Lr[X.cr], Lr[P.kap_off + X.cr]);
+                        T s[VN];
+                        nsum(X, m0p[i], mv[i], mv[i + 1], mv[i + 2], mz[i], left, right, s);
+                        const bool out = zout1 || (!PERIODIC && y0 + rr0 + i >= P.ny);
+#pragma unroll
+                        for (int e = 0; e < VN; ++e) {
+                            const T wc = fma(bc, kc[i][e], ac);
+                            const T l1 = fma(wc, lc[i][e], s[e]);
+                            l1n[i][e] = out ? T(0) : l1;
+                            wcn[i][e] = wc;
+                            T mu1 = out ? T(0) : mu_of(l1, kc[i][e]);
+                            if (!PERIODIC && x + e >= X.nx) mu1 = T(0);  // ghost column of a ragged group
+                            m1n[i][e] = mu1;
+                            m0p[i][e] = mv[i + 1][e];
+                        }
+                    }
+                    // gradient term of this step on the owned rows of an owned plane
+                    if (grad) {
+                        T uv[4][VN], uz[2][VN];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) vld(U + i * pitch + x, uv[i]);
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) vld(S1 + P.ua_off + (rr0 + 1 + i) * pitch + x, uz[i]);
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            const T* Ur = U + (i + 1) * pitch;
+                            T left = T(0), right = T(0);
+                            if (X.fixl) left = Ur[X.cl];
+                            if (X.fixr) right = Ur[X.cr];
+                            T nb[VN];
+                            nsum(X, uap[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
+#pragma unroll
+                            for (int e = 0; e < VN; ++e) {
+                                g1n[i][e] = lc[i][e] * fma(bc, uv[i + 1][e], bn * nb[e]);
+                                uap[i][e] = uv[i + 1][e];
+                            }
+                        }
+                    }
+                    if constexpr (K == 1) {
+                        // final level: lambda_out of the owned rows
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+                            if (act && rr0 + i < tye)
+                                store_row(X, lam_out + P.origin + c1 * P.plane + (y0 + rr0 + i) * P.pitch + x,
+                                          l1n[i]);
+                    } else {
+                        // publish mu_1 of the owned rows for level 2's y neighbours
+                        T* M = mring + (size_t)wslot * P.ring_elems + P.xl + (rr0 + 1) * pitch;
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+                            if (act && rr0 + i < tye) store_row(X, M + i * pitch + x, m1n[i]);
+                    }
+                    // this step's gradient term goes to the accumulator now; the
+                    // next step's (level 2, one iteration later) follows it, so
+                    // every point sums its terms in step order
+                    if (grad && own1) {
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+                            if (act && rr0 + i < tye)
+                                add_grad(X, P.origin + c1 * P.plane + (y0 + rr0 + i) * P.pitch + x, g64, g1n[i]);
+                    }
+                }
+            } else if (K == 2) {
+                // ------------------------------------------------ halo rows, level 1 only
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int rh = i == 0 ? -1 : tye;
+                    const T* L = S0 + (rh - 1 + K) * pitch;  // lambda row rh - 1
+                    const T* Kp = L + P.kap_off;
+                    if (j == 1) {
+                        T lv[VN], kv[VN];
+                        vld(L + pitch + x, lv);
+                        vld(Kp + pitch + x, kv);
+#pragma unroll
+                        for (int e = 0; e < VN; ++e) m0p[i][e] = mu_of(lv[e], kv[e]);
+                    } else if (j >= 2) {
+                        T mv[3][VN], lc[VN], kc[VN], mz[VN];
+#pragma unroll
+                        for (int r3 = 0; r3 < 3; ++r3) {
+                            T lv[VN], kv[VN];
+                            vld(L + r3 * pitch + x, lv);
+                            vld(Kp + r3 * pitch + x, kv);
+#pragma unroll
+                            for (int e = 0; e < VN; ++e) {
+                                mv[r3][e] = mu_of(lv[e], kv[e]);
+                                if (r3 == 1) {
+                                    lc[e] = lv[e];
+                                    kc[e] = kv[e];
+                                }
+                            }
+                        }
+                        {
+                            const T* L1 = S1 + (rh + K) * pitch;
+                            T lv[VN], kv[VN];
+                            vld(L1 + x, lv);
+                            vld(L1 + P.kap_off + x, kv);
+#pragma unroll
+                            for (int e = 0; e < VN; ++e) mz[e] = mu_of(lv[e], kv[e]);
+                        }
+                        const T* Lr = L + pitch;
+                        T left = T(0), right = T(0);
+                        if (X.fixl) left = mu_of(Lr[X.cl], Lr[P.kap_off + X.cl]);
+                        if (X.fixr) right = mu_of(Lr[X.cr], Lr[P.kap_off + X.cr]);
+                        T s[VN];
+                        nsum(X, m0p[i], mv[0], mv[1], mv[2], mz, left, right, s);
+                        const int64_t yabs = y0 + rh;
+                        const bool out = zout1 || (!PERIODIC && (yabs < 0 || yabs >= P.ny));
+                        T mu1[VN];
+#pragma unroll
+                        for (int e = 0; e < VN; ++e) {
+                            const T wc = fma(bc, kc[e], ac);
+                            const T l1 = fma(wc, lc[e], s[e]);
+                            mu1[e] = out ? T(0) : mu_of(l1, kc[e]);
+                            m0p[i][e] = mv[1][e];
+                        }
+                        if (act)
+                            store_row(X, mring + (size_t)wslot * P.ring_elems + P.xl + (rh + 1) * pitch + x, mu1);
+                    }
+                }
+            }
+
+            if constexpr (K == 2) {
+                if (j >= 2) {  // this warp's rows of the ring plane are written
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&rfull[wslot]);
+                }
+                // the ring plane of the previous iteration (level 2's centre)
+                const uint32_t rn = rbase + (uint32_t)j - 3u, rslot = rn % A_RING;
+                if (pairw && j >= 4 && !dead && !ptx::mbar_wait_warp(&rfull[rslot], (rn / A_RING) & 1u)) {
                     atimeout(P.status);
                     dead = true;
                 }
-            }
+                if (pairw && j >= 3) {
+                    // ------------------------------------------------ row pair, level 2
+                    const T* UB = S0 + P.ub_off + rr0 * pitch;  // u_{t-1} row rr0 - 1 at the level-2 centre
+                    if (j >= 4) {
+                        const int64_t c2 = c1 - 1;
+                        const T* M = mring + (size_t)rslot * P.ring_elems + P.xl + rr0 * pitch;  // mu_1 row rr0 - 1
+                        T mup[VN], mdn[VN];
+                        vld(M + x, mup);
+                        vld(M + 3 * pitch + x, mdn);
+                        T l2[2][VN], s[2][VN];
 #pragma unroll
-            for (int s = 1; s <= K; ++s) {
-                const int pq = j - s;  // plane (stage index) of level s this iteration
-                if (pq < s || pq > nq - 1 - s) continue;
-                const int64_t zabs = z0 - K + pq;
-                const int hs = K - s;                  // y halo of level s
-                const int rows_s = tye + 2 * hs;
-                const bool zout = !PERIODIC && (zabs < 0 || zabs >= P.nz);
-                // sources of level s-1 at planes pq-1, pq, pq+1 (row 0 of level s-1 = y0 - (hs + 1))
-                const T* src[3];
-                int src_h;  // halo of the source arrays
-                if (s == 1) {
+                        for (int i = 0; i < 2; ++i) {
+                            const T* Mr = M + (i + 1) * pitch;
+                            T left = T(0), right = T(0);
+                            if (X.fixl) left = Mr[X.cl];
+                            if (X.fixr) right = Mr[X.cr];
+                            nsum(X, m1a[i], i == 0 ? mup : m1b[0], m1b[i], i == 0 ? m1b[1] : mdn, m1n[i], left, right,
+                                 s[i]);
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) src[d] = stage(pq - 1 + d) + P.lam_off;
-                    src_h = K;
-                } else {
-#pragma unroll
-                    for (int d = 0; d < 3; ++d)
-                        src[d] = lvl + (size_t)(s - 2) * LSLOTS * P.ring_elems +
-                                 (size_t)((pq - 1 + d) % LSLOTS) * P.ring_elems;
-                    src_h = K - s + 1;
-                }
-                const T* kap[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) kap[d] = stage(pq - 1 + d) + P.kap_off;
-                const T* us[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) us[d] = stage(pq - 1 + d) + P.u_off[s - 1];
-                T* dst = (s < K) ? lvl + (size_t)(s - 1) * LSLOTS * P.ring_elems + (size_t)(pq % LSLOTS) * P.ring_elems
-                                 : nullptr;
-#pragma unroll
-                for (int ti = 0; ti < 2; ++ti) {
-                    if (!tval[s - 1][ti]) continue;
-                    const int t = ct + ti * A_NC;
-                    const int rr = trr[s - 1][ti];
-                    const int x = tgx[s - 1][ti] * VN;
-                    const int64_t yabs = y0 + rr;
-                    const bool outside = !PERIODIC && (zout || yabs < 0 || yabs >= P.ny);
-                    T o[VN];
-                    T gterm[VN];
-                    if (outside) {
-#pragma unroll
-                        for (int e = 0; e < VN; ++e) {
-                            o[e] = T(0);
-                            gterm[e] = T(0);
-                        }
-                    } else {
-                        const int so = (rr + src_h) * (int)P.pitch + P.xl;   // source row, x = 0
-                        const int ko = (rr + K) * (int)P.pitch + P.xl;       // kappa row
-                        const int uo = (rr + 1) * (int)P.pitch + P.xl;       // state row
-                        const int pt = (int)P.pitch;
-                        T lc[VN], ly[VN], lyy[VN], lzm[VN], lzp[VN];
-                        T kc[VN], ky[VN], kyy[VN], kzm[VN], kzp[VN];
-                        ald(src[1] + so + x, lc);
-                        ald(src[1] + so - pt + x, ly);
-                        ald(src[1] + so + pt + x, lyy);
-                        ald(src[0] + so + x, lzm);
-                        ald(src[2] + so + x, lzp);
-                        ald(kap[1] + ko + x, kc);
-                        ald(kap[1] + ko - pt + x, ky);
-                        ald(kap[1] + ko + pt + x, kyy);
-                        ald(kap[0] + ko + x, kzm);
-                        ald(kap[2] + ko + x, kzp);
-                        const T* lrow = src[1] + so;
-                        const T* krow = kap[1] + ko;
-                        // x neighbours
-                        T lxm[VN], lxp[VN], kxm[VN], kxp[VN];
-#pragma unroll
-                        const int nxi = (int)P.nx;
-                        for (int e = 0; e < VN; ++e) {
-                            int xm = x + e - 1, xp = x + e + 1;
-                            if (PERIODIC) {
-                                xm = xm < 0 ? xm + nxi : xm;
-                                xp = xp >= nxi ? xp - nxi : xp;
-                            }
-                            lxm[e] = e > 0 ? lc[e - 1] : lrow[xm];
-                            kxm[e] = e > 0 ? kc[e - 1] : krow[xm];
-                            lxp[e] = (e < VN - 1 && !(PERIODIC && x + e + 1 == P.nx)) ? lc[e + 1] : lrow[xp];
-                            kxp[e] = (e < VN - 1 && !(PERIODIC && x + e + 1 == P.nx)) ? kc[e + 1] : krow[xp];
+                            for (int e = 0; e < VN; ++e) l2[i][e] = fma(wcp[i][e], l1p[i][e], s[i][e]);
                         }
 #pragma unroll
-                        for (int e = 0; e < VN; ++e) {
-                            // transposed step
-                            T acc = fma(fma(bc, kc[e], ac), lc[e], T(0));
-                            acc = fma(fma(bn, kxm[e], an), lxm[e], acc);
-                            acc = fma(fma(bn, kxp[e], an), lxp[e], acc);
-                            acc = fma(fma(bn, ky[e], an), ly[e], acc);
-                            acc = fma(fma(bn, kyy[e], an), lyy[e], acc);
-                            acc = fma(fma(bn, kzm[e], an), lzm[e], acc);
-                            acc = fma(fma(bn, kzp[e], an), lzp[e], acc);
-                            o[e] = acc;
-                        }
-                        // gradient term on interior rows of this unit's planes
-                        if (rr >= 0 && rr < tye) {
-                            T uc[VN], uy[VN], uyy[VN], uzm[VN], uzp[VN];
-                            ald(us[1] + uo + x, uc);
-                            ald(us[1] + uo - pt + x, uy);
-                            ald(us[1] + uo + pt + x, uyy);
-                            ald(us[0] + uo + x, uzm);
-                            ald(us[2] + uo + x, uzp);
-                            const T* urow = us[1] + uo;
+                        for (int i = 0; i < 2; ++i)
+                            if (act && rr0 + i < tye)
+                                store_row(X, lam_out + P.origin + c2 * P.plane + (y0 + rr0 + i) * P.pitch + x, l2[i]);
+                        if (grad) {
+                            T uv[4][VN], uz[2][VN];
 #pragma unroll
-                            for (int e = 0; e < VN; ++e) {
-                                int xm = x + e - 1, xp = x + e + 1;
-                                if (PERIODIC) {
-                                    xm = xm < 0 ? xm + nxi : xm;
-                                    xp = xp >= nxi ? xp - nxi : xp;
+                            for (int i = 0; i < 4; ++i) vld(UB + i * pitch + x, uv[i]);
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) vld(S1 + P.ub_off + (rr0 + 1 + i) * pitch + x, uz[i]);
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) {
+                                const T* Ur = UB + (i + 1) * pitch;
+                                T left = T(0), right = T(0);
+                                if (X.fixl) left = Ur[X.cl];
+                                if (X.fixr) right = Ur[X.cr];
+                                T nb[VN], g2[VN];
+                                nsum(X, ubp[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
+#pragma unroll
+                                for (int e = 0; e < VN; ++e) {
+                                    g2[e] = l1p[i][e] * fma(bc, uv[i + 1][e], bn * nb[e]);
+                                    ubp[i][e] = uv[i + 1][e];
                                 }
-                                const T uxm = e > 0 ? uc[e - 1] : urow[xm];
-                                const T uxp = (e < VN - 1 && !(PERIODIC && x + e + 1 == P.nx)) ? uc[e + 1] : urow[xp];
-                                const T nb = ((((uxm + uxp) + uy[e]) + uyy[e]) + uzm[e]) + uzp[e];
-                                gterm[e] = lc[e] * fma(bc, uc[e], bn * nb);
+                                if (act && rr0 + i < tye) {
+                                    const int64_t off = P.origin + c2 * P.plane + (y0 + rr0 + i) * P.pitch + x;
+                                    add_grad(X, off, g64, g2);
+                                }
                             }
-                        } else {
+                        }
+                    } else if (grad) {
+                        // j == 3: u_{t-1} of the plane below the first level-2 centre
 #pragma unroll
-                            for (int e = 0; e < VN; ++e) gterm[e] = T(0);
-                        }
-                    }
-                    if (s < K) {
-                        T* rp = dst + (rr + hs) * (int)P.pitch + P.xl + x;
-                        if (x + VN <= P.nx) {
-                            ast(rp, o);
-                        } else {
-                            for (int e = 0; e < VN && x + e < P.nx; ++e) rp[e] = o[e];  // keep ghost columns 0
-                        }
-                    } else if (!zout && rr >= 0 && rr < tye) {
-                        T* op = lam_out + P.origin + zabs * P.plane + (y0 + rr) * P.pitch + x;
-                        if (x + VN <= P.nx) {
-                            ast(op, o);
-                        } else {
-                            for (int e = 0; e < VN && x + e < P.nx; ++e) op[e] = o[e];
-                        }
-                    }
-                    // delay line of level s: this term belongs to plane pq (owner threads only)
-                    if (t < tye * ngx && own) {
-#pragma unroll
-                        for (int e = 0; e < VN; ++e) dl[s - 1][0][e] = gterm[e];
+                        for (int i = 0; i < 2; ++i) vld(UB + (i + 1) * pitch + x, ubp[i]);
                     }
                 }
-                if (s < K) consumer_bar();  // level s is read by level s + 1 below
-            }
-            // plane j - K is complete for the owner: flush the K gradient terms once
-            {
-                const int pq = j - K;
-                const int64_t zabs = z0 - K + pq;
-                if (own && pq >= K && pq < zce + K && (sizeof(T) == 8 ? g64 != nullptr : ghi != nullptr)) {
-                    const int rr = ct / ngx;
-                    const int x = (ct - rr * ngx) * VN;
-                    const int64_t off = P.origin + zabs * P.plane + (y0 + rr) * P.pitch + x;
-                    // the K terms of plane pq, in step order (level 1 = the latest step);
-                    // the old accumulator comes from the staged tile of plane pq
-                    const T* gst = stage(pq) + P.g_off + rr * (int)P.pitch + P.xl + x;
-                    if constexpr (sizeof(T) == 8) {
-                        if (x + VN <= P.nx) {
-                            double2 gv = *reinterpret_cast<const double2*>(gst);
+                if (pairw && j >= 2) {
 #pragma unroll
-                            for (int s = 1; s <= K; ++s) {
-                                gv.x += (double)dl[s - 1][K - s][0];
-                                gv.y += (double)dl[s - 1][K - s][1];
-                            }
-                            *reinterpret_cast<double2*>(g64 + off) = gv;
-                        } else {
-                            for (int e = 0; e < VN && x + e < P.nx; ++e) {
-                                double gv = gst[e];
+                    for (int i = 0; i < 2; ++i)
 #pragma unroll
-                                for (int s = 1; s <= K; ++s) gv += (double)dl[s - 1][K - s][e];
-                                g64[off + e] = gv;
-                            }
+                        for (int e = 0; e < VN; ++e) {
+                            m1a[i][e] = m1b[i][e];
+                            m1b[i][e] = m1n[i][e];
+                            l1p[i][e] = l1n[i][e];
+                            wcp[i][e] = wcn[i][e];
                         }
-                    } else {
-                        const float* hs = reinterpret_cast<const float*>(gst);
-                        const float* ls = hs + (size_t)P.TY * P.pitch;
-                        if (x + VN <= P.nx) {
-                            float2 h = *reinterpret_cast<const float2*>(hs);
-                            float2 l = *reinterpret_cast<const float2*>(ls);
-#pragma unroll
-                            for (int s = 1; s <= K; ++s) {
-                                ff_add(h.x, l.x, (float)dl[s - 1][K - s][0]);
-                                ff_add(h.y, l.y, (float)dl[s - 1][K - s][1]);
-                            }
-                            *reinterpret_cast<float2*>(ghi + off) = h;
-                            *reinterpret_cast<float2*>(glo + off) = l;
-                        } else {
-                            for (int e = 0; e < VN && x + e < P.nx; ++e) {
-                                float h = hs[e], l = ls[e];
-#pragma unroll
-                                for (int s = 1; s <= K; ++s) ff_add(h, l, (float)dl[s - 1][K - s][e]);
-                                ghi[off + e] = h;
-                                glo[off + e] = l;
-                            }
-                        }
-                    }
                 }
-                // age every delay line by one iteration
-#pragma unroll
-                for (int s = 0; s < K; ++s)
-#pragma unroll
-                    for (int d = K - 1; d >= 1; --d)
-#pragma unroll
-                        for (int e = 0; e < VN; ++e) dl[s][d][e] = dl[s][d - 1][e];
-#pragma unroll
-                for (int s = 0; s < K; ++s)
-#pragma unroll
-                    for (int e = 0; e < VN; ++e) dl[s][0][e] = T(0);
+                if (j >= 3) {  // done with the previous ring plane (halo warps never read it)
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&rempty[rslot]);
+                }
             }
-            // staged plane j-K-1 is no longer needed
-            if (j - K - 1 >= 0) {
+
+            // staged plane j - 1 is no longer needed
+            if (j >= 1) {
                 __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(&empty[slot_of(j - K - 1)]);
+                if (lane == 0) ptx::mbar_arrive(&empty[sp]);
             }
+            sp = sj;
             if (++sj == (uint32_t)P.NS) {
                 sj = 0;
                 pj ^= 1u;
             }
         }
-        // release the planes still held (sj now belongs to plane nq)
-        jcur = nq;
-        for (int q = (nq - K - 1 > 0 ? nq - K - 1 : 0); q < nq; ++q) {
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&empty[slot_of(q)]);
+        __syncwarp();
+        if (lane == 0) {
+            ptx::mbar_arrive(&empty[sp]);  // the last staged plane
+            // the unit's last ring plane has no reader: release it as read
+            if (K == 2) ptx::mbar_arrive(&rempty[(rbase + (uint32_t)nq - 3u) % A_RING]);
         }
         gq = base + nq;
-    }
-}
-
-// gradient fold: grad[p] += hi[p] + lo[p] on the interior (FP32 grids)
-__global__ void k_fold_ff(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ grad, Geom g)
-{
-    const int64_t rows = g.nz * g.ny;
-    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int64_t z = (uint32_t)row / (uint32_t)g.ny, y = row - z * g.ny;  // 32-bit division
-        const int64_t base = g.origin + z * g.plane + y * g.pitch;
-        for (int64_t x = threadIdx.x; x < g.nx; x += blockDim.x)
-            grad[base + x] += (double)hi[base + x] + (double)lo[base + x];
+        if (K == 2) gr = rbase + (uint32_t)nq - 2u;
     }
 }
 
@@ -553,33 +666,69 @@ int adj_sm_count()
 constexpr size_t A_SMEM = 220 * 1024;
 
 struct AdjCfg {
-    int K, TY, ZC, NS;
+    int K, TY, NS, CW, pair_warps, npair, nzc;
     size_t stage_bytes, ring_bytes;
 };
 
-bool adj_cfg(const Geom& g, int kmax, AdjCfg* c)
+size_t adj_stage_rows(int TY, int K) { return 2 * (size_t)(TY + 2 * K) + (size_t)K * (TY + 2); }
+
+// Tile rows, stages and z chunks for K fused steps.  Tiles take as many row
+// pairs as one task per consumer thread allows (at most A_MAXCW warps, halo
+// tasks included) while the ring keeps two stages in flight; failing that,
+// one.
+bool adj_cfg(const Geom& g, int K, AdjCfg* c)
 {
-    const int VN = 2;  // AV<T>::N for both types
+    const int VN = g.esize == 8 ? 2 : 4;
     const int ngx = (int)((g.nx + VN - 1) / VN);
-    const int TY = (int)std::min<int64_t>(std::min(16, A_NC / std::max(1, ngx)), g.ny);
-    if (TY < 1) return false;
-    for (int K = kmax; K >= 1; --K) {
-        if ((TY + 2 * (K - 1)) * ngx > 2 * A_NC) continue;  // at most two tasks per thread and level
-        const size_t rows = 2 * (size_t)(TY + 2 * K) + (size_t)K * (TY + 2);
-        // + the gradient accumulator tile: TY rows of 8 bytes per point
-        const size_t sb = ((rows * g.pitch * g.esize + (size_t)TY * g.pitch * 8) + 127) / 128 * 128;
-        const size_t rb = (K > 1) ? (size_t)(K - 1) * LSLOTS * ((size_t)(TY + 2 * (K - 1)) * g.pitch * g.esize) : 0;
-        if (rb + (size_t)(K + 3) * sb + 256 > A_SMEM) continue;  // K+2 resident planes + 1 in flight
-        const int NS = (int)std::min<size_t>(8, (A_SMEM - rb - 256) / sb);
-        const int nyt = (int)((g.ny + TY - 1) / TY);
-        const int64_t want = 6LL * adj_sm_count();
-        const int64_t nzc = std::max<int64_t>(1, want / nyt);
-        int ZC = (int)std::max<int64_t>(8, (g.nz + nzc - 1) / nzc);
-        ZC = (int)std::min<int64_t>(ZC, g.nz);
-        *c = AdjCfg{K, TY, ZC, NS, sb, rb};
-        return true;
+    const size_t rowb = (size_t)g.pitch * g.esize;
+    int eTY = 0, eNS = 0, eNZC = 0;
+    const char* env = std::getenv("ST_ADJ_CFG");  // "TY,NS,nzc" for tuning sweeps
+    const bool use_env = env && std::sscanf(env, "%d,%d,%d", &eTY, &eNS, &eNZC) == 3 && eTY >= 2 && eTY % 2 == 0 &&
+                         eNS >= 3 && eNZC >= 1;
+    AdjCfg best{};
+    bool have = false;
+    for (int pass = 0; pass < 2 && !have; ++pass) {
+        const int min_ns = pass == 0 ? 4 : 3;
+        for (int TY = 16; TY >= 2; TY -= 2) {
+            if (use_env && TY != eTY) continue;
+            if (TY > 2 && TY - 2 >= g.ny) continue;  // no taller than the grid
+            const int npair = (TY / 2) * ngx;
+            const int pw = (npair + 31) / 32;
+            const int hw = K == 2 ? (ngx + 31) / 32 : 0;
+            if (pw + hw > A_MAXCW) continue;
+            const size_t sb = (adj_stage_rows(TY, K) * rowb + 127) / 128 * 128;
+            const size_t rb = K == 2 ? (size_t)A_RING * (TY + 2) * rowb : 0;
+            if (rb + 3 * sb + 512 > A_SMEM) continue;
+            int NS = (int)std::min<size_t>(8, (A_SMEM - rb - 512) / sb);
+            if (use_env) NS = std::min(NS, eNS);
+            if (NS < min_ns && !use_env) continue;
+            best = AdjCfg{K, TY, NS, pw + hw, pw, npair, 1, sb, rb};
+            have = true;
+            break;
+        }
     }
-    return false;
+    if (!have) return false;
+    // z chunks: balance the per-CTA critical path against the extra planes
+    // each chunk stages (2K of them)
+    const int nyt = (int)((g.ny + best.TY - 1) / best.TY);
+    const int64_t nsm = adj_sm_count();
+    double bestcost = 1e300;
+    for (int64_t nzc = 1; nzc <= g.nz; ++nzc) {
+        const int64_t units = nyt * nzc;
+        const int64_t zmax = (g.nz + nzc - 1) / nzc;
+        const double waves = (double)((units + nsm - 1) / nsm);
+        const double path = waves * (double)(zmax + 2 * K);
+        const double total = (double)nyt * (double)(g.nz + 2 * K * nzc) / (double)nsm;
+        const double cost = std::max(path, total);
+        if (cost < bestcost - 1e-9) {
+            bestcost = cost;
+            best.nzc = (int)nzc;
+        }
+        if (units > 64 * nsm) break;
+    }
+    if (use_env) best.nzc = (int)std::min<int64_t>(eNZC, g.nz);
+    *c = best;
+    return true;
 }
 
 template <typename T, int K, bool PERIODIC>
@@ -598,25 +747,27 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
     P.r = g.r;
     P.xl = (int)g.xl;
     P.TY = c.TY;
-    P.ZC = c.ZC;
     P.NS = c.NS;
+    P.CW = c.CW;
     P.nyt = (int)((g.ny + c.TY - 1) / c.TY);
-    P.nzc = (int)((g.nz + c.ZC - 1) / c.ZC);
+    P.nzc = c.nzc;
     P.units = P.nyt * P.nzc;
+    P.ngx = (int)((g.nx + AV<T>::N - 1) / AV<T>::N);
+    P.npair = c.npair;
+    P.pair_warps = c.pair_warps;
     P.stage_elems = (uint32_t)(c.stage_bytes / sizeof(T));
-    P.lam_off = 0;
     P.kap_off = (uint32_t)((c.TY + 2 * K) * g.pitch);
-    P.u_off[0] = 2 * P.kap_off;
-    P.u_off[1] = P.u_off[0] + (uint32_t)((c.TY + 2) * g.pitch);
-    P.g_off = P.u_off[0] + (uint32_t)(K * (c.TY + 2) * g.pitch);
-    P.ring_elems = (uint32_t)((c.TY + 2 * (K - 1)) * g.pitch);
+    P.ua_off = 2 * P.kap_off;
+    P.ub_off = P.ua_off + (uint32_t)((c.TY + 2) * g.pitch);
+    P.ring_elems = (uint32_t)((c.TY + 2) * g.pitch);
+    P.grad = a.gk != nullptr ? 1 : 0;
     const StarCoef& k = f.sc;
     P.ac = k.c_a;
     P.bc = k.c_b;
     P.an = k.a[0][0][0];
     P.bn = k.b[0][0][0];
     P.status = a.status;
-    const size_t smem = c.ring_bytes + (size_t)c.NS * c.stage_bytes + 2 * sizeof(uint64_t) * c.NS;
+    const size_t smem = c.ring_bytes + (size_t)c.NS * c.stage_bytes + sizeof(uint64_t) * (2 * c.NS + 2 * A_RING);
     auto fn = k_adjoint<T, K, PERIODIC>;
     static bool attr = false;
     if (!attr) {
@@ -625,8 +776,8 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
         attr = true;
     }
     const int grid = (int)std::min<int64_t>(P.units, adj_sm_count());
-    fn<<<grid, A_THREADS, smem, s>>>((const T*)a.lam_in, (T*)a.lam_out, (const T*)a.kappa, (const T*)a.u,
-                                     (const T*)a.u2, a.gk, a.ghi, a.glo, P);
+    fn<<<grid, (c.CW + 1) * 32, smem, s>>>((const T*)a.lam_in, (T*)a.lam_out, (const T*)a.kappa, (const T*)a.u,
+                                           (const T*)a.u2, a.gk, P);
     return cudaGetLastError();
 }
 
@@ -642,15 +793,15 @@ int star3d_adjoint_fuse(const Family& f)
         for (int sd = 0; sd < 2; ++sd)
             if (k.a[ax][sd][0] != k.a[0][0][0] || k.b[ax][sd][0] != k.b[0][0][0]) return 0;
     AdjCfg c;
-    if (!adj_cfg(f.g, A_KMAX, &c)) return 0;
-    return c.K;
+    if (adj_cfg(f.g, 2, &c)) return 2;
+    return adj_cfg(f.g, 1, &c) ? 1 : 0;
 }
 
 cudaError_t launch_star3d_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s)
 {
-    if (star3d_adjoint_fuse(f) < a.steps) return cudaErrorNotSupported;
+    if (a.steps < 1 || a.steps > 2 || star3d_adjoint_fuse(f) < a.steps) return cudaErrorNotSupported;
     AdjCfg c;
-    if (!adj_cfg(f.g, a.steps, &c) || c.K != a.steps) return cudaErrorNotSupported;
+    if (!adj_cfg(f.g, a.steps, &c)) return cudaErrorNotSupported;
     const bool dbl = f.g.esize == 8;
     if (a.steps == 2) {
         if (dbl) return f.periodic ? launch_adj_t<double, 2, true>(f, a, c, s) : launch_adj_t<double, 2, false>(f, a, c, s);
@@ -658,13 +809,6 @@ cudaError_t launch_star3d_adjoint(const Family& f, const AdjointArgs& a, cudaStr
     }
     if (dbl) return f.periodic ? launch_adj_t<double, 1, true>(f, a, c, s) : launch_adj_t<double, 1, false>(f, a, c, s);
     return f.periodic ? launch_adj_t<float, 1, true>(f, a, c, s) : launch_adj_t<float, 1, false>(f, a, c, s);
-}
-
-cudaError_t launch_fold_ff(const float* hi, const float* lo, double* grad, const Geom& g, cudaStream_t s)
-{
-    const int64_t rows = g.nz * g.ny;
-    k_fold_ff<<<(unsigned)std::min<int64_t>(rows, 4096), 256, 0, s>>>(hi, lo, grad, g);
-    return cudaGetLastError();
 }
 
 }  // namespace st

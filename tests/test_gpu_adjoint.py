@@ -84,6 +84,30 @@ def test_gradient_fp32_matches_fp64_oracle():
     assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
 
 
+@pytest.mark.parametrize("periodic,bc", [(False, 0.0), (False, 0.3), (True, 0.0)])
+def test_gradient_fp32_ragged_matches_fp64_oracle(periodic, bc):
+    """FP32 transpose on rows that end inside a 16-byte group (nx = 45), a
+    ragged last y tile and segments of 5, 5 and 2 steps (two-step and
+    one-step passes)."""
+    v = inputs.varcoef3d(shape=(30, 27, 45))
+    steps, m = 12, 5
+    loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, bc, steps, m)
+    uT, lam0, gk, loss, kern = gpu_grad(v, steps, m, torch.float32, periodic, bc)
+    assert rel_err(uT, uT_r) <= TOL32_FWD, kern
+    assert rel_err(lam0, lam_r) <= TOL32_FWD, kern
+    assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
+
+
+def test_checkpoint_interval_does_not_change_gradient_fp32():
+    """FP32 grids: fused two-step passes round exactly like single steps, so
+    m = 1, 6 and 20 give bitwise equal lambda_0 and gradients."""
+    v = inputs.varcoef3d(shape=(20, 26, 44))
+    base = gpu_grad(v, 20, 20, torch.float32, True)
+    for m in (1, 6):
+        other = gpu_grad(v, 20, m, torch.float32, True)
+        assert np.array_equal(base[1], other[1]) and np.array_equal(base[2], other[2])
+
+
 def test_checkpoint_interval_does_not_change_gradient():
     """Recomputation is deterministic: m = 1, 7 and 20 give bitwise equal results."""
     v = inputs.varcoef3d(shape=(20, 24, 32))
