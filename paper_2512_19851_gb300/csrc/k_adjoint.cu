@@ -155,16 +155,32 @@ __device__ __forceinline__ void nsum(const XCtx& X, const T (&zm)[AV<T>::N], con
 
 // Add one step's gradient terms of a row group to the FP64 gradient.  The
 // additions are fire-and-forget reductions performed at L2 (the thread never
-// waits on them); a point's terms all come from one thread, in step order, and
-// same-thread atomics on one address take effect in program order, so every
-// point sums its terms in step order, whatever the pass structure.
+// waits on them).  When the warp's 32 lanes hold 32 consecutive whole groups
+// of one row (`fast`, warp-uniform) the terms are first exchanged through the
+// warp's shared scratch so that each reduction instruction covers 32
+// consecutive doubles (8 sectors instead of 32).  Either way a point's terms
+// all come from one thread, in step order, and same-thread atomics on one
+// address take effect in program order, so every point sums its terms in
+// step order, whatever the pass structure.
 template <typename T>
-__device__ __forceinline__ void add_grad(const XCtx& X, int64_t off, double* __restrict__ g64, const T (&t)[AV<T>::N])
+__device__ __forceinline__ void add_grad(const XCtx& X, bool fast, double* wsc, int lane, int64_t off, bool ok,
+                                         double* __restrict__ g64, const T (&t)[AV<T>::N])
 {
     constexpr int VN = AV<T>::N;
+    if (fast) {
+        const int64_t base = __shfl_sync(0xffffffffu, off, 0);
 #pragma unroll
-    for (int e = 0; e < VN; ++e)
-        if (X.xfull || X.x + e < X.nx) atomicAdd(g64 + off + e, (double)t[e]);
+        for (int e = 0; e < VN; e += 2)
+            *reinterpret_cast<double2*>(wsc + VN * lane + e) = make_double2((double)t[e], (double)t[e + 1]);
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < VN; ++e) atomicAdd(g64 + base + lane + 32 * e, wsc[lane + 32 * e]);
+        __syncwarp();
+    } else if (ok) {
+#pragma unroll
+        for (int e = 0; e < VN; ++e)
+            if (X.xfull || X.x + e < X.nx) atomicAdd(g64 + off + e, (double)t[e]);
+    }
 }
 
 template <typename T>
@@ -191,6 +207,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
     uint64_t* empty = full + P.NS;
     uint64_t* rfull = empty + P.NS;    // K == 2: a ring plane is written (one arrival per consumer warp)
     uint64_t* rempty = rfull + A_RING;  // K == 2: a ring plane is read
+    // per consumer warp: 32 x VN doubles of gradient terms in transit
+    double* wscr = reinterpret_cast<double*>(rempty + A_RING) + (size_t)(threadIdx.x >> 5) * 32 * AV<T>::N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -341,6 +359,9 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 
         // first tile row of a row-pair task; halo tasks own rows -1 and tye
         const int rr0 = 2 * rp;
+        // gradient reductions through the warp scratch: the warp holds 32
+        // consecutive whole groups of both rows of one row pair
+        const bool fastw = pairw && (ngx % 32 == 0) && __all_sync(0xffffffffu, act && X.xfull && rr0 + 1 < tye);
         // carried state (registers), per owned row: mu and u_t of the plane below the level-1 centre
         T m0p[2][VN], uap[2][VN];
         // level 2 (K == 2): mu_1 of the planes below and at its centre, lambda_1 and w_c at its
@@ -483,8 +504,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                     if (grad && own1) {
 #pragma unroll
                         for (int i = 0; i < 2; ++i)
-                            if (act && rr0 + i < tye)
-                                add_grad(X, P.origin + c1 * P.plane + (y0 + rr0 + i) * P.pitch + x, g64, g1n[i]);
+                            add_grad(X, fastw, wscr, lane, P.origin + c1 * P.plane + (y0 + rr0 + i) * P.pitch + x,
+                                     act && rr0 + i < tye, g64, g1n[i]);
                     }
                 }
             } else if (K == 2) {
@@ -601,10 +622,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                                     g2[e] = l1p[i][e] * fma(bc, uv[i + 1][e], bn * nb[e]);
                                     ubp[i][e] = uv[i + 1][e];
                                 }
-                                if (act && rr0 + i < tye) {
-                                    const int64_t off = P.origin + c2 * P.plane + (y0 + rr0 + i) * P.pitch + x;
-                                    add_grad(X, off, g64, g2);
-                                }
+                                add_grad(X, fastw, wscr, lane, P.origin + c2 * P.plane + (y0 + rr0 + i) * P.pitch + x,
+                                         act && rr0 + i < tye, g64, g2);
                             }
                         }
                     } else if (grad) {
@@ -674,8 +693,8 @@ size_t adj_stage_rows(int TY, int K) { return 2 * (size_t)(TY + 2 * K) + (size_t
 
 // Tile rows, stages and z chunks for K fused steps.  Tiles take as many row
 // pairs as one task per consumer thread allows (at most A_MAXCW warps, halo
-// tasks included) while the ring keeps two stages in flight; failing that,
-// one.
+// tasks included) and shared memory holds with at least one stage in flight:
+// the halo rows a taller tile saves are worth more than extra stages.
 bool adj_cfg(const Geom& g, int K, AdjCfg* c)
 {
     const int VN = g.esize == 8 ? 2 : 4;
@@ -687,8 +706,8 @@ bool adj_cfg(const Geom& g, int K, AdjCfg* c)
                          eNS >= 3 && eNZC >= 1;
     AdjCfg best{};
     bool have = false;
-    for (int pass = 0; pass < 2 && !have; ++pass) {
-        const int min_ns = pass == 0 ? 4 : 3;
+    {
+        const int min_ns = 3;
         for (int TY = 16; TY >= 2; TY -= 2) {
             if (use_env && TY != eTY) continue;
             if (TY > 2 && TY - 2 >= g.ny) continue;  // no taller than the grid
@@ -698,8 +717,9 @@ bool adj_cfg(const Geom& g, int K, AdjCfg* c)
             if (pw + hw > A_MAXCW) continue;
             const size_t sb = (adj_stage_rows(TY, K) * rowb + 127) / 128 * 128;
             const size_t rb = K == 2 ? (size_t)A_RING * (TY + 2) * rowb : 0;
-            if (rb + 3 * sb + 512 > A_SMEM) continue;
-            int NS = (int)std::min<size_t>(8, (A_SMEM - rb - 512) / sb);
+            const size_t fixed = rb + 512 + (size_t)(pw + hw) * 32 * VN * 8;  // ring, barriers, warp scratch
+            if (fixed + 3 * sb > A_SMEM) continue;
+            int NS = (int)std::min<size_t>(8, (A_SMEM - fixed) / sb);
             if (use_env) NS = std::min(NS, eNS);
             if (NS < min_ns && !use_env) continue;
             best = AdjCfg{K, TY, NS, pw + hw, pw, npair, 1, sb, rb};
@@ -767,7 +787,8 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
     P.an = k.a[0][0][0];
     P.bn = k.b[0][0][0];
     P.status = a.status;
-    const size_t smem = c.ring_bytes + (size_t)c.NS * c.stage_bytes + sizeof(uint64_t) * (2 * c.NS + 2 * A_RING);
+    const size_t smem = c.ring_bytes + (size_t)c.NS * c.stage_bytes + sizeof(uint64_t) * (2 * c.NS + 2 * A_RING) +
+                        (size_t)c.CW * 32 * AV<T>::N * sizeof(double);
     auto fn = k_adjoint<T, K, PERIODIC>;
     static bool attr = false;
     if (!attr) {
