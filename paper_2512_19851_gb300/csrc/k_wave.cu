@@ -18,6 +18,8 @@
 //    overwrites u^{n-1} in place (every point's u^{n-1} is staged before the
 //    point is written, and no other CTA reads it).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "families.cuh"
@@ -344,8 +346,11 @@ int wave_sm_count()
     return n;
 }
 
-constexpr size_t W_SMEM = 210 * 1024;
+constexpr size_t W_SMEM = 226 * 1024;  // of the 227 KB a block may use
 
+// The u ring holds planes z..z+4 plus two in flight (7 stages); the (m, u^{n-1})
+// ring carries half of the bytes read and gets the rest of shared memory (2 to
+// 6 stages): with only 2 its stream is latency-bound.
 bool wave_cfg(const Geom& g, int* TY, int* ZC, int* NS, int* NSM, size_t* stage_bytes, size_t* mstage_bytes)
 {
     if (g.esize != 4) return false;
@@ -355,17 +360,24 @@ bool wave_cfg(const Geom& g, int* TY, int* ZC, int* NS, int* NSM, size_t* stage_
     for (; ty >= 1; --ty) {
         const size_t sb = ((size_t)(ty + 2 * WR) * g.pitch * 4 + 127) / 128 * 128;
         const size_t mb = ((size_t)2 * ty * g.pitch * 4 + 127) / 128 * 128;
-        // 5 u planes resident + 2 in flight; 2 (m, u^{n-1}) stages
-        if (sb * 7 + mb * 2 + 256 <= W_SMEM) {
+        const size_t fixed = 7 * sb + 256;
+        if (fixed + mb * 2 <= W_SMEM) {
             *TY = ty;
-            *NS = (int)std::min<size_t>(8, (W_SMEM - mb * 2 - 256) / sb);
-            *NSM = 2;
+            *NS = 7;
+            *NSM = (int)std::min<size_t>(6, (W_SMEM - fixed) / mb);
             *stage_bytes = sb;
             *mstage_bytes = mb;
             break;
         }
     }
     if (ty < 1) return false;
+    int eNS = 0, eNSM = 0;  // "NS,NSM" for tuning sweeps
+    const char* env = std::getenv("ST_WAVE_CFG");
+    if (env && std::sscanf(env, "%d,%d", &eNS, &eNSM) == 2 && eNS >= 7 - 2 && eNSM >= 2 &&
+        (size_t)eNS * *stage_bytes + (size_t)eNSM * *mstage_bytes + 256 <= 227 * 1024 - 16 * (eNS + eNSM)) {
+        *NS = eNS;
+        *NSM = eNSM;
+    }
     const int nyt = (int)((g.ny + *TY - 1) / *TY);
     const int64_t want = 6LL * wave_sm_count();
     const int64_t nzc = std::max<int64_t>(1, want / nyt);
