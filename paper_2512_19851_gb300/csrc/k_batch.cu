@@ -13,10 +13,12 @@
 //    one read of tile+halo and one write, instead of k reads and k writes.
 //  * One launch covers all passes: CTAs meet at a grid-wide barrier between
 //    passes (cooperative launch guarantees co-residency; the wait is bounded
-//    and sets ST_ERR_DEVICE_TIMEOUT if it runs out).  Loads that follow a
-//    barrier bypass L1 (ld.global.cg), since other SMs wrote that data.  If a
-//    cooperative launch is unavailable, one launch per pass is used (same
-//    arithmetic).
+//    and sets ST_ERR_DEVICE_TIMEOUT if it runs out).  The barrier's
+//    gpu-scope acquire orders the next pass's tile copies after the other
+//    SMs' writes.  If a cooperative launch is unavailable, one launch per pass
+//    is used (same arithmetic).
+//  * Tiles are copied into shared memory by asynchronous element copies
+//    (cp.async), so a warp keeps a whole row of loads in flight.
 //  * Arithmetic order is the same as the single-grid kernels: acc = 0, then
 //    acc = fma(w_k, u[p + o_k], acc) over the offsets in the given order, so a
 //    grid gives bit-identical results batched or alone.
@@ -103,12 +105,6 @@ __device__ bool grid_barrier(unsigned* arrivals, unsigned expected, const BatchP
     return s_ok != 0;
 }
 
-template <typename T>
-__device__ __forceinline__ T ld_cg(const T* p)
-{
-    return __ldcg(p);
-}
-
 // One pass of kp steps over one tile.
 //
 // Load: tile + kp-wide halo into s0, rows by warps, columns by lanes (wrapped
@@ -136,18 +132,21 @@ __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int sr
         if (PERIODIC) gy = wrapn(gy, ny);
         const T* srow = src + (int64_t)gy * pitch;
         T* srow_s = s0 + ly * RS;
+        // asynchronous element copies: a warp issues its whole row without
+        // waiting on any load
         for (int lx = lane; lx < W; lx += 32) {
             int gx = t.x0 - kp + lx;
-            T v;
             if (PERIODIC) {
                 gx = wrapn(gx, nx);
-                v = ld_cg(srow + gx);
+                ptx::cp_async_elem<sizeof(T)>(srow_s + lx, srow + gx);
+            } else if (yout || gx < 0 || gx >= nx) {
+                srow_s[lx] = bc;
             } else {
-                v = (yout || gx < 0 || gx >= nx) ? bc : ld_cg(srow + gx);
+                ptx::cp_async_elem<sizeof(T)>(srow_s + lx, srow + gx);
             }
-            srow_s[lx] = v;
         }
     }
+    ptx::cp_async_wait_all();
     __syncthreads();
     T w[9];
 #pragma unroll

@@ -88,6 +88,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Asynchronous copy of one 4- or 8-byte element global -> shared (through L1;
+// after a grid-wide barrier with acquire semantics the line is re-fetched).
+// Completion: cp_async_wait_all.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src)
+{
+    static_assert(BYTES == 4 || BYTES == 8, "element copies are 4 or 8 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Hint: bring the 128-byte line holding p into L2 (no register, no wait).
 __device__ __forceinline__ void prefetch_l2(const void* p)
 {
