@@ -97,6 +97,10 @@ struct st_grid_s {
     BatchPlan* plan = nullptr;  // 2D grids on the persistent tile kernel (a batch of one)
     bool plan_bound = false;
     void* staging = nullptr;    // dense interior buffer of stencil_run_host
+    // stencil_run_host splits each host copy over a few streams so that
+    // several copy engines share it (created on first use)
+    cudaStream_t cstream[4] = {};
+    cudaEvent_t cfork = nullptr, cjoin[4] = {};
 };
 
 static void drop_graphs(st_grid_t g)
@@ -250,6 +254,11 @@ st_status stencil_destroy(st_grid_t g)
         delete g->plan;
     }
     if (g->staging) cudaFree(g->staging);
+    for (int c = 0; c < 4; ++c) {
+        if (g->cstream[c]) cudaStreamDestroy(g->cstream[c]);
+        if (g->cjoin[c]) cudaEventDestroy(g->cjoin[c]);
+    }
+    if (g->cfork) cudaEventDestroy(g->cfork);
     delete g;
     return ST_OK;
 }
@@ -574,12 +583,34 @@ st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* h
             return fail(ST_ERR_OOM, "stencil_run_host: staging allocation failed");
         }
     }
-    ST_CUDA_TRY(cudaMemcpyAsync(g->staging, host_u0, bytes, cudaMemcpyHostToDevice, s));
+    if (!g->cfork) {
+        for (int c = 0; c < 4; ++c) {
+            ST_CUDA_TRY(cudaStreamCreateWithFlags(&g->cstream[c], cudaStreamNonBlocking));
+            ST_CUDA_TRY(cudaEventCreateWithFlags(&g->cjoin[c], cudaEventDisableTiming));
+        }
+        ST_CUDA_TRY(cudaEventCreateWithFlags(&g->cfork, cudaEventDisableTiming));
+    }
+    // one host copy as four concurrent pieces, forked from and joined back
+    // into the caller's stream
+    auto copy4 = [&](void* dst, const void* src, cudaMemcpyKind kind) -> cudaError_t {
+        const size_t piece = (bytes / 4 + 255) / 256 * 256;
+        cudaError_t e = cudaEventRecord(g->cfork, s);
+        for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+            const size_t off = std::min(bytes, (size_t)c * piece), n = std::min(piece, bytes - off);
+            e = cudaStreamWaitEvent(g->cstream[c], g->cfork, 0);
+            if (e == cudaSuccess && n > 0)
+                e = cudaMemcpyAsync((char*)dst + off, (const char*)src + off, n, kind, g->cstream[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(g->cjoin[c], g->cstream[c]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g->cjoin[c], 0);
+        }
+        return e;
+    };
+    ST_CUDA_TRY(copy4(g->staging, host_u0, cudaMemcpyHostToDevice));
     ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 0, s));
     rc = stencil_step(g, nsteps, stream);
     if (rc != ST_OK) return rc;
     ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 1, s));
-    ST_CUDA_TRY(cudaMemcpyAsync(host_uT, g->staging, bytes, cudaMemcpyDeviceToHost, s));
+    ST_CUDA_TRY(copy4(host_uT, g->staging, cudaMemcpyDeviceToHost));
     return ST_OK;
 }
 
