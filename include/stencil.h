@@ -36,7 +36,8 @@
  *     keeps them alive while a handle uses them.  The library allocates only
  *     its own scratch (status word, reduction partials, source table, batch
  *     tables, tuning copies) in bind/set/tune calls, and the host staging
- *     buffer and copy streams in the first stencil_run_host; never in a step.
+ *     buffer and copy streams in the first stencil_run_host that needs them;
+ *     never in a step.
  *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
  *     void*, NULL = legacy default stream) and is asynchronous, except
  *     stencil_sync() and the *_tune() calls, which synchronise that stream.
@@ -196,14 +197,15 @@ st_status stencil_tune_config(st_grid_t g, int* cfg);
 /*
  * End-to-end form of stencil_step for callers whose data is on the host:
  * copies host_u0 (dense interior, C order, the grid's dtype) into the current
- * level, runs nsteps, copies the newest level's interior to host_uT.  Each
- * direction is a contiguous copy into a dense device staging buffer, split in
- * four pieces on the handle's own copy streams (forked from and joined back
- * into `stream` by events), plus a device (un)pack kernel into the padded
- * layout; the first call on a handle allocates that buffer (interior size)
- * and the streams, later calls reuse them.  Everything is ordered on `stream`
- * (pinned host memory makes the copies asynchronous); the call returns after
- * enqueueing.  One time level only.
+ * level, runs nsteps, copies the newest level's interior to host_uT.  A
+ * pinned (page-locked, device-mapped) host buffer is read or written directly
+ * by the device (un)pack kernel.  Any other host buffer goes through a dense
+ * device staging buffer: a contiguous copy split in four pieces on the
+ * handle's own copy streams (forked from and joined back into `stream` by
+ * events) plus the (un)pack kernel; the first such call allocates the buffer
+ * (interior size) and the streams, later calls reuse them.  Everything is
+ * ordered on `stream` and the call returns after enqueueing (with pageable
+ * host memory the copies may block the calling thread).  One time level only.
  */
 st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* host_uT,
                            void* stream);

@@ -575,15 +575,29 @@ st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* h
     cudaStream_t s = (cudaStream_t)stream;
     const Geom& G = g->g;
     const size_t bytes = (size_t)G.npoints * G.esize;
-    if (!g->staging) {
-        // one dense interior buffer: a single contiguous copy per direction runs
-        // at link speed, where a row-strided 3D copy pays per row
+    // Pinned host buffers are mapped into the device address space: the
+    // (un)pack kernels then read and write them directly over the host link,
+    // with many requests in flight.  Other host memory goes through a dense
+    // device staging buffer and copy engines.
+    auto mapped = [](const void* p) -> void* {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+    };
+    void* din = mapped(host_u0);
+    void* dout = mapped(host_uT);
+    if ((!din || !dout) && !g->staging) {
+        // one dense interior buffer: a contiguous copy per direction runs at
+        // link speed, where a row-strided 3D copy pays per row
         if (cudaMalloc(&g->staging, bytes) != cudaSuccess) {
             (void)cudaGetLastError();
             return fail(ST_ERR_OOM, "stencil_run_host: staging allocation failed");
         }
     }
-    if (!g->cfork) {
+    if ((!din || !dout) && !g->cfork) {
         for (int c = 0; c < 4; ++c) {
             ST_CUDA_TRY(cudaStreamCreateWithFlags(&g->cstream[c], cudaStreamNonBlocking));
             ST_CUDA_TRY(cudaEventCreateWithFlags(&g->cjoin[c], cudaEventDisableTiming));
@@ -605,12 +619,20 @@ st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* h
         }
         return e;
     };
-    ST_CUDA_TRY(copy4(g->staging, host_u0, cudaMemcpyHostToDevice));
-    ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 0, s));
+    if (din) {
+        ST_CUDA_TRY(launch_pack(G.esize, din, g->buf[g->cur], G, 0, s));
+    } else {
+        ST_CUDA_TRY(copy4(g->staging, host_u0, cudaMemcpyHostToDevice));
+        ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 0, s));
+    }
     rc = stencil_step(g, nsteps, stream);
     if (rc != ST_OK) return rc;
-    ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 1, s));
-    ST_CUDA_TRY(copy4(host_uT, g->staging, cudaMemcpyDeviceToHost));
+    if (dout) {
+        ST_CUDA_TRY(launch_pack(G.esize, dout, g->buf[g->cur], G, 1, s));
+    } else {
+        ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 1, s));
+        ST_CUDA_TRY(copy4(host_uT, g->staging, cudaMemcpyDeviceToHost));
+    }
     return ST_OK;
 }
 

@@ -105,15 +105,56 @@ __device__ bool grid_barrier(unsigned* arrivals, unsigned expected, const BatchP
     return s_ok != 0;
 }
 
+// Shared tile rows: element (row ly, column lx) of a tile buffer sits at
+// ly * row_stride + BPAD + lx, so 4-column groups are 16-byte aligned and the
+// columns -1 and W .. W+3 exist (their values are never used by an interior
+// point).
+constexpr int BPAD = 4;
+
+template <typename T>
+__device__ __forceinline__ void ld6(const T* p, T (&v)[6])  // columns -1 .. 4 around a group
+{
+    v[0] = p[-1];
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[1] = q.x;
+        v[2] = q.y;
+        v[3] = q.z;
+        v[4] = q.w;
+    } else {
+        const double2 q0 = *reinterpret_cast<const double2*>(p);
+        const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+        v[1] = q0.x;
+        v[2] = q0.y;
+        v[3] = q1.x;
+        v[4] = q1.y;
+    }
+    v[5] = p[4];
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&o)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(o[2], o[3]);
+    }
+}
+
 // One pass of kp steps over one tile.
 //
 // Load: tile + kp-wide halo into s0, rows by warps, columns by lanes (wrapped
 // for a periodic boundary, the boundary value outside a Dirichlet domain).
-// Each step: threads own column strips (64 columns per row band, blockDim/64
-// bands); a thread walks its strip top to bottom keeping the three rows of
-// its 3x3 window in registers, so each point costs three shared loads and
-// nine FMAs.  The weights sit in a row-major 3x3 table (absent offsets 0), so
-// the FMA order is row-major over (dy, dx): the order of the box offsets.
+// Each step: threads own 4-column groups in row bands; a thread walks its
+// group down its band keeping the three rows of its 3x3 window (the group and
+// one column on each side) in registers, so 4 points cost one 16-byte shared
+// load, two scalar ones, 36 FMAs and one 16-byte store.  Groups reach past
+// the shrinking region's edge; those columns hold values that no later
+// interior point reads.  The weights sit in a row-major 3x3 table (absent
+// offsets 0), so the FMA order is row-major over (dy, dx): the order of the
+// box offsets.
 template <typename T, int SHAPE, bool PERIODIC>
 __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int src_slot, T* s0, T* s1)
 {
@@ -131,7 +172,7 @@ __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int sr
         const bool yout = !PERIODIC && (gy < 0 || gy >= ny);
         if (PERIODIC) gy = wrapn(gy, ny);
         const T* srow = src + (int64_t)gy * pitch;
-        T* srow_s = s0 + ly * RS;
+        T* srow_s = s0 + BPAD + ly * RS;
         // asynchronous element copies: a warp issues its whole row without
         // waiting on any load
         for (int lx = lane; lx < W; lx += 32) {
@@ -151,76 +192,79 @@ __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int sr
     T w[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) w[i] = T(G.w[i]);
-    const int nb = blockDim.x >> 6;  // row bands
-    const int cx = threadIdx.x & 63, band = threadIdx.x >> 6;
-    T* in = s0;
-    T* out = s1;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const T* in = s0 + BPAD;
+    T* out = s1 + BPAD;
     for (int j = 1; j <= kp; ++j) {
         const bool last = j == kp;
-        const int rw = W - 2 * j, rh = H - 2 * j;
-        const int bh = (rh + nb - 1) / nb;
-        const int r0 = j + band * bh, r1 = min(j + rh, r0 + bh);
-        for (int lx = j + cx; lx < j + rw; lx += 64) {
-            if (r0 >= r1) break;
+        const int c0 = j, c1 = W - j;  // region of this step: columns [c0, c1), rows [j, H - j)
+        const int g0 = c0 >> 2, ng = ((c1 - 1) >> 2) - g0 + 1;
+        const int nb = max(1, nthr / ng);  // row bands
+        const int gi = tid % ng, band = tid / ng;
+        const int rh = H - 2 * j, bh = (rh + nb - 1) / nb;
+        const int r0 = j + band * bh, r1 = min(H - j, r0 + bh);
+        if (band < nb && r0 < r1) {
+            const int lx = (g0 + gi) * 4;  // first column of the group
+            const int gx0 = t.x0 - kp + lx;
             const T* pin = in + (r0 - 1) * RS + lx;  // row above the first output row
-            T a0 = pin[-1], a1 = pin[0], a2 = pin[1];
+            T A[6], B[6];
+            ld6(pin, A);
             pin += RS;
-            T b0 = pin[-1], b1 = pin[0], b2 = pin[1];
+            ld6(pin, B);
             pin += RS;  // row below the current output row
-            const int gx = t.x0 - kp + lx;
-            const bool xout = !PERIODIC && (gx < 0 || gx >= nx);
-            auto point = [&](T c0, T c1, T c2) -> T {
-                T acc;
-                if constexpr (SHAPE == SHAPE_BOX9) {
-                    acc = fma(w[0], a0, T(0));
-                    acc = fma(w[1], a1, acc);
-                    acc = fma(w[2], a2, acc);
-                    acc = fma(w[3], b0, acc);
-                    acc = fma(w[4], b1, acc);
-                    acc = fma(w[5], b2, acc);
-                    acc = fma(w[6], c0, acc);
-                    acc = fma(w[7], c1, acc);
-                    acc = fma(w[8], c2, acc);
-                } else {  // five-point star: the corners carry no weight
-                    acc = fma(w[1], a1, T(0));
-                    acc = fma(w[3], b0, acc);
-                    acc = fma(w[4], b1, acc);
-                    acc = fma(w[5], b2, acc);
-                    acc = fma(w[7], c1, acc);
-                }
-                return acc;
-            };
-            if (!last) {
-                T* po = out + r0 * RS + lx;
-                for (int ly = r0; ly < r1; ++ly) {
-                    const T c0 = pin[-1], c1 = pin[0], c2 = pin[1];
-                    T acc = point(c0, c1, c2);
-                    if (!PERIODIC) {
-                        const int gy = t.y0 - kp + ly;
-                        if (xout || gy < 0 || gy >= ny) acc = bc;  // ghost stays fixed
+            for (int ly = r0; ly < r1; ++ly) {
+                T C[6];
+                ld6(pin, C);
+                T o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    T acc;
+                    if constexpr (SHAPE == SHAPE_BOX9) {
+                        acc = fma(w[0], A[e], T(0));
+                        acc = fma(w[1], A[e + 1], acc);
+                        acc = fma(w[2], A[e + 2], acc);
+                        acc = fma(w[3], B[e], acc);
+                        acc = fma(w[4], B[e + 1], acc);
+                        acc = fma(w[5], B[e + 2], acc);
+                        acc = fma(w[6], C[e], acc);
+                        acc = fma(w[7], C[e + 1], acc);
+                        acc = fma(w[8], C[e + 2], acc);
+                    } else {  // five-point star: the corners carry no weight
+                        acc = fma(w[1], A[e + 1], T(0));
+                        acc = fma(w[3], B[e], acc);
+                        acc = fma(w[4], B[e + 1], acc);
+                        acc = fma(w[5], B[e + 2], acc);
+                        acc = fma(w[7], C[e + 1], acc);
                     }
-                    *po = acc;
-                    po += RS;
-                    pin += RS;
-                    a0 = b0; a1 = b1; a2 = b2;
-                    b0 = c0; b1 = c1; b2 = c2;
+                    o[e] = acc;
                 }
-            } else {  // last step: the region is the tile interior, written to global memory
-                T* po = dst + (int64_t)(t.y0 - kp + r0) * pitch + gx;
-                for (int ly = r0; ly < r1; ++ly) {
-                    const T c0 = pin[-1], c1 = pin[0], c2 = pin[1];
-                    *po = point(c0, c1, c2);
-                    po += pitch;
-                    pin += RS;
-                    a0 = b0; a1 = b1; a2 = b2;
-                    b0 = c0; b1 = c1; b2 = c2;
+                if (!last) {
+                    if (!PERIODIC) {  // ghost points of the halo stay fixed
+                        const int gy = t.y0 - kp + ly;
+                        const bool yo = gy < 0 || gy >= ny;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (yo || gx0 + e < 0 || gx0 + e >= nx) o[e] = bc;
+                    }
+                    st4(out + ly * RS + lx, o);
+                } else {  // last step: the region is the tile interior, written to global memory
+                    T* po = dst + (int64_t)(t.y0 - kp + ly) * pitch + gx0;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (lx + e >= c0 && lx + e < c1) po[e] = o[e];
                 }
+#pragma unroll
+                for (int e = 0; e < 6; ++e) {
+                    A[e] = B[e];
+                    B[e] = C[e];
+                }
+                pin += RS;
             }
         }
         __syncthreads();
-        T* tmp = in;
+        const T* tmp = in;
         in = out;
-        out = tmp;
+        out = const_cast<T*>(tmp);
     }
 }
 
@@ -272,8 +316,8 @@ int batch_sm_count()
 
 size_t tile_smem(int TW, int TH, int k, int esize, int* row_stride)
 {
-    int rs = TW + 2 * k;
-    if ((rs & 31) == 0) rs += 1;  // avoid bank-aligned rows
+    // BPAD columns before a row and at least 4 after it, 16-byte multiple
+    const int rs = (TW + 2 * k + 8 + 3) / 4 * 4;
     *row_stride = rs;
     return (size_t)2 * (TH + 2 * k) * rs * esize;
 }

@@ -310,6 +310,26 @@ k_reduce_final(const double* __restrict__ partials, int nblocks, double* __restr
 
 // Dense interior <-> padded layout (dir 0: dense -> padded, 1: padded -> dense).
 // One block per interior row.
+// 16-byte groups of V elements, for rows whose length is a multiple of V and a
+// 16-byte aligned dense buffer (the padded interior rows always are).
+template <typename T, typename V>
+__global__ void __launch_bounds__(256) k_pack_v(T* __restrict__ dense, T* __restrict__ padded, Geom g, int dir)
+{
+    constexpr int VE = sizeof(V) / sizeof(T);
+    const int64_t rows = g.nz * g.ny;
+    const uint32_t ny32 = (uint32_t)g.ny;
+    const int64_t nv = g.nx / VE;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const uint32_t z = (uint32_t)row / ny32, y = (uint32_t)row - z * ny32;
+        V* pr = reinterpret_cast<V*>(padded + g.origin + (int64_t)z * g.plane + (int64_t)y * g.pitch);
+        V* dr = reinterpret_cast<V*>(dense + row * g.nx);
+        if (dir == 0)
+            for (int64_t x = threadIdx.x; x < nv; x += blockDim.x) pr[x] = dr[x];
+        else
+            for (int64_t x = threadIdx.x; x < nv; x += blockDim.x) dr[x] = pr[x];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_pack(T* __restrict__ dense, T* __restrict__ padded, Geom g, int dir)
 {
@@ -366,10 +386,18 @@ cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int
 {
     const int64_t rows = g.nz * g.ny;
     const unsigned blocks = (unsigned)(rows < 65535 * 8 ? rows : 65535 * 8);
-    if (esize == 8)
-        k_pack<double><<<blocks, 256, 0, s>>>((double*)dense, (double*)padded, g, dir);
-    else
-        k_pack<float><<<blocks, 256, 0, s>>>((float*)dense, (float*)padded, g, dir);
+    const bool vec = ((g.nx * esize) % 16 == 0) && (((uintptr_t)dense & 15u) == 0);
+    if (esize == 8) {
+        if (vec)
+            k_pack_v<double, double2><<<blocks, 256, 0, s>>>((double*)dense, (double*)padded, g, dir);
+        else
+            k_pack<double><<<blocks, 256, 0, s>>>((double*)dense, (double*)padded, g, dir);
+    } else {
+        if (vec)
+            k_pack_v<float, float4><<<blocks, 256, 0, s>>>((float*)dense, (float*)padded, g, dir);
+        else
+            k_pack<float><<<blocks, 256, 0, s>>>((float*)dense, (float*)padded, g, dir);
+    }
     return cudaGetLastError();
 }
 

@@ -194,16 +194,25 @@ def test_reductions_match_oracle():
         g.close()
 
 
-def test_run_host_end_to_end():
+@pytest.mark.parametrize("nx", [64, 45])
+@pytest.mark.parametrize("pinned_in,pinned_out", [(True, True), (False, False), (True, False)])
+def test_run_host_end_to_end(nx, pinned_in, pinned_out):
+    """Pinned buffers are read/written by the pack kernels directly; pageable
+    ones go through the staging copies (rows of 45 are not whole 16-byte
+    groups, so the scalar pack kernel runs too)."""
     from paper_2512_19851_gb300 import abi
     from paper_2512_19851_gb300.grid import Grid
-    shape = (20, 33, 64)
+    shape = (20, 33, nx)
     h = inputs.heat3d(shape=shape)
     offs, w = seven_point(0.1)
     for dtype, npdt in ((torch.float32, np.float32), (torch.float64, np.float64)):
         g = Grid(shape, offs, w, periodic=True, dtype=dtype)
-        src = torch.from_numpy(h.u0.astype(npdt)).pin_memory()
-        dst = torch.empty(shape, dtype=dtype).pin_memory()
+        src = torch.from_numpy(h.u0.astype(npdt))
+        dst = torch.empty(shape, dtype=dtype)
+        if pinned_in:
+            src = src.pin_memory()
+        if pinned_out:
+            dst = dst.pin_memory()
         abi.stencil_run_host(g.h, 12, src.data_ptr(), dst.data_ptr(), torch.cuda.current_stream())
         g.sync()
         ref = oracle.sweep_const(h.u0, offs, w, True, 0.0, 12)
