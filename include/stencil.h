@@ -87,6 +87,9 @@ typedef enum { ST_DIRICHLET = 0, ST_PERIODIC = 1 } st_bc;
 /* stencil_create flags */
 #define ST_FLAG_GENERIC 1u   /* always use the one-thread-per-point kernel (the
                                 paper's generated-kernel shape, Sec. III-C) */
+#define ST_FLAG_TWO_STEP 2u  /* start with two sweeps per pass over HBM where
+                                supported (FP32 constant symmetric 3D 7-point
+                                star); stencil_tune may change the choice */
 
 #define ST_MAX_POINTS 64     /* most neighbour points per stencil */
 #define ST_MAX_RADIUS 8      /* widest ghost region */
@@ -118,7 +121,7 @@ const char* stencil_last_error(void);
  *   bc          ST_DIRICHLET (ghosts = bc_value) or ST_PERIODIC.
  *   dtype       storage and arithmetic type of the fields.
  *   time_levels 1: form (1); 2: leapfrog form (3).
- *   flags       ST_FLAG_GENERIC or 0.
+ *   flags       0, ST_FLAG_GENERIC or ST_FLAG_TWO_STEP.
  * Copies all arrays; allocates only library scratch.  *out is NULL on error.
  */
 st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radius, int npts,
@@ -155,7 +158,8 @@ st_status stencil_bind(st_grid_t g, int slot, void* dev_ptr);
 st_status stencil_mark_dirty(st_grid_t g, int slot);
 
 /* Which time-level slot (ST_SLOT_A or ST_SLOT_B) holds the newest level u_t.
- * With two time levels the other slot holds u_{t-1}. */
+ * With two time levels the other slot holds u_{t-1}; with one, the other
+ * slot holds an older level (u_{t-1}, or u_{t-2} after a two-step pass). */
 st_status stencil_current(st_grid_t g, int* slot);
 st_status stencil_set_current(st_grid_t g, int slot);
 
@@ -174,24 +178,31 @@ st_status stencil_get_step_index(st_grid_t g, int64_t* t);
 
 /*
  * Advance nsteps >= 0 steps on `stream`: refresh stale ghosts, then sweep,
- * swapping the current slot after every step.  Enqueued as one CUDA graph
- * per (handle, nsteps parity) after the first call with that nsteps; the
- * launch sequence is the same either way.
+ * each launch writing the other slot.  When stencil_tune chose two-step
+ * passes (the constant symmetric 7-point star, FP32, no source) a launch
+ * advances two steps (temporal blocking; the results equal single steps bit
+ * for bit), so the newest level's slot follows the launch count:
+ * stencil_current() tells which.  Enqueued as one
+ * CUDA graph per (handle, nsteps, current slot) after the first call with
+ * that nsteps; the launch sequence is the same either way.
  */
 st_status stencil_step(st_grid_t g, int nsteps, void* stream);
 
 /*
  * Autotune the launch configuration of this grid for nsteps-step calls (2D
  * grids on the persistent tile kernel: tile shape, threads per block, steps
- * per shared-memory pass; other families have nothing to tune and return
- * ST_OK).  Times the candidates on the bound data and restores it afterwards;
- * synchronises `stream`.  With temporal blocking a call may leave the newest
- * level in either slot: stencil_current() tells which.
+ * per shared-memory pass; the FP32 constant symmetric 3D 7-point star: one
+ * sweep or two sweeps per pass over HBM; other families have nothing to tune
+ * and return ST_OK).  Times the candidates on the bound data and restores the
+ * current level afterwards (the other slot is scratch); synchronises
+ * `stream`.  With temporal blocking a call may leave the newest level in
+ * either slot: stencil_current() tells which.
  */
 st_status stencil_tune(st_grid_t g, int nsteps, void* stream);
 
 /* The configuration in use (cfg[0] tile x, cfg[1] tile y, cfg[2] threads,
- * cfg[3] steps per pass); zeros for families without one. */
+ * cfg[3] steps per pass; 3D 7-point star: zeros and the steps per pass);
+ * zeros for families without one. */
 st_status stencil_tune_config(st_grid_t g, int* cfg);
 
 /*

@@ -96,6 +96,7 @@ struct st_grid_s {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     BatchPlan* plan = nullptr;  // 2D grids on the persistent tile kernel (a batch of one)
     bool plan_bound = false;
+    bool pairs = false;         // two-step passes chosen by stencil_tune (3D 7-point heat, FP32)
     void* staging = nullptr;    // dense interior buffer of stencil_run_host
     // stencil_run_host splits each host copy over a few streams so that
     // several copy engines share it (created on first use)
@@ -155,7 +156,7 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     if (bc != ST_DIRICHLET && bc != ST_PERIODIC) return fail(ST_ERR_ARG, "stencil_create: bad bc");
     if (dtype != ST_F32 && dtype != ST_F64) return fail(ST_ERR_ARG, "stencil_create: bad dtype");
     if (time_levels != 1 && time_levels != 2) return fail(ST_ERR_ARG, "stencil_create: time_levels must be 1 or 2");
-    if (flags & ~ST_FLAG_GENERIC) return fail(ST_ERR_ARG, "stencil_create: unknown flags");
+    if (flags & ~(ST_FLAG_GENERIC | ST_FLAG_TWO_STEP)) return fail(ST_ERR_ARG, "stencil_create: unknown flags");
     if (radius < 0 || radius > ST_MAX_RADIUS) return fail(ST_ERR_ARG, "stencil_create: radius out of range");
     int64_t d3[3] = {1, 1, 1};
     for (int i = 0; i < ndim; ++i) {
@@ -205,6 +206,7 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     g->dtype = dtype;
     g->levels = time_levels;
     g->flags = flags;
+    g->pairs = (flags & ST_FLAG_TWO_STEP) != 0;
     FamilyDesc d{};
     d.g = g->g;
     d.npts = npts;
@@ -445,12 +447,31 @@ static st_status check_ready(st_grid_t g, const char* who)
     return ST_OK;
 }
 
+// Two-step passes (temporal blocking) where the family has them; a source
+// term needs its step index per sweep, so it keeps single sweeps.
+static bool use_pairs(st_grid_t g) { return g->pairs && g->src < 0 && star3d_pair_supported(g->fam); }
+
+// Slot of the newest level after n steps from slot `cur`: every launch (one
+// sweep or one two-step pass) writes the other slot.
+static int final_slot(st_grid_t g, int cur, int n)
+{
+    const int launches = use_pairs(g) ? n / 2 + (n & 1) : n;
+    return (launches & 1) ? 1 - cur : cur;
+}
+
 static st_status enqueue_steps(st_grid_t g, int cur, int64_t step0, int n, cudaStream_t s)
 {
-    for (int i = 0; i < n; ++i) {
+    const bool pairs = use_pairs(g);
+    for (int i = 0; i < n;) {
         const int nxt = 1 - cur;
         SweepArgs a = sweep_args(g, g->buf[cur], g->buf[nxt], step0 + i);
-        ST_CUDA_TRY(launch_family(g->fam, a, s));
+        if (pairs && n - i >= 2) {
+            ST_CUDA_TRY(launch_star3d_pair(g->fam, a, g->bc_value, s));
+            i += 2;
+        } else {
+            ST_CUDA_TRY(launch_family(g->fam, a, s));
+            i += 1;
+        }
         cur = nxt;
     }
     return ST_OK;
@@ -528,7 +549,7 @@ st_status stencil_step(st_grid_t g, int nsteps, void* stream)
         }
         ST_CUDA_TRY(cudaGraphLaunch(it->second, s));
     }
-    if (nsteps & 1) g->cur = 1 - g->cur;
+    g->cur = final_slot(g, g->cur, nsteps);
     g->step += nsteps;
     return ST_OK;
 }
@@ -543,6 +564,44 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
     g->last = s;
     rc = refresh_ghosts(g, s);
     if (rc != ST_OK) return rc;
+    if ((!g->plan || !g->plan_bound) && g->levels == 1 && g->src < 0 && star3d_pair_supported(g->fam)) {
+        // single sweeps or two-step passes: time both on the bound data, keep
+        // the faster, and put the current level back
+        const size_t bytes = (size_t)g->g.elems * g->g.esize;
+        void* keep = nullptr;
+        if (cudaMalloc(&keep, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(ST_ERR_OOM, "stencil_tune: backup allocation failed");
+        }
+        const int cur0 = g->cur;
+        const int64_t step0 = g->step;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        float ms[2] = {0.f, 0.f};
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(keep, g->buf[cur0], bytes, cudaMemcpyDeviceToDevice, s);
+        for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+            g->pairs = v == 1;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms up
+                e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess && enqueue_steps(g, cur0, step0, nsteps, s) != ST_OK) e = cudaErrorUnknown;
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[v], e0, e1);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(g->buf[cur0], keep, bytes, cudaMemcpyDeviceToDevice, s);
+            }
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        g->pairs = e == cudaSuccess && ms[1] < ms[0];
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(keep);
+        g->cur = cur0;
+        g->step = step0;
+        drop_graphs(g);
+        if (e != cudaSuccess) return cuda_fail(e, "stencil_tune");
+        return ST_OK;
+    }
     if (!g->plan || !g->plan_bound) {
         ST_CUDA_TRY(cudaStreamSynchronize(s));
         return ST_OK;  // this family has nothing to tune
@@ -558,7 +617,8 @@ st_status stencil_tune_config(st_grid_t g, int* cfg)
 {
     if (!g || !cfg) return fail(ST_ERR_ARG, "stencil_tune_config: NULL argument");
     if (!g->plan) {
-        cfg[0] = cfg[1] = cfg[2] = cfg[3] = 0;
+        cfg[0] = cfg[1] = cfg[2] = 0;
+        cfg[3] = star3d_pair_supported(g->fam) ? (g->pairs ? 2 : 1) : 0;
         return ST_OK;
     }
     batch_plan_config(*g->plan, cfg);
@@ -708,7 +768,7 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stre
         const int seg = std::min(m, nsteps - t);
         rc = enqueue_steps(g, g->cur, g->step, seg, s);
         if (rc != ST_OK) return rc;
-        if (seg & 1) g->cur = 1 - g->cur;
+        g->cur = final_slot(g, g->cur, seg);
         g->step += seg;
     }
     return ST_OK;

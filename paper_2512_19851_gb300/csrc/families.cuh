@@ -81,6 +81,9 @@ cudaError_t launch_family_adjoint(const Family& f, const AdjointArgs& a, cudaStr
 cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_star3d_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
 int star3d_adjoint_fuse(const Family& f);
+// Two sweeps per pass of the constant symmetric 7-point star (FP32): a.in -> a.out
+bool star3d_pair_supported(const Family& f);
+cudaError_t launch_star3d_pair(const Family& f, const SweepArgs& a, double bc_value, cudaStream_t s);
 bool star3d_supports(const FamilyDesc& d, int* variant, const char** name);
 cudaError_t launch_tile2d(const Family& f, const SweepArgs& a, cudaStream_t s);
 bool wave_supports(const FamilyDesc& d);

@@ -371,10 +371,13 @@ bool wave_cfg(const Geom& g, int* TY, int* ZC, int* NS, int* NSM, size_t* stage_
         }
     }
     if (ty < 1) return false;
-    int eNS = 0, eNSM = 0;  // "NS,NSM" for tuning sweeps
+    int eNS = 0, eNSM = 0, eZC = 0;  // "NS,NSM,ZC" for tuning sweeps
     const char* env = std::getenv("ST_WAVE_CFG");
-    if (env && std::sscanf(env, "%d,%d", &eNS, &eNSM) == 2 && eNS >= 7 - 2 && eNSM >= 2 &&
-        (size_t)eNS * *stage_bytes + (size_t)eNSM * *mstage_bytes + 256 <= 227 * 1024 - 16 * (eNS + eNSM)) {
+    const bool use_env = env && std::sscanf(env, "%d,%d,%d", &eNS, &eNSM, &eZC) == 3 && eNS >= 5 && eNSM >= 2 &&
+                         eZC >= 1 &&
+                         (size_t)eNS * *stage_bytes + (size_t)eNSM * *mstage_bytes + 256 <=
+                             227 * 1024 - 16 * (eNS + eNSM);
+    if (use_env) {
         *NS = eNS;
         *NSM = eNSM;
     }
@@ -382,6 +385,7 @@ bool wave_cfg(const Geom& g, int* TY, int* ZC, int* NS, int* NSM, size_t* stage_
     const int64_t want = 6LL * wave_sm_count();
     const int64_t nzc = std::max<int64_t>(1, want / nyt);
     int zc = (int)std::max<int64_t>(16, (g.nz + nzc - 1) / nzc);
+    if (use_env) zc = eZC;
     *ZC = (int)std::min<int64_t>(zc, g.nz);
     return true;
 }

@@ -25,7 +25,7 @@ class Grid:
     """A grid handle with its two time-level buffers (and coefficient field)."""
 
     def __init__(self, shape, offsets, alpha, beta=None, periodic=False, bc_value=0.0, dtype=torch.float64,
-                 time_levels=1, radius=0, generic=False, device=None):
+                 time_levels=1, radius=0, generic=False, device=None, two_step=False):
         self.shape = tuple(int(s) for s in shape)
         self.ndim = len(self.shape)
         self.dtype = dtype
@@ -33,7 +33,8 @@ class Grid:
         self.periodic = bool(periodic)
         self.h = abi.stencil_create(self.ndim, self.shape, radius, offsets, alpha, beta,
                                     ST_PERIODIC if periodic else ST_DIRICHLET, bc_value, _ST_DTYPE[dtype],
-                                    time_levels, ST_FLAG_GENERIC if generic else 0)
+                                    time_levels, (ST_FLAG_GENERIC if generic else 0) |
+                                    (abi.ST_FLAG_TWO_STEP if two_step else 0))
         self.padded, self.origin, self.elems = abi.stencil_layout(self.h, self.ndim)
         self.radius, self.npts, self.kernel = abi.stencil_info(self.h)
         self.bufs = [torch.zeros(self.padded, dtype=dtype, device=self.device) for _ in range(2)]

@@ -24,10 +24,11 @@ def seven_point(a):
     return inputs.OFFSETS_7PT, [1 - 6 * a] + [a] * 6
 
 
-def run_const(u0, offsets, weights, periodic, bc_value, nsteps, dtype, generic=False, chunks=None):
+def run_const(u0, offsets, weights, periodic, bc_value, nsteps, dtype, generic=False, chunks=None, two_step=False):
     """Run nsteps sweeps on the GPU; chunks splits the run into several
     stencil_step calls (graph and direct paths, odd/even parities)."""
-    g = Grid(u0.shape, offsets, weights, periodic=periodic, bc_value=bc_value, dtype=dtype, generic=generic)
+    g = Grid(u0.shape, offsets, weights, periodic=periodic, bc_value=bc_value, dtype=dtype, generic=generic,
+             two_step=two_step)
     g.set_field(u0)
     for n in (chunks or [nsteps]):
         g.step(n)

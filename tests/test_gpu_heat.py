@@ -137,6 +137,43 @@ def test_heat3d_translation_equivariance_bitwise():
     assert np.array_equal(np.roll(a, s, axis=(0, 1, 2)), b)
 
 
+@pytest.mark.parametrize("shape", [(30, 27, 45), (16, 20, 64), (9, 7, 13), (40, 33, 130), (5, 3, 4)])
+@pytest.mark.parametrize("periodic,bc", [(True, 0.0), (False, 0.0), (False, 0.35)])
+def test_two_step_passes_equal_single_sweeps_bitwise(shape, periodic, bc):
+    """FP32 heat runs two sweeps per launch (temporal blocking); the result must
+    equal single sweeps (one stencil_step(1) call each) bit for bit, for odd and
+    even counts, ragged rows, thin tiles and both boundaries."""
+    h = inputs.heat3d(shape=shape)
+    offs, w = seven_point(0.1)
+    for steps in (2, 7, 12):
+        fused, kern = run_const(h.u0, offs, w, periodic, bc, steps, torch.float32, two_step=True)
+        single, _ = run_const(h.u0, offs, w, periodic, bc, steps, torch.float32, chunks=[1] * steps)
+        assert np.array_equal(fused, single), (shape, periodic, bc, steps, kern)
+    ref = oracle.sweep_const(h.u0, offs, w, periodic, bc, 12)
+    assert rel_err(fused, ref) <= TOL32
+
+
+def test_tune_chooses_between_single_sweeps_and_two_step_passes():
+    """stencil_tune times both forms on the bound data, keeps the faster one,
+    restores the current level, and the tuned grid still matches the oracle."""
+    from paper_2512_19851_gb300 import abi
+    from paper_2512_19851_gb300.grid import Grid
+    shape = (48, 40, 64)
+    h = inputs.heat3d(shape=shape)
+    offs, w = seven_point(0.1)
+    g = Grid(shape, offs, w, periodic=True, dtype=torch.float32)
+    g.set_field(h.u0)
+    before = g.current().clone()
+    g.tune(10)
+    assert torch.equal(g.current(), before)
+    assert abi.stencil_tune_config(g.h)[3] in (1, 2)
+    g.step(10)
+    g.sync()
+    ref = oracle.sweep_const(h.u0, offs, w, True, 0.0, 10)
+    assert rel_err(g.current().double().cpu().numpy(), ref) <= TOL32
+    g.close()
+
+
 def test_deterministic_repeat():
     h = inputs.heat3d(shape=(30, 31, 70))
     offs, w = seven_point(0.1)
