@@ -169,7 +169,13 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
         const int row = active ? ct / ngx : 0;
         const int x = active ? (ct - row * ngx) * 4 : 0;
         const bool full4 = x + 4 <= P.nx;
+        // A Dirichlet row's ghost columns (4 of them, and the pitch padding)
+        // follow it in the staged copy, so 16-byte loads of a ragged last group
+        // stay inside the row and its in-range points see the right
+        // neighbours; only a periodic ragged group must gather wrapped ones.
+        const bool fast = full4 || !PERIODIC;
         const int64_t gofs = P.origin + (y0 + row) * P.pitch + x;  // + z * plane
+        const bool src_here = active && P.sz >= 0 && P.sy == y0 + row && P.sx >= x && P.sx < x + 4;
         float4 q[2 * WR + 1];
 
         auto stage_of = [&](int qq) -> const float* {
@@ -186,14 +192,9 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
         // plane q is a centre (output z0 + q - 4) for q in [4, zce + 4); all
         // other planes of the chunk only feed the z queues
         auto is_centre = [&](int qq) -> bool { return qq >= WR && qq < zce + WR; };
-        auto read4 = [&](const float* rp) -> float4 {
-            if (full4) return *reinterpret_cast<const float4*>(rp + x);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (x + 0 < P.nx) v.x = rp[x + 0];
-            if (x + 1 < P.nx) v.y = rp[x + 1];
-            if (x + 2 < P.nx) v.z = rp[x + 2];
-            return v;
-        };
+        // a staged row holds the whole pitch, so the group's 16 bytes are
+        // always inside it (lanes past the row end read padding they discard)
+        auto read4 = [&](const float* rp) -> float4 { return *reinterpret_cast<const float4*>(rp + x); };
         auto read_q = [&](int qq) -> float4 { return read4(stage_of(qq) + (int64_t)(row + WR) * P.pitch); };
         // prime: queue planes z0-4 .. z0+3 (q = 0..7)
         for (int qq = 0; qq < 2 * WR; ++qq) {
@@ -252,7 +253,7 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
                     add_pair(j, 2, zl.z + zh.z);
                     add_pair(j, 3, zl.w + zh.w);
                 }
-                if (full4) {
+                if (fast) {
 #pragma unroll 2
                     for (int j = 1; j <= WR; ++j) {  // y neighbours
                         const float4 yl = *reinterpret_cast<const float4*>(rc - j * P.pitch + x);
@@ -302,7 +303,7 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
 #pragma unroll
                 for (int e = 0; e < 4; ++e) o[e] = fmaf(mm[e], lb[e], fmaf(P.ac, c[e], -pp[e]) + la[e]);
                 const int64_t z = z0 + i;
-                if (P.sz == z && P.sy == y0 + row && P.sx >= x && P.sx < x + 4) {
+                if (src_here && P.sz == z) {
                     const float amp = (float)P.src_amp[P.step];
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
