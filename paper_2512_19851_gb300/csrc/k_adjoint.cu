@@ -111,6 +111,9 @@ __device__ __forceinline__ void vst(T* p, const T (&v)[AV<T>::N])
     *reinterpret_cast<typename AV<T>::type*>(p) = t;
 }
 
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 __device__ __forceinline__ int64_t amin(int64_t a, int64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ int64_t amax(int64_t a, int64_t b) { return a > b ? a : b; }
 
@@ -338,8 +341,10 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
     X.xfull = X.x + VN <= X.nx;
     const int x = X.x;
     const T ac = T(P.ac), bc = T(P.bc), an = T(P.an), bn = T(P.bn);
-    // mu = w_n * lambda of a staged (lambda, kappa) pair
-    auto mu_of = [&](T l, T k) -> T { return fma(bn, k, an) * l; };
+    // mu = w_n * lambda of a staged (lambda, kappa) pair; the product is
+    // rounded on its own (never contracted into a later add), so every level
+    // and every pass gets the same mu whatever code surrounds it
+    auto mu_of = [&](T l, T k) -> T { return mul_rn(fma(bn, k, an), l); };
 
     bool dead = false;
     uint32_t gq = 0, gr = 0;
@@ -479,7 +484,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                             nsum(X, uap[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
 #pragma unroll
                             for (int e = 0; e < VN; ++e) {
-                                g1n[i][e] = lc[i][e] * fma(bc, uv[i + 1][e], bn * nb[e]);
+                                g1n[i][e] = mul_rn(lc[i][e], fma(bc, uv[i + 1][e], mul_rn(bn, nb[e])));
                                 uap[i][e] = uv[i + 1][e];
                             }
                         }
@@ -619,7 +624,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                                 nsum(X, ubp[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
 #pragma unroll
                                 for (int e = 0; e < VN; ++e) {
-                                    g2[e] = l1p[i][e] * fma(bc, uv[i + 1][e], bn * nb[e]);
+                                    g2[e] = mul_rn(l1p[i][e], fma(bc, uv[i + 1][e], mul_rn(bn, nb[e])));
                                     ubp[i][e] = uv[i + 1][e];
                                 }
                                 add_grad(X, fastw, wscr, lane, P.origin + c2 * P.plane + (y0 + rr0 + i) * P.pitch + x,
