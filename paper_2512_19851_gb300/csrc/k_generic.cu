@@ -315,18 +315,23 @@ k_reduce_final(const double* __restrict__ partials, int nblocks, double* __restr
 template <typename T, typename V>
 __global__ void __launch_bounds__(256) k_pack_v(T* __restrict__ dense, T* __restrict__ padded, Geom g, int dir)
 {
+    // one flat grid-stride loop over (row, group) so that every thread has
+    // work whatever the row length (this kernel may stream host memory);
+    // the caller guarantees fewer than 2^31 groups, so indices are 32-bit
     constexpr int VE = sizeof(V) / sizeof(T);
-    const int64_t rows = g.nz * g.ny;
     const uint32_t ny32 = (uint32_t)g.ny;
-    const int64_t nv = g.nx / VE;
-    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        const uint32_t z = (uint32_t)row / ny32, y = (uint32_t)row - z * ny32;
-        V* pr = reinterpret_cast<V*>(padded + g.origin + (int64_t)z * g.plane + (int64_t)y * g.pitch);
-        V* dr = reinterpret_cast<V*>(dense + row * g.nx);
+    const uint32_t nv = (uint32_t)(g.nx / VE);
+    const uint32_t total = (uint32_t)(g.nz * g.ny) * nv;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const uint32_t row = i / nv;
+        const uint32_t xv = i - row * nv;
+        const uint32_t z = row / ny32, y = row - z * ny32;
+        V* pr = reinterpret_cast<V*>(padded + g.origin + (int64_t)z * g.plane + (int64_t)y * g.pitch) + xv;
+        V* dr = reinterpret_cast<V*>(dense + (int64_t)row * g.nx) + xv;
         if (dir == 0)
-            for (int64_t x = threadIdx.x; x < nv; x += blockDim.x) pr[x] = dr[x];
+            *pr = *dr;
         else
-            for (int64_t x = threadIdx.x; x < nv; x += blockDim.x) dr[x] = pr[x];
+            *dr = *pr;
     }
 }
 
@@ -386,15 +391,17 @@ cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int
 {
     const int64_t rows = g.nz * g.ny;
     const unsigned blocks = (unsigned)(rows < 65535 * 8 ? rows : 65535 * 8);
-    const bool vec = ((g.nx * esize) % 16 == 0) && (((uintptr_t)dense & 15u) == 0);
+    const bool vec = ((g.nx * esize) % 16 == 0) && (((uintptr_t)dense & 15u) == 0) &&
+                     g.npoints * esize / 16 < ((int64_t)1 << 31);
+    const unsigned vblocks = 152 * 16;  // grid-stride: a few waves of 256-thread blocks
     if (esize == 8) {
         if (vec)
-            k_pack_v<double, double2><<<blocks, 256, 0, s>>>((double*)dense, (double*)padded, g, dir);
+            k_pack_v<double, double2><<<vblocks, 256, 0, s>>>((double*)dense, (double*)padded, g, dir);
         else
             k_pack<double><<<blocks, 256, 0, s>>>((double*)dense, (double*)padded, g, dir);
     } else {
         if (vec)
-            k_pack_v<float, float4><<<blocks, 256, 0, s>>>((float*)dense, (float*)padded, g, dir);
+            k_pack_v<float, float4><<<vblocks, 256, 0, s>>>((float*)dense, (float*)padded, g, dir);
         else
             k_pack<float><<<blocks, 256, 0, s>>>((float*)dense, (float*)padded, g, dir);
     }

@@ -100,11 +100,5 @@ __device__ __forceinline__ void cp_async_elem(void* dst, const void* src)
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Hint: bring the 128-byte line holding p into L2 (no register, no wait).
-__device__ __forceinline__ void prefetch_l2(const void* p)
-{
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 }  // namespace ptx
 }  // namespace st
