@@ -381,11 +381,11 @@ bool pick_cfg(const Geom& g, bool kappa, Cfg* c)
     if (G > 2) return false;
     int NS = (int)std::min<size_t>(8, SMEM_BUDGET / stage_bytes(g, TY, kappa));
     const int nyt = (int)((g.ny + TY - 1) / TY);
-    // z-chunk: about 7 units per CTA, at least 8 planes
-    const int64_t want_units = 7LL * sm_count();
-    int64_t nzc = std::max<int64_t>(1, want_units / nyt);
-    int ZC = (int)std::max<int64_t>(8, (g.nz + nzc - 1) / nzc);
-    ZC = (int)std::min<int64_t>(ZC, g.nz);
+    // z-chunk: 32 planes (each chunk stages 2 halo planes and fills and
+    // drains its pipeline once; measured best at 256^3 and 512^3), halved
+    // while the units would not reach half of the SMs
+    int ZC = (int)std::min<int64_t>(32, g.nz);
+    while (ZC > 8 && nyt * ((g.nz + ZC - 1) / ZC) < sm_count() / 2) ZC /= 2;
     if (use_env) {
         ZC = (int)std::min<int64_t>(eZC, g.nz);
         NS = std::min(eNS, (int)(SMEM_BUDGET / stage_bytes(g, TY, kappa)));
