@@ -29,6 +29,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -71,7 +72,10 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the samples are kept next to other run outputs when BENCH_CLOCKS_DIR
+        # names a directory, else in the system temporary directory
+        out_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"stencil_bench_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
