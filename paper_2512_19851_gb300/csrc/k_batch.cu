@@ -212,29 +212,32 @@ __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int sr
             pin += RS;
             ld6(pin, B);
             pin += RS;  // row below the current output row
-            for (int ly = r0; ly < r1; ++ly) {
-                T C[6];
-                ld6(pin, C);
+            // one output row from the rows above (X), at (Y) and below (Z, loaded
+            // here); the row walk is unrolled by three with the window rotating
+            // through A, B, C, so no register is copied
+            auto row_step = [&](const T (&X)[6], const T (&Y)[6], T (&Z)[6], int ly) {
+                ld6(pin, Z);
+                pin += RS;
                 T o[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     T acc;
                     if constexpr (SHAPE == SHAPE_BOX9) {
-                        acc = fma(w[0], A[e], T(0));
-                        acc = fma(w[1], A[e + 1], acc);
-                        acc = fma(w[2], A[e + 2], acc);
-                        acc = fma(w[3], B[e], acc);
-                        acc = fma(w[4], B[e + 1], acc);
-                        acc = fma(w[5], B[e + 2], acc);
-                        acc = fma(w[6], C[e], acc);
-                        acc = fma(w[7], C[e + 1], acc);
-                        acc = fma(w[8], C[e + 2], acc);
+                        acc = fma(w[0], X[e], T(0));
+                        acc = fma(w[1], X[e + 1], acc);
+                        acc = fma(w[2], X[e + 2], acc);
+                        acc = fma(w[3], Y[e], acc);
+                        acc = fma(w[4], Y[e + 1], acc);
+                        acc = fma(w[5], Y[e + 2], acc);
+                        acc = fma(w[6], Z[e], acc);
+                        acc = fma(w[7], Z[e + 1], acc);
+                        acc = fma(w[8], Z[e + 2], acc);
                     } else {  // five-point star: the corners carry no weight
-                        acc = fma(w[1], A[e + 1], T(0));
-                        acc = fma(w[3], B[e], acc);
-                        acc = fma(w[4], B[e + 1], acc);
-                        acc = fma(w[5], B[e + 2], acc);
-                        acc = fma(w[7], C[e + 1], acc);
+                        acc = fma(w[1], X[e + 1], T(0));
+                        acc = fma(w[3], Y[e], acc);
+                        acc = fma(w[4], Y[e + 1], acc);
+                        acc = fma(w[5], Y[e + 2], acc);
+                        acc = fma(w[7], Z[e + 1], acc);
                     }
                     o[e] = acc;
                 }
@@ -253,13 +256,16 @@ __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int sr
                     for (int e = 0; e < 4; ++e)
                         if (lx + e >= c0 && lx + e < c1) po[e] = o[e];
                 }
-#pragma unroll
-                for (int e = 0; e < 6; ++e) {
-                    A[e] = B[e];
-                    B[e] = C[e];
-                }
-                pin += RS;
+            };
+            T C[6];
+            int ly = r0;
+            for (; ly + 3 <= r1; ly += 3) {
+                row_step(A, B, C, ly);
+                row_step(B, C, A, ly + 1);
+                row_step(C, A, B, ly + 2);
             }
+            if (ly < r1) row_step(A, B, C, ly);
+            if (ly + 1 < r1) row_step(B, C, A, ly + 1);
         }
         __syncthreads();
         const T* tmp = in;
