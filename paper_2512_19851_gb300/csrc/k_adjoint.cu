@@ -130,13 +130,17 @@ struct XCtx {
     bool fixl, fixr;  // that neighbour is not held by the adjacent lane
     bool wig;         // periodic row end inside the group: element nx-1-x wraps to column 0
     bool xfull;       // the whole group is interior
+    // columns each lane loads for the x edges, unconditionally: its own cl / cr
+    // where fixl / fixr, else those of lane 0 / lane 31, so that one broadcast
+    // access serves the warp and no edge load needs a branch
+    int lcl, lcr;
 };
 
 // Neighbour sum of one row of values v in the fixed order
 //   z-1, y-1, y+1, x-1, x+1, z+1
 // shared by every level and every pass.  `left`/`right` are the values at
-// columns X.cl / X.cr when X.fixl / X.fixr; otherwise they come from the
-// adjacent lanes.  All lanes of the warp must call it.
+// columns X.lcl / X.lcr; they are used where X.fixl / X.fixr, otherwise the
+// edge values come from the adjacent lanes.  All lanes of the warp must call it.
 template <typename T>
 __device__ __forceinline__ void nsum(const XCtx& X, const T (&zm)[AV<T>::N], const T (&ym)[AV<T>::N],
                                      const T (&v)[AV<T>::N], const T (&yp)[AV<T>::N], const T (&zp)[AV<T>::N],
@@ -193,6 +197,23 @@ __device__ __forceinline__ void store_row(const XCtx& X, T* p, const T (&v)[AV<T
         vst(p, v);
     } else {
         for (int e = 0; e < AV<T>::N && X.x + e < X.nx; ++e) p[e] = v[e];  // columns past nx stay untouched
+    }
+}
+
+// Store the two rows of a row-pair task (row i at p + i * stride).  `okw`
+// (warp-uniform) says every lane's group is whole and both rows are in the
+// tile, so the warp stores without per-lane checks.
+template <typename T>
+__device__ __forceinline__ void store_pair(bool okw, const XCtx& X, bool act, int rr0, int tye, T* p, int64_t stride,
+                                           const T (&v)[2][AV<T>::N])
+{
+    if (okw) {
+        vst(p, v[0]);
+        vst(p + stride, v[1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+            if (act && rr0 + i < tye) store_row(X, p + i * stride, v[i]);
     }
 }
 
@@ -339,6 +360,11 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
     // elements are not interior and their results are dropped)
     X.cr = X.x + VN >= X.nx ? (PERIODIC ? 0 : X.nx) : X.x + VN;
     X.xfull = X.x + VN <= X.nx;
+    {
+        const int cl0 = __shfl_sync(0xffffffffu, X.cl, 0), cr31 = __shfl_sync(0xffffffffu, X.cr, 31);
+        X.lcl = X.fixl ? X.cl : cl0;
+        X.lcr = X.fixr ? X.cr : cr31;
+    }
     const int x = X.x;
     const T ac = T(P.ac), bc = T(P.bc), an = T(P.an), bn = T(P.bn);
     // mu = w_n * lambda of a staged (lambda, kappa) pair; the product is
@@ -366,7 +392,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
         const int rr0 = 2 * rp;
         // gradient reductions through the warp scratch: the warp holds 32
         // consecutive whole groups of both rows of one row pair
-        const bool fastw = pairw && (ngx % 32 == 0) && __all_sync(0xffffffffu, act && X.xfull && rr0 + 1 < tye);
+        const bool okw = pairw && __all_sync(0xffffffffu, act && X.xfull && rr0 + 1 < tye);
+        const bool fastw = okw && (ngx % 32 == 0);
         // carried state (registers), per owned row: mu and u_t of the plane below the level-1 centre
         T m0p[2][VN], uap[2][VN];
         // level 2 (K == 2): mu_1 of the planes below and at its centre, lambda_1 and w_c at its
@@ -449,9 +476,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         const T* Lr = L + (i + 1) * pitch;
-                        T left = T(0), right = T(0);
-                        if (X.fixl) left = mu_of(Lr[X.cl], Lr[P.kap_off + X.cl]);
-                        if (X.fixr) right = mu_of(Lr[X.cr], Lr[P.kap_off + X.cr]);
+                        const T left = mu_of(Lr[X.lcl], Lr[P.kap_off + X.lcl]);
+                        const T right = mu_of(Lr[X.lcr], Lr[P.kap_off + X.lcr]);
                         T s[VN];
                         nsum(X, m0p[i], mv[i], mv[i + 1], mv[i + 2], mz[i], left, right, s);
                         const bool out = zout1 || (!PERIODIC && y0 + rr0 + i >= P.ny);
@@ -477,9 +503,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 #pragma unroll
                         for (int i = 0; i < 2; ++i) {
                             const T* Ur = U + (i + 1) * pitch;
-                            T left = T(0), right = T(0);
-                            if (X.fixl) left = Ur[X.cl];
-                            if (X.fixr) right = Ur[X.cr];
+                            const T left = Ur[X.lcl], right = Ur[X.lcr];
                             T nb[VN];
                             nsum(X, uap[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
 #pragma unroll
@@ -491,17 +515,12 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                     }
                     if constexpr (K == 1) {
                         // final level: lambda_out of the owned rows
-#pragma unroll
-                        for (int i = 0; i < 2; ++i)
-                            if (act && rr0 + i < tye)
-                                store_row(X, lam_out + P.origin + c1 * P.plane + (y0 + rr0 + i) * P.pitch + x,
-                                          l1n[i]);
+                        store_pair(okw, X, act, rr0, tye, lam_out + P.origin + c1 * P.plane + (y0 + rr0) * P.pitch + x,
+                                   P.pitch, l1n);
                     } else {
                         // publish mu_1 of the owned rows for level 2's y neighbours
                         T* M = mring + (size_t)wslot * P.ring_elems + P.xl + (rr0 + 1) * pitch;
-#pragma unroll
-                        for (int i = 0; i < 2; ++i)
-                            if (act && rr0 + i < tye) store_row(X, M + i * pitch + x, m1n[i]);
+                        store_pair(okw, X, act, rr0, tye, M + x, (int64_t)pitch, m1n);
                     }
                     // this step's gradient term goes to the accumulator now; the
                     // next step's (level 2, one iteration later) follows it, so
@@ -551,9 +570,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                             for (int e = 0; e < VN; ++e) mz[e] = mu_of(lv[e], kv[e]);
                         }
                         const T* Lr = L + pitch;
-                        T left = T(0), right = T(0);
-                        if (X.fixl) left = mu_of(Lr[X.cl], Lr[P.kap_off + X.cl]);
-                        if (X.fixr) right = mu_of(Lr[X.cr], Lr[P.kap_off + X.cr]);
+                        const T left = mu_of(Lr[X.lcl], Lr[P.kap_off + X.lcl]);
+                        const T right = mu_of(Lr[X.lcr], Lr[P.kap_off + X.lcr]);
                         T s[VN];
                         nsum(X, m0p[i], mv[0], mv[1], mv[2], mz, left, right, s);
                         const int64_t yabs = y0 + rh;
@@ -596,18 +614,14 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 #pragma unroll
                         for (int i = 0; i < 2; ++i) {
                             const T* Mr = M + (i + 1) * pitch;
-                            T left = T(0), right = T(0);
-                            if (X.fixl) left = Mr[X.cl];
-                            if (X.fixr) right = Mr[X.cr];
+                            const T left = Mr[X.lcl], right = Mr[X.lcr];
                             nsum(X, m1a[i], i == 0 ? mup : m1b[0], m1b[i], i == 0 ? m1b[1] : mdn, m1n[i], left, right,
                                  s[i]);
 #pragma unroll
                             for (int e = 0; e < VN; ++e) l2[i][e] = fma(wcp[i][e], l1p[i][e], s[i][e]);
                         }
-#pragma unroll
-                        for (int i = 0; i < 2; ++i)
-                            if (act && rr0 + i < tye)
-                                store_row(X, lam_out + P.origin + c2 * P.plane + (y0 + rr0 + i) * P.pitch + x, l2[i]);
+                        store_pair(okw, X, act, rr0, tye, lam_out + P.origin + c2 * P.plane + (y0 + rr0) * P.pitch + x,
+                                   P.pitch, l2);
                         if (grad) {
                             T uv[4][VN], uz[2][VN];
 #pragma unroll
@@ -617,9 +631,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 #pragma unroll
                             for (int i = 0; i < 2; ++i) {
                                 const T* Ur = UB + (i + 1) * pitch;
-                                T left = T(0), right = T(0);
-                                if (X.fixl) left = Ur[X.cl];
-                                if (X.fixr) right = Ur[X.cr];
+                                const T left = Ur[X.lcl], right = Ur[X.lcr];
                                 T nb[VN], g2[VN];
                                 nsum(X, ubp[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
 #pragma unroll
