@@ -483,9 +483,11 @@ def run_profile(case: str, launches: int = 3):
 
     torch.cuda.set_device(0)
     s = torch.cuda.current_stream()
-    if case in ("heat3d_f32", "heat3d_f64"):
-        dt = torch.float32 if case == "heat3d_f32" else torch.float64
-        shape = (256, 512, 512)
+    if case in ("heat3d_f32", "heat3d_f64", "heat3d_f32_512"):
+        dt = torch.float64 if case == "heat3d_f64" else torch.float32
+        # the 512^3 case is the headline sweep itself (about 1.1 GB on the
+        # device), for single-pass counter captures
+        shape = (512, 512, 512) if case == "heat3d_f32_512" else (256, 512, 512)
         offs, w, _ = stencils.heat3d()
         g = Grid(shape, offs, w, periodic=True, dtype=dt)
         g.set_field(inputs.heat3d(shape=shape).u0)
@@ -545,7 +547,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--headline-only", action="store_true")
-    ap.add_argument("--profile", default=None, help="run one small case for ncu (heat3d_f32, heat3d_f64, wave, "
+    ap.add_argument("--profile", default=None, help="run one small case for ncu (heat3d_f32, heat3d_f32_512, heat3d_f64, wave, "
                                                       "varcoef_fwd, varcoef_adj) and exit")
     args = ap.parse_args()
     if args.profile:
