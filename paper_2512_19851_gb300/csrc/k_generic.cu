@@ -88,23 +88,40 @@ k_adjoint_generic(const T* __restrict__ u, const T* __restrict__ lam, T* __restr
     if (gk) gk[q] += (double)lam[q] * (double)s;
 }
 
-// Write `value` into every cell of a padded buffer that is not interior.
-// One block per padded row.
+// Write `value` into every cell of a padded buffer that is not interior: the
+// whole rows of the z ghost planes and of the y ghost rows, then the lead and
+// tail columns of the interior rows.  Flat grid-stride loops over those cells
+// only, so the cost follows the ghost shell, not the row count.
 template <typename T>
-__global__ void k_fill_ghosts(T* __restrict__ buf, Geom g, T value)
+__global__ void __launch_bounds__(256) k_fill_ghosts(T* __restrict__ buf, Geom g, T value)
 {
-    const int64_t rows = g.pnz * g.pny;
-    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int64_t pz = (uint32_t)row / (uint32_t)g.pny;  // 32-bit: rows < 2^32
-        const int64_t py = row - pz * g.pny;
-        T* rp = buf + pz * g.plane + py * g.pitch;
-        const bool ghost_row = (pz < g.rz) || (pz >= g.rz + g.nz) || (py < g.r) || (py >= g.r + g.ny);
-        if (ghost_row) {
-            for (int64_t x = threadIdx.x; x < g.pitch; x += blockDim.x) rp[x] = value;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t zrows = 2 * g.rz * g.pny;  // rows of the z ghost planes
+    const int64_t yrows = g.nz * 2 * g.r;    // y ghost rows of the interior planes
+    const int64_t full = (zrows + yrows) * g.pitch;
+    for (int64_t i = tid; i < full; i += nthr) {
+        const int64_t row = i / g.pitch, x = i - row * g.pitch;
+        int64_t pz, py;
+        if (row < zrows) {
+            const int64_t zp = row / g.pny;
+            py = row - zp * g.pny;
+            pz = zp < g.rz ? zp : zp + g.nz;
         } else {
-            for (int64_t x = threadIdx.x; x < g.xl; x += blockDim.x) rp[x] = value;
-            for (int64_t x = g.xl + g.nx + threadIdx.x; x < g.pitch; x += blockDim.x) rp[x] = value;
+            const int64_t k = row - zrows;
+            const int64_t zi = k / (2 * g.r), yk = k - zi * 2 * g.r;
+            pz = g.rz + zi;
+            py = yk < g.r ? yk : yk + g.ny;
         }
+        buf[pz * g.plane + py * g.pitch + x] = value;
+    }
+    const int64_t side = g.pitch - g.nx;  // lead [0, xl) and tail [xl + nx, pitch) of a row
+    const int64_t nside = g.nz * g.ny * side;
+    for (int64_t i = tid; i < nside; i += nthr) {
+        const int64_t row = i / side, c = i - row * side;
+        const int64_t zi = row / g.ny, yi = row - zi * g.ny;
+        const int64_t x = c < g.xl ? c : g.nx + c;
+        buf[(g.rz + zi) * g.plane + (g.r + yi) * g.pitch + x] = value;
     }
 }
 
@@ -421,8 +438,9 @@ cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int
 
 cudaError_t launch_fill_ghosts(int esize, void* buf, const Geom& g, double value, cudaStream_t s)
 {
-    const int64_t rows = g.pnz * g.pny;
-    const unsigned blocks = (unsigned)(rows < 65535 ? rows : 65535);
+    const int64_t cells = (2 * g.rz * g.pny + g.nz * 2 * g.r) * g.pitch + g.nz * g.ny * (g.pitch - g.nx);
+    const int64_t want = (cells + 255) / 256;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
     if (esize == 8)
         k_fill_ghosts<double><<<blocks, 256, 0, s>>>((double*)buf, g, value);
     else
