@@ -60,6 +60,8 @@ struct AdjParams {
     int TY, NS, CW;                 // rows per tile, stages, consumer warps
     int nyt, nzc, units;
     int ngx, npair, pair_warps;     // row-pair tasks fill warps [0, pair_warps); halo row tasks the rest
+    int halo_warps;                 // K == 2: halo warps; each covers x groups [32 w, 32 w + 32) and,
+                                    // one warp count further, [32 (w + halo_warps), ...)
     uint32_t stage_elems, kap_off, ua_off, ub_off;  // lambda at offset 0 of a stage
     uint32_t ring_elems;            // one plane of the mu ring: TY + 2 rows
     int grad;                       // gradient requested
@@ -135,6 +137,27 @@ struct XCtx {
     // access serves the warp and no edge load needs a branch
     int lcl, lcr;
 };
+
+// The context of x group gx for this lane.  All lanes of the warp must call it.
+template <int VN, bool PERIODIC>
+__device__ __forceinline__ XCtx make_xctx(int gx, int lane, int ngx, int nx)
+{
+    XCtx X;
+    X.nx = nx;
+    X.x = gx * VN;
+    X.fixl = lane == 0 || gx == 0;
+    X.fixr = lane == 31 || gx == ngx - 1;
+    X.wig = PERIODIC && X.x + VN > X.nx;
+    X.cl = X.x > 0 ? X.x - 1 : (PERIODIC ? X.nx - 1 : -1);
+    // (a Dirichlet ragged group reads the ghost column instead: its last
+    // elements are not interior and their results are dropped)
+    X.cr = X.x + VN >= X.nx ? (PERIODIC ? 0 : X.nx) : X.x + VN;
+    X.xfull = X.x + VN <= X.nx;
+    const int cl0 = __shfl_sync(0xffffffffu, X.cl, 0), cr31 = __shfl_sync(0xffffffffu, X.cr, 31);
+    X.lcl = X.fixl ? X.cl : cl0;
+    X.lcr = X.fixr ? X.cr : cr31;
+    return X;
+}
 
 // Neighbour sum of one row of values v in the fixed order
 //   z-1, y-1, y+1, x-1, x+1, z+1
@@ -344,27 +367,13 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
             gx = t - rp * ngx;
         }
     } else if (K == 2) {
-        // both halo rows (above and below the tile) of one x group
+        // both halo rows (above and below the tile) of one x group (the first
+        // of the warp's two halo sub-tasks)
         const int t = threadIdx.x - 32 * P.pair_warps;
         act = t < ngx;
         if (act) gx = t;
     }
-    XCtx X;
-    X.nx = (int)P.nx;
-    X.x = gx * VN;
-    X.fixl = lane == 0 || gx == 0;
-    X.fixr = lane == 31 || gx == ngx - 1;
-    X.wig = PERIODIC && X.x + VN > X.nx;
-    X.cl = X.x > 0 ? X.x - 1 : (PERIODIC ? X.nx - 1 : -1);
-    // (a Dirichlet ragged group reads the ghost column instead: its last
-    // elements are not interior and their results are dropped)
-    X.cr = X.x + VN >= X.nx ? (PERIODIC ? 0 : X.nx) : X.x + VN;
-    X.xfull = X.x + VN <= X.nx;
-    {
-        const int cl0 = __shfl_sync(0xffffffffu, X.cl, 0), cr31 = __shfl_sync(0xffffffffu, X.cr, 31);
-        X.lcl = X.fixl ? X.cl : cl0;
-        X.lcr = X.fixr ? X.cr : cr31;
-    }
+    const XCtx X = make_xctx<VN, PERIODIC>(gx, lane, ngx, (int)P.nx);
     const int x = X.x;
     const T ac = T(P.ac), bc = T(P.bc), an = T(P.an), bn = T(P.bn);
     // mu = w_n * lambda of a staged (lambda, kappa) pair; the product is
@@ -534,59 +543,72 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                 }
             } else if (K == 2) {
                 // ------------------------------------------------ halo rows, level 1 only
+                // Two sub-tasks per halo warp (x groups 32 apart by the halo warp
+                // count); the second keeps its carried mu rows in m1a, which only
+                // the row-pair tasks' level 2 uses otherwise.
+                auto halo = [&](const XCtx& Xh, bool acth, T (&m0)[2][VN]) {
+                    const int xh = Xh.x;
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int rh = i == 0 ? -1 : tye;
-                    const T* L = S0 + (rh - 1 + K) * pitch;  // lambda row rh - 1
-                    const T* Kp = L + P.kap_off;
-                    if (j == 1) {
-                        T lv[VN], kv[VN];
-                        vld(L + pitch + x, lv);
-                        vld(Kp + pitch + x, kv);
-#pragma unroll
-                        for (int e = 0; e < VN; ++e) m0p[i][e] = mu_of(lv[e], kv[e]);
-                    } else if (j >= 2) {
-                        T mv[3][VN], lc[VN], kc[VN], mz[VN];
-#pragma unroll
-                        for (int r3 = 0; r3 < 3; ++r3) {
+                    for (int i = 0; i < 2; ++i) {
+                        const int rh = i == 0 ? -1 : tye;
+                        const T* L = S0 + (rh - 1 + K) * pitch;  // lambda row rh - 1
+                        const T* Kp = L + P.kap_off;
+                        if (j == 1) {
                             T lv[VN], kv[VN];
-                            vld(L + r3 * pitch + x, lv);
-                            vld(Kp + r3 * pitch + x, kv);
+                            vld(L + pitch + xh, lv);
+                            vld(Kp + pitch + xh, kv);
 #pragma unroll
-                            for (int e = 0; e < VN; ++e) {
-                                mv[r3][e] = mu_of(lv[e], kv[e]);
-                                if (r3 == 1) {
-                                    lc[e] = lv[e];
-                                    kc[e] = kv[e];
+                            for (int e = 0; e < VN; ++e) m0[i][e] = mu_of(lv[e], kv[e]);
+                        } else if (j >= 2) {
+                            T mv[3][VN], lc[VN], kc[VN], mz[VN];
+#pragma unroll
+                            for (int r3 = 0; r3 < 3; ++r3) {
+                                T lv[VN], kv[VN];
+                                vld(L + r3 * pitch + xh, lv);
+                                vld(Kp + r3 * pitch + xh, kv);
+#pragma unroll
+                                for (int e = 0; e < VN; ++e) {
+                                    mv[r3][e] = mu_of(lv[e], kv[e]);
+                                    if (r3 == 1) {
+                                        lc[e] = lv[e];
+                                        kc[e] = kv[e];
+                                    }
                                 }
                             }
-                        }
-                        {
-                            const T* L1 = S1 + (rh + K) * pitch;
-                            T lv[VN], kv[VN];
-                            vld(L1 + x, lv);
-                            vld(L1 + P.kap_off + x, kv);
+                            {
+                                const T* L1 = S1 + (rh + K) * pitch;
+                                T lv[VN], kv[VN];
+                                vld(L1 + xh, lv);
+                                vld(L1 + P.kap_off + xh, kv);
 #pragma unroll
-                            for (int e = 0; e < VN; ++e) mz[e] = mu_of(lv[e], kv[e]);
-                        }
-                        const T* Lr = L + pitch;
-                        const T left = mu_of(Lr[X.lcl], Lr[P.kap_off + X.lcl]);
-                        const T right = mu_of(Lr[X.lcr], Lr[P.kap_off + X.lcr]);
-                        T s[VN];
-                        nsum(X, m0p[i], mv[0], mv[1], mv[2], mz, left, right, s);
-                        const int64_t yabs = y0 + rh;
-                        const bool out = zout1 || (!PERIODIC && (yabs < 0 || yabs >= P.ny));
-                        T mu1[VN];
+                                for (int e = 0; e < VN; ++e) mz[e] = mu_of(lv[e], kv[e]);
+                            }
+                            const T* Lr = L + pitch;
+                            const T left = mu_of(Lr[Xh.lcl], Lr[P.kap_off + Xh.lcl]);
+                            const T right = mu_of(Lr[Xh.lcr], Lr[P.kap_off + Xh.lcr]);
+                            T s[VN];
+                            nsum(Xh, m0[i], mv[0], mv[1], mv[2], mz, left, right, s);
+                            const int64_t yabs = y0 + rh;
+                            const bool out = zout1 || (!PERIODIC && (yabs < 0 || yabs >= P.ny));
+                            T mu1[VN];
 #pragma unroll
-                        for (int e = 0; e < VN; ++e) {
-                            const T wc = fma(bc, kc[e], ac);
-                            const T l1 = fma(wc, lc[e], s[e]);
-                            mu1[e] = out ? T(0) : mu_of(l1, kc[e]);
-                            m0p[i][e] = mv[1][e];
+                            for (int e = 0; e < VN; ++e) {
+                                const T wc = fma(bc, kc[e], ac);
+                                const T l1 = fma(wc, lc[e], s[e]);
+                                mu1[e] = out ? T(0) : mu_of(l1, kc[e]);
+                                m0[i][e] = mv[1][e];
+                            }
+                            if (acth)
+                                store_row(Xh, mring + (size_t)wslot * P.ring_elems + P.xl + (rh + 1) * pitch + xh,
+                                          mu1);
                         }
-                        if (act)
-                            store_row(X, mring + (size_t)wslot * P.ring_elems + P.xl + (rh + 1) * pitch + x, mu1);
                     }
+                };
+                halo(X, act, m0p);
+                const int s2 = warp - P.pair_warps + P.halo_warps;  // second sub-task (warp-uniform)
+                if (32 * s2 < ngx) {
+                    const int gx2 = 32 * s2 + lane;
+                    halo(make_xctx<VN, PERIODIC>(gx2, lane, ngx, (int)P.nx), gx2 < ngx, m1a);
                 }
             }
 
@@ -710,8 +732,10 @@ size_t adj_stage_rows(int TY, int K) { return 2 * (size_t)(TY + 2 * K) + (size_t
 
 // Tile rows, stages and z chunks for K fused steps.  Tiles take as many row
 // pairs as one task per consumer thread allows (at most A_MAXCW warps, halo
-// tasks included) and shared memory holds with at least one stage in flight:
-// the halo rows a taller tile saves are worth more than extra stages.
+// warps included, each halo warp covering two 32-group sub-tasks) and shared
+// memory holds with at least one stage in flight: the halo rows a taller tile
+// saves are worth more than extra stages (256^3 FP32: 10-row tiles, 117.5 us
+// per reverse step, against 118.9 with 8 rows and one sub-task per halo warp).
 bool adj_cfg(const Geom& g, int K, AdjCfg* c)
 {
     const int VN = g.esize == 8 ? 2 : 4;
@@ -730,7 +754,7 @@ bool adj_cfg(const Geom& g, int K, AdjCfg* c)
             if (TY > 2 && TY - 2 >= g.ny) continue;  // no taller than the grid
             const int npair = (TY / 2) * ngx;
             const int pw = (npair + 31) / 32;
-            const int hw = K == 2 ? (ngx + 31) / 32 : 0;
+            const int hw = K == 2 ? ((ngx + 31) / 32 + 1) / 2 : 0;  // two halo sub-tasks per warp
             if (pw + hw > A_MAXCW) continue;
             const size_t sb = (adj_stage_rows(TY, K) * rowb + 127) / 128 * 128;
             const size_t rb = K == 2 ? (size_t)A_RING * (TY + 2) * rowb : 0;
@@ -792,6 +816,7 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
     P.ngx = (int)((g.nx + AV<T>::N - 1) / AV<T>::N);
     P.npair = c.npair;
     P.pair_warps = c.pair_warps;
+    P.halo_warps = c.CW - c.pair_warps;
     P.stage_elems = (uint32_t)(c.stage_bytes / sizeof(T));
     P.kap_off = (uint32_t)((c.TY + 2 * K) * g.pitch);
     P.ua_off = 2 * P.kap_off;
