@@ -158,6 +158,13 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
     const int ngx = (int)((P.nx + 3) / 4);
     const float bj[WR] = {P.bj[0], P.bj[1], P.bj[2], P.bj[3]};
     const float aj[WR] = {P.aj[0], P.aj[1], P.aj[2], P.aj[3]};
+    // Shared memory addressed by 32-bit indices in 16-byte units: stage s of
+    // the u ring starts at s * st4, stage s of the (m, u^{n-1}) ring at
+    // mr4 + s * mst4 (every stage, row and group start is 16-byte aligned).
+    const float4* S4 = reinterpret_cast<const float4*>(smem_raw);
+    const uint32_t st4 = P.stage_elems / 4u, mst4 = P.mstage_elems / 4u;
+    const uint32_t mr4 = (uint32_t)P.NS * st4;
+    const uint32_t pitch4 = (uint32_t)P.pitch / 4u;
     uint32_t gq = 0, gm = 0;
     for (int u = blockIdx.x; u < P.units; u += gridDim.x) {
         const int yt = u % P.nyt, zc = u / P.nyt;
@@ -176,60 +183,57 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
         const bool fast = full4 || !PERIODIC;
         const int64_t gofs = P.origin + (y0 + row) * P.pitch + x;  // + z * plane
         const bool src_here = active && P.sz >= 0 && P.sy == y0 + row && P.sx >= x && P.sx < x + 4;
-        float4 q[2 * WR + 1];
+        // this thread's group in a u stage (its centre row) and in an (m, u^{n-1}) stage
+        const uint32_t t4 = (uint32_t)((P.xl + (row + WR) * P.pitch + x) / 4);
+        const uint32_t m4 = (uint32_t)((P.xl + row * P.pitch + x) / 4);
+        const uint32_t prev4 = (uint32_t)(P.TY * P.pitch / 4);  // u^{n-1} rows follow the m rows
+        // z queue: before output plane i, q[0 .. 7] hold the group at planes
+        // i .. i + 7 of the chunk (z - 4 .. z + 3 of the output); the step
+        // for a window w (= q or q + 1) takes plane i + 8 into w[8]
+        float4 q[2 * WR + 2];
 
-        auto stage_of = [&](int qq) -> const float* {
-            return ring + (size_t)((base + qq) % P.NS) * P.stage_elems + P.xl;
-        };
         auto wait_plane = [&](int qq) -> bool {
             const uint32_t g = base + qq;
             return ptx::mbar_wait_warp(&full[g % P.NS], (g / P.NS) & 1);
         };
-        auto release = [&](int qq) {
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&empty[(base + qq) % P.NS]);
-        };
         // plane q is a centre (output z0 + q - 4) for q in [4, zce + 4); all
         // other planes of the chunk only feed the z queues
         auto is_centre = [&](int qq) -> bool { return qq >= WR && qq < zce + WR; };
-        // a staged row holds the whole pitch, so the group's 16 bytes are
-        // always inside it (lanes past the row end read padding they discard)
-        auto read4 = [&](const float* rp) -> float4 { return *reinterpret_cast<const float4*>(rp + x); };
-        auto read_q = [&](int qq) -> float4 { return read4(stage_of(qq) + (int64_t)(row + WR) * P.pitch); };
-        // prime: queue planes z0-4 .. z0+3 (q = 0..7)
+        // prime: planes z0-4 .. z0+3 (q = 0..7)
+#pragma unroll
         for (int qq = 0; qq < 2 * WR; ++qq) {
             if (!wait_plane(qq)) {
                 timeout(P.status);
                 return;
             }
-            q[qq + 1] = active ? read_q(qq) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (!is_centre(qq)) release(qq);
+            q[qq] = active ? S4[((base + qq) % P.NS) * st4 + t4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!is_centre(qq)) {
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&empty[(base + qq) % P.NS]);
+            }
         }
         // running ring slots (no modulo per plane): the centre plane i + 4,
         // the incoming plane i + 8 with its phase parity, and the (m, u^{n-1})
         // stage of output i with its parity
         uint32_t s_c = (base + WR) % P.NS, s_n = (base + 2 * WR) % P.NS, p_n = ((base + 2 * WR) / P.NS) & 1;
         uint32_t s_m = mbase % P.NSM, p_m = (mbase / P.NSM) & 1;
-        for (int i = 0; i < zce; ++i) {
-            // shift the queue and take plane z+4 (q = i + 8)
-#pragma unroll
-            for (int d = 0; d < 2 * WR; ++d) q[d] = q[d + 1];
+        // one output plane i from window w; false when a wait ran out
+        auto step = [&](float4* w, int i) -> bool {
             if (!ptx::mbar_wait_warp(&full[s_n], p_n) || !ptx::mbar_wait_warp(&mfull[s_m], p_m)) {
                 timeout(P.status);
-                return;
+                return false;
             }
-            if (active) q[2 * WR] = read4(ring + (size_t)s_n * P.stage_elems + P.xl + (int64_t)(row + WR) * P.pitch);
+            if (active) w[2 * WR] = S4[s_n * st4 + t4];
             if (!is_centre(i + 2 * WR)) {
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&empty[s_n]);
             }
             if (active) {
-                const float* ms = mring + (size_t)s_m * P.mstage_elems + P.xl + (int64_t)row * P.pitch;
-                const float4 mv = read4(ms);
-                const float4 pv = read4(ms + (size_t)P.TY * P.pitch);
-                const float* cp = ring + (size_t)s_c * P.stage_elems + P.xl;  // centre plane
-                const float* rc = cp + (int64_t)(row + WR) * P.pitch;
-                const float c[4] = {q[WR].x, q[WR].y, q[WR].z, q[WR].w};
+                const uint32_t mb = mr4 + s_m * mst4 + m4;
+                const float4 mv = S4[mb];
+                const float4 pv = S4[mb + prev4];
+                const uint32_t cb = s_c * st4 + t4;  // centre plane, own group of the centre row
+                const float c[4] = {w[WR].x, w[WR].y, w[WR].z, w[WR].w};
                 // running sums per point: lb = sum_k beta_k u_k, la = sum_{k != 0} alpha_k u_k
                 float lb[4], la[4];
 #pragma unroll
@@ -239,50 +243,51 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
                 }
                 // coefficient of distance j by register selects (j may be a loop
                 // variable: indexing a local array with it would go to local memory)
-                auto cb = [&](int j) { return j == 1 ? bj[0] : (j == 2 ? bj[1] : (j == 3 ? bj[2] : bj[3])); };
-                auto ca = [&](int j) { return j == 1 ? aj[0] : (j == 2 ? aj[1] : (j == 3 ? aj[2] : aj[3])); };
+                auto cb_ = [&](int j) { return j == 1 ? bj[0] : (j == 2 ? bj[1] : (j == 3 ? bj[2] : bj[3])); };
+                auto ca_ = [&](int j) { return j == 1 ? aj[0] : (j == 2 ? aj[1] : (j == 3 ? aj[2] : aj[3])); };
                 auto add_pair = [&](int j, int e, float s2) {  // the two neighbours at distance j
-                    lb[e] = fmaf(cb(j), s2, lb[e]);
-                    if (!ALPHA0) la[e] = fmaf(ca(j), s2, la[e]);
+                    lb[e] = fmaf(cb_(j), s2, lb[e]);
+                    if (!ALPHA0) la[e] = fmaf(ca_(j), s2, la[e]);
                 };
 #pragma unroll
                 for (int j = 1; j <= WR; ++j) {  // z neighbours from the register queue
-                    const float4 zl = q[WR - j], zh = q[WR + j];
+                    const float4 zl = w[WR - j], zh = w[WR + j];
                     add_pair(j, 0, zl.x + zh.x);
                     add_pair(j, 1, zl.y + zh.y);
                     add_pair(j, 2, zl.z + zh.z);
                     add_pair(j, 3, zl.w + zh.w);
                 }
                 if (fast) {
-#pragma unroll 2
+#pragma unroll
                     for (int j = 1; j <= WR; ++j) {  // y neighbours
-                        const float4 yl = *reinterpret_cast<const float4*>(rc - j * P.pitch + x);
-                        const float4 yh = *reinterpret_cast<const float4*>(rc + j * P.pitch + x);
+                        const float4 yl = S4[cb - j * pitch4];
+                        const float4 yh = S4[cb + j * pitch4];
                         add_pair(j, 0, yl.x + yh.x);
                         add_pair(j, 1, yl.y + yh.y);
                         add_pair(j, 2, yl.z + yh.z);
                         add_pair(j, 3, yl.w + yh.w);
                     }
-                    // x window: 4 left, the group, 4 right.  Vector loads only
-                    // at multiples of 4 from the row start (16-byte aligned); a
-                    // periodic window that wraps is gathered element-wise.
+                    // x window: 4 left, the group, 4 right (16-byte groups of the
+                    // row); a periodic window that wraps is gathered element-wise
                     float4 L, R;
+                    const float* rc = reinterpret_cast<const float*>(S4 + cb) - x;  // column 0 of the centre row
                     if (PERIODIC && x == 0)
                         L = make_float4(rc[wrapw(x - 4, P.nx)], rc[wrapw(x - 3, P.nx)], rc[wrapw(x - 2, P.nx)],
                                         rc[wrapw(x - 1, P.nx)]);
                     else
-                        L = *reinterpret_cast<const float4*>(rc + x - 4);
+                        L = S4[cb - 1];
                     if (PERIODIC && x + 8 > P.nx)
                         R = make_float4(rc[wrapw(x + 4, P.nx)], rc[wrapw(x + 5, P.nx)], rc[wrapw(x + 6, P.nx)],
                                         rc[wrapw(x + 7, P.nx)]);
                     else
-                        R = *reinterpret_cast<const float4*>(rc + x + 4);
-                    const float w[12] = {L.x, L.y, L.z, L.w, c[0], c[1], c[2], c[3], R.x, R.y, R.z, R.w};
+                        R = S4[cb + 1];
+                    const float wx[12] = {L.x, L.y, L.z, L.w, c[0], c[1], c[2], c[3], R.x, R.y, R.z, R.w};
 #pragma unroll
                     for (int j = 1; j <= WR; ++j)
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) add_pair(j, e, w[4 + e - j] + w[4 + e + j]);
+                        for (int e = 0; e < 4; ++e) add_pair(j, e, wx[4 + e - j] + wx[4 + e + j]);
                 } else {
+                    const float* rc = reinterpret_cast<const float*>(S4 + cb) - x;  // column 0 of the centre row
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int64_t xe = x + e;
@@ -330,7 +335,17 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
                 s_m = 0;
                 p_m ^= 1u;
             }
+            return true;
+        };
+        // two output planes per iteration: the queue moves by two planes
+        // (8 float4 moves per two planes instead of per plane)
+        int i = 0;
+        for (; i + 2 <= zce; i += 2) {
+            if (!step(q, i) || !step(q + 1, i + 1)) return;
+#pragma unroll
+            for (int d = 0; d < 2 * WR; ++d) q[d] = q[d + 2];
         }
+        if (i < zce && !step(q, i)) return;
         gq = base + zce + 2 * WR;
         gm = mbase + zce;
     }
