@@ -98,6 +98,29 @@ def test_gradient_fp32_ragged_matches_fp64_oracle(periodic, bc):
     assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
 
 
+@pytest.mark.parametrize("periodic,bc", [(False, 0.0), (True, 0.0)])
+def test_gradient_wide_rows_matches_oracle(periodic, bc):
+    """Rows wider than one warp of x groups: FP32 rows of 150 points (38
+    groups, the last one ragged) and FP64 rows of 70 points (35 groups), so a
+    tile's halo rows take two 32-group sub-tasks per halo warp, the second
+    partly filled.  FP32 m = 5 and m = 1 must also agree bitwise."""
+    steps, m = 10, 5
+    v = inputs.varcoef3d(shape=(14, 22, 150))
+    loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, bc, steps, m)
+    uT, lam0, gk, loss, kern = gpu_grad(v, steps, m, torch.float32, periodic, bc)
+    assert rel_err(uT, uT_r) <= TOL32_FWD, kern
+    assert rel_err(lam0, lam_r) <= TOL32_FWD, kern
+    assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
+    other = gpu_grad(v, steps, 1, torch.float32, periodic, bc)
+    assert np.array_equal(lam0, other[1]) and np.array_equal(gk, other[2])
+    v = inputs.varcoef3d(shape=(14, 22, 70))
+    loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, bc, steps, m)
+    uT, lam0, gk, loss, kern = gpu_grad(v, steps, m, torch.float64, periodic, bc)
+    assert rel_err(uT, uT_r) <= TOL64, kern
+    assert rel_err(lam0, lam_r) <= TOL64, kern
+    assert rel_err(gk, gk_r) <= TOL64, kern
+
+
 def test_checkpoint_interval_does_not_change_gradient_fp32():
     """FP32 grids: fused two-step passes round exactly like single steps, so
     m = 1, 6 and 20 give bitwise equal lambda_0 and gradients."""
