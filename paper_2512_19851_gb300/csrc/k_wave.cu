@@ -337,15 +337,25 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
             }
             return true;
         };
-        // two output planes per iteration: the queue moves by two planes
-        // (8 float4 moves per two planes instead of per plane)
-        int i = 0;
-        for (; i + 2 <= zce; i += 2) {
-            if (!step(q, i) || !step(q + 1, i + 1)) return;
+        if constexpr (PERIODIC) {
+            // one plane per iteration (the wrapped gathers leave no registers
+            // for a second window)
+            for (int i = 0; i < zce; ++i) {
+                if (!step(q, i)) return;
 #pragma unroll
-            for (int d = 0; d < 2 * WR; ++d) q[d] = q[d + 2];
+                for (int d = 0; d < 2 * WR; ++d) q[d] = q[d + 1];
+            }
+        } else {
+            // two output planes per iteration: the queue moves by two planes
+            // (8 float4 moves per two planes instead of per plane)
+            int i = 0;
+            for (; i + 2 <= zce; i += 2) {
+                if (!step(q, i) || !step(q + 1, i + 1)) return;
+#pragma unroll
+                for (int d = 0; d < 2 * WR; ++d) q[d] = q[d + 2];
+            }
+            if (i < zce && !step(q, i)) return;
         }
-        if (i < zce && !step(q, i)) return;
         gq = base + zce + 2 * WR;
         gm = mbase + zce;
     }
