@@ -270,19 +270,24 @@ st_status stencil_residual(st_grid_t g, const void* u, const void* target, void*
 
 /*
  * Adjoint with checkpoint-every-m recomputation (one time level only).
- * Workspace bytes for a run of nsteps with checkpoints every ckpt_every steps
- * (ceil(nsteps/ckpt_every) checkpoints + ckpt_every-1 recomputed levels).
+ * Workspace bytes for a run of nsteps with checkpoints every ckpt_every steps:
+ * ceil(nsteps/ckpt_every) checkpoints, ckpt_every-1 levels for the
+ * recomputation of a segment, and the ckpt_every-1 inner levels of the last
+ * segment, which the forward run keeps so that the reverse pass need not
+ * recompute them.
  */
 st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int ckpt_every, size_t* bytes);
 
-/* Forward nsteps from the current level, storing u at t = 0, m, 2m, ... in
- * `workspace` (device, >= stencil_adjoint_workspace bytes, 16-byte aligned). */
+/* Forward nsteps from the current level, storing u at t = 0, m, 2m, ... and
+ * the inner levels of the last segment in `workspace` (device,
+ * >= stencil_adjoint_workspace bytes, 16-byte aligned). */
 st_status stencil_step_ckpt(st_grid_t g, int nsteps, int ckpt_every, void* workspace,
                             void* stream);
 
 /*
  * Reverse pass of a run recorded by stencil_step_ckpt with the same nsteps
- * and ckpt_every.  lambda (in: dL/du_T, out: dL/du_0) and lambda_tmp are
+ * and ckpt_every (it reads the workspace and never writes the checkpoints or
+ * the kept levels, so it may run again on the same record).  lambda (in: dL/du_T, out: dL/du_0) and lambda_tmp are
  * field-layout buffers of the grid's dtype; grad_coeff (may be NULL) is a
  * field-layout buffer of DOUBLES into which
  *     sum_t lambda_{t+1}[p] * sum_k beta_k u_t[p + o_k]     (= dL/dkappa_p)

@@ -744,7 +744,9 @@ st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* byte
     if (!g || !bytes) return fail(ST_ERR_ARG, "stencil_adjoint_workspace: NULL argument");
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_adjoint_workspace: nsteps >= 0, ckpt_every >= 1");
     const int64_t nck = (nsteps + m - 1) / m;
-    *bytes = state_bytes(g) * (size_t)(nck + (m - 1));
+    // checkpoints, the recomputation buffer of a segment, and the states of
+    // the last segment kept from the forward run
+    *bytes = state_bytes(g) * (size_t)(nck + 2 * (m - 1));
     return ST_OK;
 }
 
@@ -762,12 +764,30 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stre
     if (rc != ST_OK) return rc;
     const size_t sb = state_bytes(g);
     const size_t bytes = (size_t)g->g.elems * g->g.esize;
+    const int64_t nck = (nsteps + m - 1) / m;
+    char* last = (char*)ws + (size_t)(nck + (m - 1)) * sb;  // states t0 + 1 .. t0 + L - 1 of the last segment
     for (int t = 0; t < nsteps; t += m) {
         ST_CUDA_TRY(cudaMemcpyAsync((char*)ws + (size_t)(t / m) * sb, g->buf[g->cur], bytes,
                                     cudaMemcpyDeviceToDevice, s));
         const int seg = std::min(m, nsteps - t);
-        rc = enqueue_steps(g, g->cur, g->step, seg, s);
-        if (rc != ST_OK) return rc;
+        if (t + m < nsteps) {
+            rc = enqueue_steps(g, g->cur, g->step, seg, s);
+            if (rc != ST_OK) return rc;
+        } else {
+            // the last segment: its inner states go to the workspace, where the
+            // reverse pass reads them instead of recomputing them; the final
+            // state lands in the slot a plain run would leave it in
+            const int fin = final_slot(g, g->cur, seg);
+            const void* in = g->buf[g->cur];
+            for (int j = 1; j <= seg; ++j) {
+                void* out = j < seg ? (void*)(last + (size_t)(j - 1) * sb) : g->buf[fin];
+                if (j < seg && g->bc == ST_DIRICHLET)
+                    ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, out, g->g, g->bc_value, s));
+                SweepArgs a = sweep_args(g, in, out, g->step + j - 1);
+                ST_CUDA_TRY(launch_family(g->fam, a, s));
+                in = out;
+            }
+        }
         g->cur = final_slot(g, g->cur, seg);
         g->step += seg;
     }
@@ -808,10 +828,15 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     const int fuse = star3d_adjoint_fuse(g->fam);  // steps per optimised transpose launch (0: generic)
     void* lin = lambda;
     void* lout = lambda_tmp;
+    char* last = base + (size_t)(nck + (m - 1)) * sb;  // the last segment's states, kept by the forward run
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t t0 = c * m;
         const int L = (int)std::min<int64_t>(m, nsteps - t0);
-        for (int j = 1; j < L; ++j) {
+        const bool kept = c == nck - 1;
+        auto st = [&](int j) -> void* {
+            return (kept && j > 0) ? (void*)(last + (size_t)(j - 1) * sb) : state(c, j);
+        };
+        for (int j = 1; j < L && !kept; ++j) {
             SweepArgs a = sweep_args(g, state(c, j - 1), state(c, j), t0 + j - 1);
             ST_CUDA_TRY(launch_family(g->fam, a, s));
         }
@@ -819,8 +844,8 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
         while (j >= 0) {
             const int k = (fuse >= 2 && j >= 1) ? 2 : 1;
             AdjointArgs a{};
-            a.u = state(c, j);
-            a.u2 = k == 2 ? state(c, j - 1) : nullptr;
+            a.u = st(j);
+            a.u2 = k == 2 ? st(j - 1) : nullptr;
             a.lam_in = lin;
             a.lam_out = lout;
             a.kappa = g->has_beta ? g->buf[ST_SLOT_COEFF] : nullptr;
