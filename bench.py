@@ -371,11 +371,28 @@ def extra_configs(dev, hbm_peak):
 
     fwd_ckpt()
     t_adj = _time(adj, 2, s)
+    # the same reverse pass when the forward run keeps every state (one
+    # 200-step segment, about 13 GB of workspace): no recomputation
+    del p
+    torch.cuda.empty_cache()
+    p = VarCoefProblem(g, 200, 200)
+    abi.stencil_set_current(g.h, 0)
+    abi.stencil_step_ckpt(g.h, 200, 200, p.ws.data_ptr(), s)
+
+    def adj_all():
+        cur = g.bufs[g.current_slot()]
+        abi.stencil_residual(g.h, cur.data_ptr(), tgt.data_ptr(), p.lam.data_ptr(), p.loss.data_ptr(), s)
+        abi.stencil_adjoint(g.h, 200, 200, p.ws.data_ptr(), p.lam.data_ptr(), p.lam_tmp.data_ptr(),
+                            p.gk.data_ptr(), s)
+
+    t_all = _time(adj_all, 2, s)
     n4 = 256 ** 3
     out["varcoef3d_f32"] = {"fwd_glups": n4 * 200 / t_fwd / 1e9, "fwd_us_per_step": t_fwd / 200 * 1e6,
                             "fwd_hbm_frac": 12 * n4 / (t_fwd / 200) / 1e9 / hbm_peak,
                             "adj_glups": n4 * 200 / t_adj / 1e9, "adj_us_per_step": t_adj / 200 * 1e6,
-                            "adj_over_fwd": t_adj / t_fwd, "kernel": g.kernel}
+                            "adj_over_fwd": t_adj / t_fwd, "ckpt_every": 20,
+                            "adj_keep_all_us_per_step": t_all / 200 * 1e6, "adj_keep_all_over_fwd": t_all / t_fwd,
+                            "kernel": g.kernel}
     g.close()
     del p
     torch.cuda.empty_cache()

@@ -738,6 +738,12 @@ st_status stencil_residual(st_grid_t g, const void* u, const void* target, void*
 
 static size_t state_bytes(st_grid_t g) { return (size_t)((g->g.elems * g->g.esize + 255) / 256 * 256); }
 
+// Adjoint workspace, in levels: nck checkpoints, then (when there is more
+// than one segment) the m-1 levels a segment is recomputed into, then the
+// m-1 inner levels of the last segment kept by the forward run.
+static int64_t ws_recompute_levels(int64_t nck, int m) { return nck > 1 ? m - 1 : 0; }
+static size_t ws_last_offset(int64_t nck, int m, size_t sb) { return (size_t)(nck + ws_recompute_levels(nck, m)) * sb; }
+
 
 st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* bytes)
 {
@@ -746,7 +752,7 @@ st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* byte
     const int64_t nck = (nsteps + m - 1) / m;
     // checkpoints, the recomputation buffer of a segment, and the states of
     // the last segment kept from the forward run
-    *bytes = state_bytes(g) * (size_t)(nck + 2 * (m - 1));
+    *bytes = state_bytes(g) * (size_t)(nck + ws_recompute_levels(nck, m) + (m - 1));
     return ST_OK;
 }
 
@@ -765,7 +771,7 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stre
     const size_t sb = state_bytes(g);
     const size_t bytes = (size_t)g->g.elems * g->g.esize;
     const int64_t nck = (nsteps + m - 1) / m;
-    char* last = (char*)ws + (size_t)(nck + (m - 1)) * sb;  // states t0 + 1 .. t0 + L - 1 of the last segment
+    char* last = (char*)ws + ws_last_offset(nck, m, sb);  // states t0 + 1 .. t0 + L - 1 of the last segment
     for (int t = 0; t < nsteps; t += m) {
         ST_CUDA_TRY(cudaMemcpyAsync((char*)ws + (size_t)(t / m) * sb, g->buf[g->cur], bytes,
                                     cudaMemcpyDeviceToDevice, s));
@@ -824,11 +830,12 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
         return j == 0 ? (void*)(base + (size_t)c * sb) : (void*)(seg + (size_t)(j - 1) * sb);
     };
     if (g->bc == ST_DIRICHLET)
-        for (int j = 1; j < m; ++j) ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, state(0, j), g->g, g->bc_value, s));
+        for (int j = 1; j <= ws_recompute_levels(nck, m); ++j)
+            ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, state(0, j), g->g, g->bc_value, s));
     const int fuse = star3d_adjoint_fuse(g->fam);  // steps per optimised transpose launch (0: generic)
     void* lin = lambda;
     void* lout = lambda_tmp;
-    char* last = base + (size_t)(nck + (m - 1)) * sb;  // the last segment's states, kept by the forward run
+    char* last = base + ws_last_offset(nck, m, sb);  // the last segment's states, kept by the forward run
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t t0 = c * m;
         const int L = (int)std::min<int64_t>(m, nsteps - t0);

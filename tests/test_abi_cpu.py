@@ -128,6 +128,8 @@ def test_adjoint_workspace_size():
     # checkpoints + one segment's recomputation buffer + the kept last segment
     assert abi.stencil_adjoint_workspace(h, 200, 20) == per * (10 + 19 + 19)
     assert abi.stencil_adjoint_workspace(h, 7, 3) == per * (3 + 2 + 2)
+    # one segment: the checkpoint and the kept levels, no recomputation buffer
+    assert abi.stencil_adjoint_workspace(h, 200, 200) == per * (1 + 199)
     with pytest.raises(abi.StencilError):
         abi.stencil_adjoint_workspace(h, 10, 0)
     abi.stencil_destroy(h)
