@@ -182,7 +182,13 @@ class Batch:
 # ---------------------------------------------------------------------------
 class VarCoefProblem:
     """u_{t+1} = sum_k (alpha_k + beta_k kappa) u_t[p + o_k] run for nsteps with
-    checkpoints every ckpt_every steps; gradient of 0.5||u_T - target||^2."""
+    checkpoints every ckpt_every steps; gradient of 0.5||u_T - target||^2.
+
+    The forward run also keeps the inner levels of its last segment, so the
+    reverse pass recomputes every segment but that one: ckpt_every = nsteps
+    keeps every level (nsteps fields of workspace, nothing recomputed, the
+    fastest reverse pass), small ckpt_every trades recomputation for memory.
+    """
 
     def __init__(self, grid: Grid, nsteps: int, ckpt_every: int):
         self.grid, self.nsteps, self.m = grid, int(nsteps), int(ckpt_every)
