@@ -238,6 +238,7 @@ class StencilFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u0, kappa, problem: VarCoefProblem):
         ctx.problem = problem
+        ctx.u0_dtype = u0.dtype
         ctx.kappa_dtype = kappa.dtype
         out = problem.forward(u0, kappa)
         return out.clone()
@@ -245,4 +246,4 @@ class StencilFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         lam0, gk, _ = ctx.problem.backward_from(lam_T=grad_out)
-        return lam0.clone(), gk.to(ctx.kappa_dtype), None
+        return lam0.to(ctx.u0_dtype, copy=True), gk.to(ctx.kappa_dtype), None

@@ -213,6 +213,25 @@ def test_autograd_function():
     g.close()
 
 
+def test_autograd_function_fp32_grid_takes_float64_tensors():
+    """An FP32 grid fed float64 tensors: the gradients come back in the
+    inputs' dtypes, close to the FP64 oracle."""
+    shape = (12, 14, 40)
+    v = inputs.varcoef3d(shape=shape)
+    steps, m = 8, 3
+    _, _, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, False, 0.0, steps, m)
+    g = make(shape, torch.float32)
+    prob = VarCoefProblem(g, steps, m)
+    u0 = torch.tensor(v.u0, device="cuda", requires_grad=True)
+    kappa = torch.tensor(v.kappa, device="cuda", requires_grad=True)
+    uT = StencilFn.apply(u0, kappa, prob)
+    (0.5 * ((uT - torch.as_tensor(v.target, device="cuda")) ** 2).sum()).backward()
+    assert u0.grad.dtype == torch.float64 and kappa.grad.dtype == torch.float64
+    assert rel_err(u0.grad.cpu().numpy(), lam_r) <= TOL32_FWD
+    assert rel_err(kappa.grad.cpu().numpy(), gk_r) <= TOL32_GRAD
+    g.close()
+
+
 def test_adjoint_argument_errors():
     g = make((8, 8, 8), torch.float32)
     prob = VarCoefProblem(g, 4, 2)
