@@ -84,6 +84,23 @@ def test_gradient_fp32_matches_fp64_oracle():
     assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
 
 
+def test_gradient_full_size_fused_pass():
+    """256^3 FP32 Dirichlet, the benchmark's grid: four steps with a
+    checkpoint every 2, so the reverse pass runs the fused two-step kernel in
+    the benchmark's launch configuration (10-row tiles, two halo sub-tasks,
+    the flat (tile, plane) distribution) on a recomputed and on a kept
+    segment; every point of lambda_0 and of the gradient against the FP64
+    oracle."""
+    v = inputs.varcoef3d(n=256)
+    steps, m = 4, 2
+    loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, False, 0.0, steps, m)
+    uT, lam0, gk, loss, kern = gpu_grad(v, steps, m, torch.float32)
+    assert rel_err(uT, uT_r) <= TOL32_FWD, kern
+    assert abs(loss - loss_r) <= TOL32_FWD * loss_r
+    assert rel_err(lam0, lam_r) <= TOL32_FWD, kern
+    assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
+
+
 @pytest.mark.parametrize("periodic,bc", [(False, 0.0), (False, 0.3), (True, 0.0)])
 def test_gradient_fp32_ragged_matches_fp64_oracle(periodic, bc):
     """FP32 transpose on rows that end inside a 16-byte group (nx = 45), a
@@ -207,7 +224,7 @@ def test_autograd_function():
     uT = StencilFn.apply(u0, kappa, prob)
     loss = 0.5 * ((uT - torch.as_tensor(v.target, device="cuda")) ** 2).sum()
     loss.backward()
-    assert abs(float(loss) - loss_r) <= 1e-12 * loss_r
+    assert abs(float(loss.detach()) - loss_r) <= 1e-12 * loss_r
     assert rel_err(u0.grad.cpu().numpy(), lam_r) <= TOL64
     assert rel_err(kappa.grad.cpu().numpy(), gk_r) <= TOL64
     g.close()
