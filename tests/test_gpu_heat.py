@@ -231,6 +231,29 @@ def test_reductions_match_oracle():
         g.close()
 
 
+def test_reductions_full_size():
+    """The headline's FP64 reduction of a 512^3 FP32 field (single field and
+    difference of two), against pairwise double-precision sums of the same
+    FP32 values (error ~log2(N) eps relative); the maximum exactly."""
+    from paper_2512_19851_gb300.grid import Grid
+    offs, w = seven_point(0.1)
+    h = inputs.heat3d(shape=(512, 512, 512))
+    a32 = h.u0.astype(np.float32)
+    b32 = (h.u0 * 0.5 + 0.25).astype(np.float32)
+    g = Grid((512, 512, 512), offs, w, periodic=True, dtype=torch.float32)
+    g.set_field(a32, 0)
+    g.set_field(b32, 1)
+    one = g.reduce(g.bufs[0]).cpu().numpy()
+    two = g.reduce(g.bufs[0], g.bufs[1]).cpu().numpy()
+    g.close()
+    a = a32.astype(np.float64)
+    d = a - b32.astype(np.float64)  # exact: both are FP32 values of similar size
+    for got, x in ((one, a), (two, d)):
+        assert abs(got[0] - np.sum(x)) <= 1e-11 * np.sum(np.abs(x))
+        assert abs(got[1] - np.sum(x * x)) <= 1e-11 * np.sum(x * x)
+        assert got[2] == np.max(np.abs(x))
+
+
 @pytest.mark.parametrize("nx", [64, 45])
 @pytest.mark.parametrize("pinned_in,pinned_out", [(True, True), (False, False), (True, False)])
 def test_run_host_end_to_end(nx, pinned_in, pinned_out):
