@@ -32,11 +32,15 @@
 //  * Outside the interior (Dirichlet) every level is 0 by selection, never by
 //    arithmetic on ghost data: ghosts are boundary data, not variables.
 //  * Each fused level evaluates exactly the expressions of a single-step pass
-//    in the same order and adds its gradient term to the FP64 gradient as
-//    soon as it is computed, by reductions performed at L2 (the SMs never wait
-//    on the accumulator).  Level 1 of a plane runs one iteration before level
-//    2 of the same plane, so every point sums its terms in step order and a
-//    fused pass rounds exactly like K single-step passes.
+//    in the same order, so lambda rounds exactly like K single-step passes.
+//    The gradient goes to the FP64 accumulator by reductions performed at L2
+//    (the SMs never wait on it): a single-step pass adds its term; a fused
+//    pass holds level 1's term of a plane in registers until level 2 reaches
+//    that plane one iteration later and adds the two terms (in T) as one
+//    reduction, which halves the reductions, conversions and shared-memory
+//    transposes of the gradient.  The gradient then depends on how the steps
+//    are paired into passes (pairs are taken from the top of each checkpoint
+//    segment), by one rounding of T per pair.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -118,6 +122,8 @@ __device__ __forceinline__ void vst(T* p, const T (&v)[AV<T>::N])
 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 
 __device__ __forceinline__ int64_t amin(int64_t a, int64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ int64_t amax(int64_t a, int64_t b) { return a > b ? a : b; }
@@ -231,8 +237,8 @@ __device__ __forceinline__ void nsum(const XCtx& X, const T (&zm)[AV<T>::N], con
 // warp's shared scratch so that each reduction instruction covers 32
 // consecutive doubles (8 sectors instead of 32).  Either way a point's terms
 // all come from one thread, in step order, and same-thread atomics on one
-// address take effect in program order, so every point sums its terms in
-// step order, whatever the pass structure.
+// address take effect in program order, so every point sums its terms (or
+// pairs of terms) in step order.
 template <typename T>
 __device__ __forceinline__ void add_grad(const XCtx& X, bool fast, double* wsc, int lane, int64_t off, bool ok,
                                          double* __restrict__ g64, const T (&t)[AV<T>::N])
@@ -484,6 +490,43 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
             }
 
             if (pairw) {
+                if constexpr (K == 2) {
+                    if (grad && j >= 3) {
+                        // ------------------------------------ row pair, level-2 gradient
+                        // Level 2's centre this iteration is plane c1 - 1, which level 1
+                        // computed last iteration; its term there is still in g1n.  The
+                        // two steps' terms of a point are added in FP (T) and the pair
+                        // goes to the FP64 accumulator in one reduction.
+                        const T* UB = S0 + P.ub_off + rr0 * pitch;  // u_{t-1} row rr0 - 1 at plane c1 - 1
+                        if (j == 3) {
+                            // u_{t-1} of the plane below the first level-2 centre
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) vld(UB + (i + 1) * pitch + x, ubp[i]);
+                        } else {
+                            const int64_t c2 = c1 - 1;
+                            T uv[4][VN], uz[2][VN];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) vld(UB + i * pitch + x, uv[i]);
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) vld(S1 + P.ub_off + (rr0 + 1 + i) * pitch + x, uz[i]);
+#pragma unroll
+                            for (int i = 0; i < 2; ++i) {
+                                const T* Ur = UB + (i + 1) * pitch;
+                                const T left = Ur[X.lcl], right = Ur[X.lcr];
+                                T nb[VN], gp[VN];
+                                nsum(X, ubp[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
+#pragma unroll
+                                for (int e = 0; e < VN; ++e) {
+                                    const T g2 = mul_rn(l1p[i][e], fma(bc, uv[i + 1][e], mul_rn(bn, nb[e])));
+                                    gp[e] = add_rn(g1n[i][e], g2);
+                                    ubp[i][e] = uv[i + 1][e];
+                                }
+                                add_grad(X, fastw, wscr, lane, P.origin + c2 * P.plane + (y0 + rr0 + i) * P.pitch + x,
+                                         act && rr0 + i < tye, g64, gp);
+                            }
+                        }
+                    }
+                }
                 // ------------------------------------------------ row pair, level 1
                 const T* L = S0 + (rr0 - 1 + K) * pitch;  // lambda row rr0 - 1
                 const T* Kp = L + P.kap_off;
@@ -574,10 +617,10 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                         T* M = mring + (size_t)wslot * P.ring_elems + P.xl + (rr0 + 1) * pitch;
                         store_pair(okw, X, act, rr0, tye, M + x, (int64_t)pitch, m1n);
                     }
-                    // this step's gradient term goes to the accumulator now; the
-                    // next step's (level 2, one iteration later) follows it, so
-                    // every point sums its terms in step order
-                    if (grad && own1) {
+                    // K == 1: this step's gradient term goes to the accumulator now.
+                    // K == 2: it stays in g1n until the next iteration, where level 2's
+                    // term of the same plane joins it (one reduction per point and pass)
+                    if (K == 1 && grad && own1) {
 #pragma unroll
                         for (int i = 0; i < 2; ++i)
                             add_grad(X, fastw, wscr, lane, P.origin + c1 * P.plane + (y0 + rr0 + i) * P.pitch + x,
@@ -666,10 +709,9 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                     atimeout(P.status);
                     dead = true;
                 }
-                if (pairw && j >= 3) {
+                if (pairw && j >= 4) {
                     // ------------------------------------------------ row pair, level 2
-                    const T* UB = S0 + P.ub_off + rr0 * pitch;  // u_{t-1} row rr0 - 1 at the level-2 centre
-                    if (j >= 4) {
+                    {
                         const int64_t c2 = c1 - 1;
                         const T* M = mring + (size_t)rslot * P.ring_elems + P.xl + rr0 * pitch;  // mu_1 row rr0 - 1
                         T mup[VN], mdn[VN];
@@ -687,31 +729,6 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                         }
                         store_pair(okw, X, act, rr0, tye, lam_out + P.origin + c2 * P.plane + (y0 + rr0) * P.pitch + x,
                                    P.pitch, l2);
-                        if (grad) {
-                            T uv[4][VN], uz[2][VN];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) vld(UB + i * pitch + x, uv[i]);
-#pragma unroll
-                            for (int i = 0; i < 2; ++i) vld(S1 + P.ub_off + (rr0 + 1 + i) * pitch + x, uz[i]);
-#pragma unroll
-                            for (int i = 0; i < 2; ++i) {
-                                const T* Ur = UB + (i + 1) * pitch;
-                                const T left = Ur[X.lcl], right = Ur[X.lcr];
-                                T nb[VN], g2[VN];
-                                nsum(X, ubp[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
-#pragma unroll
-                                for (int e = 0; e < VN; ++e) {
-                                    g2[e] = mul_rn(l1p[i][e], fma(bc, uv[i + 1][e], mul_rn(bn, nb[e])));
-                                    ubp[i][e] = uv[i + 1][e];
-                                }
-                                add_grad(X, fastw, wscr, lane, P.origin + c2 * P.plane + (y0 + rr0 + i) * P.pitch + x,
-                                         act && rr0 + i < tye, g64, g2);
-                            }
-                        }
-                    } else if (grad) {
-                        // j == 3: u_{t-1} of the plane below the first level-2 centre
-#pragma unroll
-                        for (int i = 0; i < 2; ++i) vld(UB + (i + 1) * pitch + x, ubp[i]);
                     }
                 }
                 if (pairw && j >= 2) {

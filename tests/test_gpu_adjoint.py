@@ -21,6 +21,12 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
 TOL32_FWD = 1e-5
 TOL32_GRAD = 1e-3
+# Different pairings of steps into fused passes: one extra rounding of the
+# working precision per pair of gradient terms (2^-24 or 2^-53 relative to the
+# pair), amplified by the cancellation between a point's terms over the run
+# (|sum of terms| is at least ~1e-2 of sum |terms| on these fields).
+PAIR32 = 1e-5
+PAIR64 = 1e-13
 ALPHA = [1.0] + [0.0] * 6
 BETA = [-6.0] + [1.0] * 6
 
@@ -120,7 +126,8 @@ def test_gradient_wide_rows_matches_oracle(periodic, bc):
     """Rows wider than one warp of x groups: FP32 rows of 150 points (38
     groups, the last one ragged) and FP64 rows of 70 points (35 groups), so a
     tile's halo rows take two 32-group sub-tasks per halo warp, the second
-    partly filled.  FP32 m = 5 and m = 1 must also agree bitwise."""
+    partly filled.  FP32 m = 5 and m = 1 give the same lambda_0 bitwise and
+    gradients within the pairing tolerance."""
     steps, m = 10, 5
     v = inputs.varcoef3d(shape=(14, 22, 150))
     loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, bc, steps, m)
@@ -129,7 +136,8 @@ def test_gradient_wide_rows_matches_oracle(periodic, bc):
     assert rel_err(lam0, lam_r) <= TOL32_FWD, kern
     assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
     other = gpu_grad(v, steps, 1, torch.float32, periodic, bc)
-    assert np.array_equal(lam0, other[1]) and np.array_equal(gk, other[2])
+    assert np.array_equal(lam0, other[1])
+    assert rel_err(other[2], gk) <= PAIR32
     v = inputs.varcoef3d(shape=(14, 22, 70))
     loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, bc, steps, m)
     uT, lam0, gk, loss, kern = gpu_grad(v, steps, m, torch.float64, periodic, bc)
@@ -139,22 +147,32 @@ def test_gradient_wide_rows_matches_oracle(periodic, bc):
 
 
 def test_checkpoint_interval_does_not_change_gradient_fp32():
-    """FP32 grids: fused two-step passes round exactly like single steps, so
-    m = 1, 6 and 20 give bitwise equal lambda_0 and gradients."""
+    """FP32 grids: fused two-step passes round lambda exactly like single
+    steps, so m = 1, 6 and 20 give bitwise equal lambda_0.  The gradient adds
+    the two fused steps' terms of a point before the FP64 accumulator, so it
+    is bitwise equal where the steps pair up alike (m = 6 and 20 over 20 steps:
+    every segment has an even length) and within PAIR32 otherwise (m = 1)."""
     v = inputs.varcoef3d(shape=(20, 26, 44))
     base = gpu_grad(v, 20, 20, torch.float32, True)
-    for m in (1, 6):
-        other = gpu_grad(v, 20, m, torch.float32, True)
-        assert np.array_equal(base[1], other[1]) and np.array_equal(base[2], other[2])
+    other = gpu_grad(v, 20, 6, torch.float32, True)
+    assert np.array_equal(base[1], other[1]) and np.array_equal(base[2], other[2])
+    other = gpu_grad(v, 20, 1, torch.float32, True)
+    assert np.array_equal(base[1], other[1])
+    assert rel_err(other[2], base[2]) <= PAIR32
 
 
 def test_checkpoint_interval_does_not_change_gradient():
-    """Recomputation is deterministic: m = 1, 7 and 20 give bitwise equal results."""
+    """Recomputation is deterministic: m = 1, 7, 10 and 20 give bitwise equal
+    lambda_0; gradients are bitwise equal for m = 10 and 20 (the same pairs of
+    steps) and within PAIR64 for m = 1 and 7."""
     v = inputs.varcoef3d(shape=(20, 24, 32))
     base = gpu_grad(v, 20, 20, torch.float64)
+    other = gpu_grad(v, 20, 10, torch.float64)
+    assert np.array_equal(base[1], other[1]) and np.array_equal(base[2], other[2])
     for m in (1, 7):
         other = gpu_grad(v, 20, m, torch.float64)
-        assert np.array_equal(base[1], other[1]) and np.array_equal(base[2], other[2])
+        assert np.array_equal(base[1], other[1])
+        assert rel_err(other[2], base[2]) <= PAIR64
 
 
 def test_dot_product_identity_gpu():
