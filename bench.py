@@ -425,8 +425,77 @@ def extra_configs(dev, hbm_peak):
                                "max_normwise_err_vs_plain_f64": err})
     bp.close()
     bt.close()
+    del bp, bt
     torch.cuda.empty_cache()
+    out.update(frontend_laplace(dev, hbm_peak))
     return out
+
+
+def frontend_laplace(dev, hbm_peak, n=16384, iters=1000):
+    """Example 1 of the paper (2D Laplace/Jacobi written as slice assignments,
+    boundary ring 1, interior 0) at the paper's per-GPU size, 16384^2 and
+    1000 iterations, recorded and executed through the frontend.  Wall time
+    of recording the 1000 assignments plus sync(), after one untimed
+    identical run (array placement, graph capture)."""
+    import numpy as np
+    import torch
+
+    from paper_2512_19851_gb300.frontend import Program
+
+    out = {}
+    for dt, name in ((np.float64, "laplace2d_frontend_f64"), (np.float32, "laplace2d_frontend_f32")):
+        p = Program(device=dev)
+        u1, u2 = p.create_array((n, n), dt), p.create_array((n, n), dt)
+        u1[0, :] = u1[-1, :] = u1[:, 0] = u1[:, -1] = 1
+        u2[0, :] = u2[-1, :] = u2[:, 0] = u2[:, -1] = 1
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for rep in range(2):
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            for _ in range(iters):
+                u2[1:-1, 1:-1] = 0.25 * (u1[:-2, 1:-1] + u1[2:, 1:-1] + u1[1:-1, :-2] + u1[1:-1, 2:])
+                u1, u2 = u2, u1
+            t_rec = time.perf_counter() - t
+            e0.record(stream)
+            p.sync()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            wall = time.perf_counter() - t
+        dev_s = e0.elapsed_time(e1) * 1e-3
+        pts = (n - 2) ** 2
+        esz = np.dtype(dt).itemsize
+        per = dev_s / iters
+        out[name] = {"glups": pts * iters / dev_s / 1e9, "us_per_iteration": per * 1e6,
+                     "glups_wall_incl_recording": pts * iters / wall / 1e9, "recording_s": t_rec,
+                     "hbm_frac": 2 * esz * pts / per / 1e9 / hbm_peak, "grid": [n, n], "iterations": iters,
+                     "timing": "CUDA events around sync() (the 1000 sweeps), second of two identical runs; "
+                               "glups_wall_incl_recording adds the Python recording of the 1000 assignments",
+                     "kernel": _fe_kernel(p), "config": _fe_config(p)}
+        if dt == np.float64:
+            # four DP instructions per point (a chain of four FMAs), the FP64 pipe's rate
+            out[name].update({"bound": "alu", "alu_peak_glups": FP64_INSTR_PER_S / 4 / 1e9,
+                              "alu_frac": pts * iters / dev_s / (FP64_INSTR_PER_S / 4)})
+        p.close()
+        del u1, u2, p
+        torch.cuda.empty_cache()
+    return out
+
+
+def _fe_kernel(p):
+    from paper_2512_19851_gb300 import abi
+    for key, h in p._handles.items():
+        if key[0] == "grid":
+            return abi.stencil_info(h.h)[2]
+    return None
+
+
+def _fe_config(p):
+    from paper_2512_19851_gb300 import abi
+    for key, h in p._handles.items():
+        if key[0] == "grid":
+            return list(abi.stencil_tune_config(h.h))
+    return None
 
 
 # ----------------------------------------------------------------------------- CPU oracle
