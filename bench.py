@@ -581,6 +581,13 @@ def run_profile(case: str, launches: int = 3):
         for _ in range(2 + launches):
             abi.stencil_step(g.h, 1, s)
             abi.stencil_reduce(g.h, g.bufs[g.current_slot()].data_ptr(), 0, red.data_ptr(), s)
+    elif case == "laplace2d_f64":
+        # Example 1's update in FP64 on a 6144^2 interior (302 MB per buffer)
+        n = 6144
+        g = Grid((n, n), [(-1, 0), (1, 0), (0, -1), (0, 1)], [0.25] * 4, bc_value=1.0, dtype=torch.float64)
+        g.set_field(np.random.default_rng(0).random((n, n)))
+        for _ in range(2 + launches):
+            abi.stencil_step(g.h, 1, s)
     elif case == "heat2d":
         offs, w, _ = stencils.heat2d()
         g = Grid((256, 256), offs, w, dtype=torch.float64)
@@ -633,7 +640,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--headline-only", action="store_true")
-    ap.add_argument("--profile", default=None, help="run one small case for ncu (heat3d_f32, heat3d_f32_512, heat3d_f64, wave, "
+    ap.add_argument("--profile", default=None, help="run one small case for ncu (heat3d_f32, heat3d_f32_512, heat3d_f64, laplace2d_f64, wave, "
                                                       "varcoef_fwd, varcoef_adj) and exit")
     args = ap.parse_args()
     if args.profile:
