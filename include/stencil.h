@@ -54,7 +54,7 @@
  *   stencil_layout() returns the padded shape and the interior origin.  The
  *   buffer's base address must be 16-byte aligned.  Ghost cells belong to the
  *   library: it (re)writes them before a step when the buffer was bound or
- *   marked dirty.
+ *   marked dirty, unless the handle was created with ST_FLAG_CALLER_GHOSTS.
  */
 #ifndef STENCIL_H
 #define STENCIL_H
@@ -90,6 +90,19 @@ typedef enum { ST_DIRICHLET = 0, ST_PERIODIC = 1 } st_bc;
 #define ST_FLAG_TWO_STEP 2u  /* start with two sweeps per pass over HBM where
                                 supported (FP32 constant symmetric 3D 7-point
                                 star); stencil_tune may change the choice */
+#define ST_FLAG_CALLER_GHOSTS 4u  /* Dirichlet ghost cells hold the caller's
+                                values (any value per cell: per-face or
+                                varying boundary data, such as Example 1's
+                                boundary ring when its edges differ, Sec.
+                                III-A): the library never writes them and every
+                                sweep reads them, and bc_value is ignored.  The
+                                caller fills the ghosts of both time-level
+                                buffers (stencil_layout gives the layout).
+                                Dirichlet only (ST_ERR_ARG with periodic);
+                                2D grids then take the one-thread-per-point
+                                kernel, 3D grids single sweeps; the adjoint
+                                and stencil_step_ckpt return
+                                ST_ERR_UNSUPPORTED */
 
 #define ST_MAX_POINTS 64     /* most neighbour points per stencil */
 #define ST_MAX_RADIUS 8      /* widest ghost region */
@@ -121,7 +134,8 @@ const char* stencil_last_error(void);
  *   bc          ST_DIRICHLET (ghosts = bc_value) or ST_PERIODIC.
  *   dtype       storage and arithmetic type of the fields.
  *   time_levels 1: form (1); 2: leapfrog form (3).
- *   flags       0, ST_FLAG_GENERIC or ST_FLAG_TWO_STEP.
+ *   flags       0 or a combination of ST_FLAG_GENERIC, ST_FLAG_TWO_STEP and
+ *               ST_FLAG_CALLER_GHOSTS.
  * Copies all arrays; allocates only library scratch.  *out is NULL on error.
  */
 st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radius, int npts,

@@ -22,6 +22,10 @@ Functions and the passage each follows:
   checkpoint-every-m recomputation is :func:`varcoef7_gradient`.
 * :func:`wave25` -- radius-4 star Laplacian in a leapfrog update.
 * :func:`reduce` -- sum, sum of squares and max-abs in double precision.
+* :func:`sweep_ghosts` (in :mod:`oracle.ghosts`) -- the sweep of
+  :func:`sweep_const` on a padded array whose Dirichlet ring holds arbitrary
+  per-cell values (Example 1's boundary ring set by slice assignment, Sec.
+  III-A), plain numpy.
 * :func:`taylor_second_derivative_coeffs` (in :mod:`oracle.taylor`) -- the
   8th-order central coefficients from the Taylor conditions.
 
@@ -36,6 +40,7 @@ import sys
 
 import numpy as np
 
+from .ghosts import sweep_ghosts  # noqa: F401
 from .taylor import taylor_second_derivative_coeffs  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

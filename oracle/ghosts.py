@@ -1,0 +1,53 @@
+"""Constant-weight sweep with arbitrary Dirichlet ghost values (part of the
+oracle; TEST INFRASTRUCTURE ONLY, see the package header).
+
+Example 1 of Sec. III-A sets the boundary ring of both arrays once by slice
+assignment and never writes it again; the update reads the ring wherever a
+neighbour falls outside the interior.  The ring may hold any values (one per
+cell), not only one constant.  This module evaluates that definition
+literally on a padded array:
+
+    for every interior p:  out[p] = sum_k w_k * in[p + o_k]   (offset order)
+
+with ``in`` and ``out`` both padded by r cells on every side, the ring copied
+unchanged from step to step, and the two arrays swapped after each step
+(Sec. III-A's ``u1, u2 = u2, u1``).  Plain numpy: for each offset the shifted
+interior view of ``in`` is multiplied by w_k and added to the accumulator in
+offset order (a multiply, then an add: no fused multiply-add), which is the
+order the C oracle uses.  Float64 unless ``dtype`` says otherwise.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def sweep_ghosts(u_padded, radius: int, offsets, weights, nsteps: int, dtype=np.float64):
+    """Run ``nsteps`` sweeps on a padded array (interior plus ``radius`` ghost
+    cells per side on every axis); returns the padded array after the last
+    step (ring unchanged)."""
+    r = int(radius)
+    u = np.array(u_padded, dtype=dtype, copy=True)
+    nd = u.ndim
+    offs = [tuple(int(c) for c in o) for o in offsets]
+    if any(len(o) != nd for o in offs):
+        raise ValueError("one offset component per axis")
+    if any(abs(c) > r for o in offs for c in o):
+        raise ValueError("an offset reaches beyond the ghost ring")
+    w = [dtype(x) for x in weights]
+    if len(w) != len(offs):
+        raise ValueError("one weight per offset")
+    n = [s - 2 * r for s in u.shape]
+    if min(n) < 1:
+        raise ValueError("empty interior")
+    inner = tuple(slice(r, r + m) for m in n)
+    tmp = u.copy()
+    for _ in range(int(nsteps)):
+        acc = np.zeros(n, dtype=dtype)
+        for o, wk in zip(offs, w):
+            src = tuple(slice(r + c, r + c + m) for c, m in zip(o, n))
+            acc = acc + wk * u[src]
+        tmp[inner] = acc
+        u, tmp = tmp, u
+        # the ring of the array that now holds the older level is still the
+        # initial ring (sweeps write interiors only)
+    return u

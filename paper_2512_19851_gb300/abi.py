@@ -29,6 +29,7 @@ ST_F32, ST_F64 = 0, 1
 ST_DIRICHLET, ST_PERIODIC = 0, 1
 ST_FLAG_GENERIC = 1
 ST_FLAG_TWO_STEP = 2
+ST_FLAG_CALLER_GHOSTS = 4
 ST_SLOT_A, ST_SLOT_B, ST_SLOT_COEFF = 0, 1, 2
 ST_MAX_POINTS = 64
 ST_MAX_RADIUS = 8

@@ -97,6 +97,7 @@ struct st_grid_s {
     BatchPlan* plan = nullptr;  // 2D grids on the persistent tile kernel (a batch of one)
     bool plan_bound = false;
     bool pairs = false;         // two-step passes chosen by stencil_tune (3D 7-point heat, FP32)
+    bool caller_ghosts = false; // ST_FLAG_CALLER_GHOSTS: Dirichlet ghost cells hold the caller's values
     void* staging = nullptr;    // dense interior buffer of stencil_run_host
     // stencil_run_host splits each host copy over a few streams so that
     // several copy engines share it (created on first use)
@@ -156,7 +157,10 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     if (bc != ST_DIRICHLET && bc != ST_PERIODIC) return fail(ST_ERR_ARG, "stencil_create: bad bc");
     if (dtype != ST_F32 && dtype != ST_F64) return fail(ST_ERR_ARG, "stencil_create: bad dtype");
     if (time_levels != 1 && time_levels != 2) return fail(ST_ERR_ARG, "stencil_create: time_levels must be 1 or 2");
-    if (flags & ~(ST_FLAG_GENERIC | ST_FLAG_TWO_STEP)) return fail(ST_ERR_ARG, "stencil_create: unknown flags");
+    if (flags & ~(ST_FLAG_GENERIC | ST_FLAG_TWO_STEP | ST_FLAG_CALLER_GHOSTS))
+        return fail(ST_ERR_ARG, "stencil_create: unknown flags");
+    if ((flags & ST_FLAG_CALLER_GHOSTS) && bc != ST_DIRICHLET)
+        return fail(ST_ERR_ARG, "stencil_create: ST_FLAG_CALLER_GHOSTS needs a Dirichlet boundary");
     if (radius < 0 || radius > ST_MAX_RADIUS) return fail(ST_ERR_ARG, "stencil_create: radius out of range");
     int64_t d3[3] = {1, 1, 1};
     for (int i = 0; i < ndim; ++i) {
@@ -206,7 +210,10 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     g->dtype = dtype;
     g->levels = time_levels;
     g->flags = flags;
-    g->pairs = (flags & ST_FLAG_TWO_STEP) != 0;
+    g->caller_ghosts = (flags & ST_FLAG_CALLER_GHOSTS) != 0;
+    // the two-step 3D pass substitutes bc_value for ghost reads, so caller
+    // ghosts keep single sweeps
+    g->pairs = (flags & ST_FLAG_TWO_STEP) != 0 && !g->caller_ghosts;
     FamilyDesc d{};
     d.g = g->g;
     d.npts = npts;
@@ -219,6 +226,13 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     d.star = is_star(g->off, npts, ndim);
     d.force_generic = (flags & ST_FLAG_GENERIC) != 0;
     g->fam = select_family(d);
+    if (g->fam.kind == FAM_2D_TILE && g->caller_ghosts) {
+        // the persistent 2D tile kernel substitutes bc_value for points
+        // outside the interior; the one-thread-per-point kernel reads the
+        // ghost cells themselves
+        d.force_generic = true;
+        g->fam = select_family(d);
+    }
     if (g->fam.kind == FAM_2D_TILE) {
         std::vector<int32_t> off2(2 * npts);
         for (int k = 0; k < npts; ++k) {
@@ -429,7 +443,7 @@ static st_status refresh_ghosts(st_grid_t g, cudaStream_t s)
 {
     for (int slot = 0; slot < 3; ++slot) {
         if (!g->stale[slot] || !g->buf[slot]) continue;
-        if (g->bc == ST_DIRICHLET || slot == ST_SLOT_COEFF) {
+        if ((g->bc == ST_DIRICHLET && !g->caller_ghosts) || slot == ST_SLOT_COEFF) {
             const double v = (slot == ST_SLOT_COEFF) ? 0.0 : g->bc_value;
             ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, g->buf[slot], g->g, v, s));
         }
@@ -449,7 +463,10 @@ static st_status check_ready(st_grid_t g, const char* who)
 
 // Two-step passes (temporal blocking) where the family has them; a source
 // term needs its step index per sweep, so it keeps single sweeps.
-static bool use_pairs(st_grid_t g) { return g->pairs && g->src < 0 && star3d_pair_supported(g->fam); }
+static bool use_pairs(st_grid_t g)
+{
+    return g->pairs && !g->caller_ghosts && g->src < 0 && star3d_pair_supported(g->fam);
+}
 
 // Slot of the newest level after n steps from slot `cur`: every launch (one
 // sweep or one two-step pass) writes the other slot.
@@ -564,7 +581,8 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
     g->last = s;
     rc = refresh_ghosts(g, s);
     if (rc != ST_OK) return rc;
-    if ((!g->plan || !g->plan_bound) && g->levels == 1 && g->src < 0 && star3d_pair_supported(g->fam)) {
+    if ((!g->plan || !g->plan_bound) && g->levels == 1 && g->src < 0 && !g->caller_ghosts &&
+        star3d_pair_supported(g->fam)) {
         // single sweeps or two-step passes: time both on the bound data, keep
         // the faster, and put the current level back
         const size_t bytes = (size_t)g->g.elems * g->g.esize;
@@ -761,6 +779,7 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stre
     if (!g || !ws) return fail(ST_ERR_ARG, "stencil_step_ckpt: NULL argument");
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_step_ckpt: nsteps >= 0, ckpt_every >= 1");
     if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_step_ckpt: one time level only");
+    if (g->caller_ghosts) return fail(ST_ERR_UNSUPPORTED, "stencil_step_ckpt: not with ST_FLAG_CALLER_GHOSTS");
     if (((uintptr_t)ws & 15u) != 0) return fail(ST_ERR_ARG, "stencil_step_ckpt: workspace not 16-byte aligned");
     st_status rc = check_ready(g, "stencil_step_ckpt");
     if (rc != ST_OK) return rc;
@@ -806,6 +825,7 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     if (!g || !ws || !lambda || !lambda_tmp) return fail(ST_ERR_ARG, "stencil_adjoint: NULL argument");
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_adjoint: nsteps >= 0, ckpt_every >= 1");
     if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: one time level only");
+    if (g->caller_ghosts) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: not with ST_FLAG_CALLER_GHOSTS");
     if (lambda == lambda_tmp) return fail(ST_ERR_ALIAS, "stencil_adjoint: lambda and lambda_tmp alias");
     if ((((uintptr_t)ws) | ((uintptr_t)lambda) | ((uintptr_t)lambda_tmp) | ((uintptr_t)grad)) & 15u)
         return fail(ST_ERR_ARG, "stencil_adjoint: buffers must be 16-byte aligned");

@@ -34,8 +34,11 @@ describes its frontend and backend:
   u_out[p] = sum_k w_k u_in[p + o_k] with offsets o_k read off the slice
   bounds and weights w_k from the constant factors; the ghost width of an
   array is the largest offset of the kernels that touch it (Sec. III-C
-  "Data layout").  The ring outside the interior must hold one value, which
-  becomes the Dirichlet boundary value of the sweep (Example 1's ring of 1s).
+  "Data layout").  The ring outside the interior is the Dirichlet boundary:
+  when both arrays' rings hold one value it becomes the sweep's boundary
+  value (Example 1's ring of 1s); otherwise (per-face or varying values) the
+  rings are handed to the library as caller-owned ghost cells, which every
+  sweep reads and none writes.
 * Execution: a run of nodes with the same AST that alternate between the same
   two arrays (the ``u1, u2 = u2, u1`` loop) becomes ONE ``stencil_step(n)``
   call on a grid handle whose two time-level buffers are the two arrays'
@@ -47,8 +50,8 @@ describes its frontend and backend:
 Every sweep runs in libstencil's kernels; this module only records,
 analyses, allocates (through torch) and calls the C ABI.  Expressions that
 do not lower (products of arrays, a constant term, an output region other
-than a centred interior, several input arrays, non-uniform boundary rings,
-assignments to an array after a sweep has written it on the device) raise
+than a centred interior, several input arrays, assignments to an array after
+a sweep has written it on the device) raise
 ``UnsupportedExpression``; there is no CPU evaluation path.
 """
 from __future__ import annotations
@@ -536,13 +539,8 @@ class _Executor:
 
     def _run(self, members, n) -> None:
         for m in members:
-            lo = m.lowered
             for a in m.args:
-                self._place(a, lo.ghost)
-            bv = {m.args[0].boundary, m.args[1].boundary}
-            if None in bv or len(bv) != 1:
-                raise UnsupportedExpression("the ring outside the interior must hold one value in both arrays "
-                                            "(a Dirichlet boundary)")
+                self._place(a, m.lowered.ghost)
         if len(members) > 1 and _batchable(members):
             self._run_batch(members, n)
         else:
@@ -560,13 +558,19 @@ class _Executor:
         abi = self.abi
         lo, src, dst = m.lowered, m.args[1], m.args[0]
         pair = frozenset((src.dev.data_ptr(), dst.dev.data_ptr()))
-        key = ("grid", dst.shape, lo, dst.dtype.str, dst.boundary, pair)
+        # one value on both rings: the library's Dirichlet value (it fills the
+        # ghosts with it); otherwise the rings are the caller's ghost cells,
+        # which the sweep reads and never writes
+        uniform = src.boundary is not None and src.boundary == dst.boundary
+        mode = ("bc", dst.boundary) if uniform else ("caller",)
+        key = ("grid", dst.shape, lo, dst.dtype.str, mode, pair)
         h = self.prog._handles.get(key)
         if h is None:
             dims = tuple(s - 2 * lo.ghost for s in dst.shape)
             h = _Handle(abi, abi.stencil_create(len(dims), dims, lo.ghost, list(lo.offsets), list(lo.weights), None,
-                                                abi.ST_DIRICHLET, dst.boundary,
-                                                abi.ST_F64 if dst.dtype == np.float64 else abi.ST_F32, 1, 0), False)
+                                                abi.ST_DIRICHLET, dst.boundary if uniform else 0.0,
+                                                abi.ST_F64 if dst.dtype == np.float64 else abi.ST_F32, 1,
+                                                0 if uniform else abi.ST_FLAG_CALLER_GHOSTS), False)
             self.prog._handles[key] = h
             abi.stencil_bind(h.h, abi.ST_SLOT_A, src.dev.data_ptr())
             abi.stencil_bind(h.h, abi.ST_SLOT_B, dst.dev.data_ptr())
@@ -662,9 +666,12 @@ def _batchable(members) -> bool:
     """Fused members that one batched launch can run: 2D, radius 1 in a 3x3
     neighbourhood, ghost width 1, one dtype and one boundary value."""
     a0 = members[0].args[0]
+    if a0.boundary is None:
+        return False
     for m in members:
-        a = m.args[0]
-        if len(a.shape) != 2 or m.lowered.ghost != 1 or a.dtype != a0.dtype or a.boundary != a0.boundary:
+        if len(m.args[0].shape) != 2 or m.lowered.ghost != 1 or m.args[0].dtype != a0.dtype:
+            return False
+        if any(a.boundary is None or a.boundary != a0.boundary for a in m.args):
             return False
     return True
 

@@ -25,7 +25,7 @@ class Grid:
     """A grid handle with its two time-level buffers (and coefficient field)."""
 
     def __init__(self, shape, offsets, alpha, beta=None, periodic=False, bc_value=0.0, dtype=torch.float64,
-                 time_levels=1, radius=0, generic=False, device=None, two_step=False):
+                 time_levels=1, radius=0, generic=False, device=None, two_step=False, caller_ghosts=False):
         self.shape = tuple(int(s) for s in shape)
         self.ndim = len(self.shape)
         self.dtype = dtype
@@ -34,7 +34,8 @@ class Grid:
         self.h = abi.stencil_create(self.ndim, self.shape, radius, offsets, alpha, beta,
                                     ST_PERIODIC if periodic else ST_DIRICHLET, bc_value, _ST_DTYPE[dtype],
                                     time_levels, (ST_FLAG_GENERIC if generic else 0) |
-                                    (abi.ST_FLAG_TWO_STEP if two_step else 0))
+                                    (abi.ST_FLAG_TWO_STEP if two_step else 0) |
+                                    (abi.ST_FLAG_CALLER_GHOSTS if caller_ghosts else 0))
         self.padded, self.origin, self.elems = abi.stencil_layout(self.h, self.ndim)
         self.radius, self.npts, self.kernel = abi.stencil_info(self.h)
         self.bufs = [torch.zeros(self.padded, dtype=dtype, device=self.device) for _ in range(2)]
@@ -48,6 +49,12 @@ class Grid:
     # -- views -------------------------------------------------------------
     def interior(self, t: torch.Tensor) -> torch.Tensor:
         return t[tuple(slice(o, o + s) for o, s in zip(self.origin, self.shape))]
+
+    def ring(self, t: torch.Tensor) -> torch.Tensor:
+        """View of a buffer's interior plus its ghost ring (radius r on every
+        side), the region ST_FLAG_CALLER_GHOSTS leaves to the caller."""
+        r = self.radius
+        return t[tuple(slice(o - r, o + s + r) for o, s in zip(self.origin, self.shape))]
 
     def new_field(self, dtype=None) -> torch.Tensor:
         return torch.zeros(self.padded, dtype=dtype or self.dtype, device=self.device)

@@ -88,6 +88,7 @@ def test_radius_is_derived_from_offsets():
     (dict(dtype=7), abi.ST_ERR_ARG),
     (dict(time_levels=3), abi.ST_ERR_ARG),
     (dict(flags=8), abi.ST_ERR_ARG),
+    (dict(bc=abi.ST_PERIODIC, flags=abi.ST_FLAG_CALLER_GHOSTS), abi.ST_ERR_ARG),
     (dict(alpha=[float("nan"), 0.25, 0.25]), abi.ST_ERR_ARG),
 ])
 def test_create_rejects_bad_arguments(kw, code):
@@ -151,3 +152,20 @@ def test_batch_create_validation_and_layout():
     abi.stencil_batch_destroy(h)
     with pytest.raises(abi.StencilError):
         abi.stencil_batch_create([[1, 10]], inputs.OFFSETS_BOX9, np.ones((1, 9)), abi.ST_PERIODIC, 0.0, abi.ST_F32)
+
+
+def test_caller_ghosts_choose_kernels_that_read_ghost_cells():
+    """A 2D FP32 grid leaves the persistent tile kernel (which substitutes the
+    boundary value) for the one-thread-per-point kernel when its ghosts are
+    the caller's; 3D keeps the star kernel."""
+    h = abi.stencil_create(2, (64, 64), 0, [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)], [0.2] * 5, dtype=abi.ST_F32)
+    assert abi.stencil_info(h)[2] == "tile2d_persistent"
+    abi.stencil_destroy(h)
+    h = abi.stencil_create(2, (64, 64), 0, [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)], [0.2] * 5, dtype=abi.ST_F32,
+                           flags=abi.ST_FLAG_CALLER_GHOSTS)
+    assert abi.stencil_info(h)[2] == "generic_point"
+    abi.stencil_destroy(h)
+    h = _create(offsets=[(0, 0, 0), (0, 0, 1), (0, 0, -1), (0, 1, 0), (0, -1, 0), (1, 0, 0), (-1, 0, 0)],
+                alpha=[0.4] + [0.1] * 6, flags=abi.ST_FLAG_CALLER_GHOSTS)
+    assert abi.stencil_info(h)[2].startswith("star3d")
+    abi.stencil_destroy(h)

@@ -147,13 +147,37 @@ def test_3d_heat_program(dtype, tol):
     p.close()
 
 
-def test_errors_surface_at_sync():
+@pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-12), (np.float32, 1e-5)])
+def test_edges_with_different_values(dtype, tol):
+    """Example 1 with a hot top edge (1) and the other edges at 0 in one
+    array, and another ring in the other: the rings go to the library as
+    caller-owned ghost cells; each sweep reads its input array's ring."""
     p = Program()
-    a, b = p.create_array((8, 8)), p.create_array((8, 8))
-    a[0, :] = 2.0                        # one edge differs from the others
-    b[1:-1, 1:-1] = a[1:-1, 1:-1]
-    with pytest.raises(UnsupportedExpression, match="one value"):
-        p.sync()
+    u1, u2 = p.create_array((50, 41), dtype), p.create_array((50, 41), dtype)
+    u1[0, :] = 1.0
+    u2[0, :] = 1.0
+    u2[:, -1] = 0.5                      # differs from u1's ring
+    for _ in range(31):
+        u2[1:-1, 1:-1] = 0.25 * (u1[:-2, 1:-1] + u1[2:, 1:-1] + u1[1:-1, :-2] + u1[1:-1, 2:])
+        u1, u2 = u2, u1
+    p.sync()
+    # reference: steps alternate between the two rings, one step at a time
+    r1 = np.zeros((50, 41))
+    r1[0, :] = 1.0
+    r2 = r1.copy()
+    r2[:, -1] = 0.5
+    a, b = r1, r2
+    for _ in range(31):
+        out = oracle.sweep_ghosts(a, 1, OFF4, [0.25] * 4, 1)
+        b = b.copy()
+        b[1:-1, 1:-1] = out[1:-1, 1:-1]
+        a, b = b, a
+    assert rel_err(u1.get().astype(np.float64), a) <= tol
+    assert rel_err(u2.get().astype(np.float64), b) <= tol
+    p.close()
+
+
+def test_errors_surface_at_sync():
     p = Program()
     a, b = p.create_array((8, 8)), p.create_array((8, 8))
     b[1:-1, 1:-1] = a[1:-1, 1:-1]

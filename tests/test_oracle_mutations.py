@@ -112,3 +112,45 @@ def test_pins_catch_planted_mistake(name):
 def test_unmutated_oracle_passes_the_same_pins():
     for key, fn in PINS.items():
         fn()
+
+
+# ------------------------------------------------ the numpy ghost-ring sweep
+GHOST_SRC = os.path.join(os.path.dirname(oracle.__file__), "ghosts.py")
+
+GHOST_MUTANTS = {
+    "ghost sweep drops the last neighbour": ("for o, wk in zip(offs, w):", "for o, wk in zip(offs[:-1], w[:-1]):"),
+    "ghost sweep reads the offset with the wrong sign": ("slice(r + c, r + c + m)", "slice(r - c, r - c + m)"),
+    "ghost sweep transposes the offset axes": ("for c, m in zip(o, n))", "for c, m in zip(o[::-1], n))"),
+    "ghost sweep never swaps the arrays": ("u, tmp = tmp, u", "tmp = tmp"),
+    "ghost sweep reads the output array": ("acc = acc + wk * u[src]", "acc = acc + wk * tmp[src]"),
+}
+
+GHOST_PINS = [
+    lambda: [pins.test_ghost_sweep_uniform_ring_equals_constant_boundary(*a) for a in [
+        ((9, 7), [(-1, 0), (1, 0), (0, -1), (0, 1)], [0.25] * 4, 1),
+        ((8, 9), [(0, 0), (-2, 1), (1, -2), (0, 2), (2, 0)], [0.3, 0.1, 0.25, -0.15, 0.2], 2)]],
+    pins.test_ghost_sweep_converges_to_the_discrete_dirichlet_solution,
+    pins.test_ghost_sweep_vs_assembled_operator,
+]
+
+
+@pytest.mark.parametrize("name", sorted(GHOST_MUTANTS))
+def test_ghost_pins_catch_planted_mistake(name, monkeypatch):
+    old, new = GHOST_MUTANTS[name]
+    src = open(GHOST_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    ns = {}
+    exec(compile(src.replace(old, new), "ghosts_mutant", "exec"), ns)
+    monkeypatch.setattr(oracle, "sweep_ghosts", ns["sweep_ghosts"])
+    caught = []
+    for fn in GHOST_PINS:
+        try:
+            fn()
+        except Exception as e:
+            caught.append(type(e).__name__)
+    assert caught, f"no pin caught the planted mistake: {name}"
+
+
+def test_unmutated_ghost_sweep_passes_the_same_pins():
+    for fn in GHOST_PINS:
+        fn()
