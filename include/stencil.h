@@ -191,6 +191,29 @@ st_status stencil_set_step_index(st_grid_t g, int64_t t);
 st_status stencil_get_step_index(st_grid_t g, int64_t* t);
 
 /*
+ * Device-resident snapshot and restore of a grid's state, the single-process
+ * form of the paper's rescale checkpoint (Sec. IV "Checkpoint and restart":
+ * GPU data is parked in device memory owned by someone else, a memory daemon
+ * there, and copied back device to device, avoiding the host link).
+ *   stencil_snapshot_bytes: bytes of a snapshot = time_levels whole padded
+ *     buffers (stencil_layout's elems each).
+ *   stencil_snapshot: enqueues device-to-device copies of the newest level
+ *     (then, with two time levels, the previous level) into dst (device,
+ *     caller-owned, 16-byte aligned, >= stencil_snapshot_bytes) on `stream`
+ *     and returns the step counter in *step_out.  The snapshot does not
+ *     depend on the handle: dst may outlive it and its buffers.
+ *   stencil_restore: enqueues the copies back into slot A (newest) and slot B
+ *     (previous, two levels), makes slot A current and sets the step counter;
+ *     the snapshot must come from a grid of the same layout and dtype.  Ghost
+ *     cells owned by the library are rewritten before the next step; with
+ *     ST_FLAG_CALLER_GHOSTS they are the snapshot's.
+ * Both slots must be bound (ST_ERR_STATE otherwise).
+ */
+st_status stencil_snapshot_bytes(st_grid_t g, size_t* bytes);
+st_status stencil_snapshot(st_grid_t g, void* dst, int64_t* step_out, void* stream);
+st_status stencil_restore(st_grid_t g, const void* src, int64_t step, void* stream);
+
+/*
  * Advance nsteps >= 0 steps on `stream`: refresh stale ghosts, then sweep,
  * each launch writing the other slot.  When stencil_tune chose two-step
  * passes (the constant symmetric 7-point star, FP32, no source) a launch

@@ -57,6 +57,9 @@ SIGNATURES = {
     "stencil_set_source": (_I, [_VP, _PI64, _PD, _I64]),
     "stencil_set_step_index": (_I, [_VP, _I64]),
     "stencil_get_step_index": (_I, [_VP, _PI64]),
+    "stencil_snapshot_bytes": (_I, [_VP, _PSZ]),
+    "stencil_snapshot": (_I, [_VP, _VP, _PI64, _VP]),
+    "stencil_restore": (_I, [_VP, _VP, _I64, _VP]),
     "stencil_step": (_I, [_VP, _I, _VP]),
     "stencil_tune": (_I, [_VP, _I, _VP]),
     "stencil_tune_config": (_I, [_VP, _PI]),
@@ -193,6 +196,25 @@ def stencil_get_step_index(h) -> int:
     t = ctypes.c_int64()
     _check(lib().stencil_get_step_index(h, ctypes.byref(t)), "stencil_get_step_index")
     return t.value
+
+
+def stencil_snapshot_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().stencil_snapshot_bytes(h, ctypes.byref(n)), "stencil_snapshot_bytes")
+    return n.value
+
+
+def stencil_snapshot(h, dst_ptr, stream=None) -> int:
+    """Enqueue the snapshot copies into dst_ptr; returns the step counter."""
+    t = ctypes.c_int64()
+    _check(lib().stencil_snapshot(h, ctypes.c_void_p(int(dst_ptr)), ctypes.byref(t),
+                                  ctypes.c_void_p(_stream(stream))), "stencil_snapshot")
+    return t.value
+
+
+def stencil_restore(h, src_ptr, step, stream=None) -> None:
+    _check(lib().stencil_restore(h, ctypes.c_void_p(int(src_ptr)), int(step), ctypes.c_void_p(_stream(stream))),
+           "stencil_restore")
 
 
 def stencil_step(h, nsteps, stream=None) -> None:

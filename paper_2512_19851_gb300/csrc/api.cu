@@ -419,6 +419,54 @@ st_status stencil_get_step_index(st_grid_t g, int64_t* t)
     return ST_OK;
 }
 
+st_status stencil_snapshot_bytes(st_grid_t g, size_t* bytes)
+{
+    if (!g || !bytes) return fail(ST_ERR_ARG, "stencil_snapshot_bytes: NULL argument");
+    *bytes = (size_t)g->levels * (size_t)g->g.elems * g->g.esize;
+    return ST_OK;
+}
+
+// A snapshot is the newest level's whole padded buffer, then (two time
+// levels) the previous level's: device-to-device copies on the caller's
+// stream, so the state never leaves HBM.
+st_status stencil_snapshot(st_grid_t g, void* dst, int64_t* step_out, void* stream)
+{
+    if (!g || !dst || !step_out) return fail(ST_ERR_ARG, "stencil_snapshot: NULL argument");
+    if (((uintptr_t)dst & 15u) != 0) return fail(ST_ERR_ARG, "stencil_snapshot: dst not 16-byte aligned");
+    if (!g->buf[ST_SLOT_A] || !g->buf[ST_SLOT_B])
+        return fail(ST_ERR_STATE, "stencil_snapshot: both time-level slots must be bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last = s;
+    const size_t bytes = (size_t)g->g.elems * g->g.esize;
+    ST_CUDA_TRY(cudaMemcpyAsync(dst, g->buf[g->cur], bytes, cudaMemcpyDeviceToDevice, s));
+    if (g->levels == 2)
+        ST_CUDA_TRY(cudaMemcpyAsync((char*)dst + bytes, g->buf[1 - g->cur], bytes, cudaMemcpyDeviceToDevice, s));
+    *step_out = g->step;
+    return ST_OK;
+}
+
+st_status stencil_restore(st_grid_t g, const void* src, int64_t step, void* stream)
+{
+    if (!g || !src) return fail(ST_ERR_ARG, "stencil_restore: NULL argument");
+    if (((uintptr_t)src & 15u) != 0) return fail(ST_ERR_ARG, "stencil_restore: src not 16-byte aligned");
+    if (step < 0) return fail(ST_ERR_ARG, "stencil_restore: negative step index");
+    if (!g->buf[ST_SLOT_A] || !g->buf[ST_SLOT_B])
+        return fail(ST_ERR_STATE, "stencil_restore: both time-level slots must be bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    g->last = s;
+    const size_t bytes = (size_t)g->g.elems * g->g.esize;
+    ST_CUDA_TRY(cudaMemcpyAsync(g->buf[ST_SLOT_A], src, bytes, cudaMemcpyDeviceToDevice, s));
+    if (g->levels == 2)
+        ST_CUDA_TRY(cudaMemcpyAsync(g->buf[ST_SLOT_B], (const char*)src + bytes, bytes, cudaMemcpyDeviceToDevice,
+                                    s));
+    g->cur = ST_SLOT_A;
+    g->step = step;
+    // the library's ghost values are rewritten before the next step (a
+    // snapshot taken from a handle of another boundary value stays valid)
+    g->stale[ST_SLOT_A] = g->stale[ST_SLOT_B] = true;
+    return ST_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

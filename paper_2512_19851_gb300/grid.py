@@ -91,6 +91,21 @@ class Grid:
     def set_step_index(self, t) -> None:
         abi.stencil_set_step_index(self.h, t)
 
+    # -- snapshot / restore -------------------------------------------------
+    def snapshot(self, stream=None):
+        """Park the state in a new device buffer (device-to-device copies):
+        returns (buffer, step counter).  The buffer belongs to the caller and
+        may outlive this grid."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        buf = torch.empty(abi.stencil_snapshot_bytes(self.h), dtype=torch.uint8, device=self.device)
+        step = abi.stencil_snapshot(self.h, buf.data_ptr(), s)
+        return buf, step
+
+    def restore(self, snap, stream=None) -> None:
+        buf, step = snap
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        abi.stencil_restore(self.h, buf.data_ptr(), step, s)
+
     # -- work --------------------------------------------------------------
     def step(self, nsteps: int, stream=None) -> None:
         s = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -169,3 +169,18 @@ def test_caller_ghosts_choose_kernels_that_read_ghost_cells():
                 alpha=[0.4] + [0.1] * 6, flags=abi.ST_FLAG_CALLER_GHOSTS)
     assert abi.stencil_info(h)[2].startswith("star3d")
     abi.stencil_destroy(h)
+
+
+def test_snapshot_needs_bound_buffers():
+    h = _create()
+    assert abi.stencil_snapshot_bytes(h) == abi.stencil_layout(h, 3)[2] * 4
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_snapshot(h, 16)
+    assert e.value.code == abi.ST_ERR_STATE
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_restore(h, 16, -1)
+    assert e.value.code == abi.ST_ERR_ARG
+    abi.stencil_destroy(h)
+    h = _create(time_levels=2)
+    assert abi.stencil_snapshot_bytes(h) == 2 * abi.stencil_layout(h, 3)[2] * 4
+    abi.stencil_destroy(h)
