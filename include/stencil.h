@@ -82,7 +82,20 @@ typedef enum {
 } st_status;
 
 typedef enum { ST_F32 = 0, ST_F64 = 1 } st_dtype;
-typedef enum { ST_DIRICHLET = 0, ST_PERIODIC = 1 } st_bc;
+/* Boundary rules (the paper's ghost refresh, Sec. III-C, folded into one GPU):
+ *   ST_DIRICHLET  ghost cells hold bc_value (or the caller's values with
+ *                 ST_FLAG_CALLER_GHOSTS) and are never written by a sweep;
+ *   ST_PERIODIC   neighbour indices wrap around each axis;
+ *   ST_NEUMANN    zero flux: before every sweep each ghost cell takes the
+ *                 value of its mirror image across the boundary face (index
+ *                 i < 0 reads -1 - i, i >= n reads 2n - 1 - i, per axis);
+ *                 needs every extent >= radius; constant weights, one time
+ *                 level and single grids only (otherwise stencil_create
+ *                 returns ST_ERR_UNSUPPORTED; the batched form ST_ERR_ARG;
+ *                 stencil_step_ckpt and the adjoint ST_ERR_UNSUPPORTED);
+ *                 2D grids take the one-thread-per-point kernel, 3D grids
+ *                 single sweeps. */
+typedef enum { ST_DIRICHLET = 0, ST_PERIODIC = 1, ST_NEUMANN = 2 } st_bc;
 
 /* stencil_create flags */
 #define ST_FLAG_GENERIC 1u   /* always use the one-thread-per-point kernel (the
@@ -131,7 +144,7 @@ const char* stencil_last_error(void);
  *   alpha       npts doubles (the constant part of each weight).
  *   beta        npts doubles, or NULL for constant weights; non-NULL
  *               requires a coefficient buffer bound at ST_SLOT_COEFF.
- *   bc          ST_DIRICHLET (ghosts = bc_value) or ST_PERIODIC.
+ *   bc          ST_DIRICHLET (ghosts = bc_value), ST_PERIODIC or ST_NEUMANN.
  *   dtype       storage and arithmetic type of the fields.
  *   time_levels 1: form (1); 2: leapfrog form (3).
  *   flags       0 or a combination of ST_FLAG_GENERIC, ST_FLAG_TWO_STEP and

@@ -25,7 +25,9 @@ Functions and the passage each follows:
 * :func:`sweep_ghosts` (in :mod:`oracle.ghosts`) -- the sweep of
   :func:`sweep_const` on a padded array whose Dirichlet ring holds arbitrary
   per-cell values (Example 1's boundary ring set by slice assignment, Sec.
-  III-A), plain numpy.
+  III-A), plain numpy; :func:`sweep_neumann` the same update with a
+  zero-flux boundary (mirror-image ghosts refreshed before every step, the
+  ghost exchange of Sec. III-C on one domain).
 * :func:`taylor_second_derivative_coeffs` (in :mod:`oracle.taylor`) -- the
   8th-order central coefficients from the Taylor conditions.
 
@@ -40,7 +42,7 @@ import sys
 
 import numpy as np
 
-from .ghosts import sweep_ghosts  # noqa: F401
+from .ghosts import sweep_ghosts, sweep_neumann  # noqa: F401
 from .taylor import taylor_second_derivative_coeffs  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

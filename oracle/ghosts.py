@@ -1,5 +1,6 @@
-"""Constant-weight sweep with arbitrary Dirichlet ghost values (part of the
-oracle; TEST INFRASTRUCTURE ONLY, see the package header).
+"""Constant-weight sweeps with arbitrary Dirichlet ghost values and with a
+zero-flux (Neumann) boundary (part of the oracle; TEST INFRASTRUCTURE ONLY,
+see the package header).
 
 Example 1 of Sec. III-A sets the boundary ring of both arrays once by slice
 assignment and never writes it again; the update reads the ring wherever a
@@ -42,12 +43,34 @@ def sweep_ghosts(u_padded, radius: int, offsets, weights, nsteps: int, dtype=np.
     inner = tuple(slice(r, r + m) for m in n)
     tmp = u.copy()
     for _ in range(int(nsteps)):
-        acc = np.zeros(n, dtype=dtype)
-        for o, wk in zip(offs, w):
-            src = tuple(slice(r + c, r + c + m) for c, m in zip(o, n))
-            acc = acc + wk * u[src]
-        tmp[inner] = acc
+        tmp[inner] = _sweep_once(u, r, offs, w, n, dtype)
         u, tmp = tmp, u
         # the ring of the array that now holds the older level is still the
         # initial ring (sweeps write interiors only)
+    return u
+
+
+def _sweep_once(u, r, offs, w, n, dtype):
+    """The new interior from the padded array u (offset order, multiply then add)."""
+    acc = np.zeros(n, dtype=dtype)
+    for o, wk in zip(offs, w):
+        src = tuple(slice(r + c, r + c + m) for c, m in zip(o, n))
+        acc = acc + wk * u[src]
+    return acc
+
+
+def sweep_neumann(u0, offsets, weights, nsteps: int, dtype=np.float64):
+    """Zero-flux (Neumann) boundary: before every sweep the ghost ring of
+    the input is its mirror image across each boundary face (cell-centred
+    reflection: index -1 - i for i < 0, 2n - 1 - i for i >= n, per axis),
+    which numpy's symmetric padding is; then the sweep of sweep_ghosts.
+    Takes and returns the dense interior."""
+    offs = [tuple(int(c) for c in o) for o in offsets]
+    r = max(abs(c) for o in offs for c in o)
+    u = np.array(u0, dtype=dtype, copy=True)
+    if r > min(u.shape):
+        raise ValueError("a mirror image must be interior (extent >= radius)")
+    w = [dtype(x) for x in weights]
+    for _ in range(int(nsteps)):
+        u = _sweep_once(np.pad(u, r, mode="symmetric"), r, offs, w, list(u.shape), dtype)
     return u

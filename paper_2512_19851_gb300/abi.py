@@ -26,7 +26,7 @@ ST_ERR_BOUNDS = -6
 ST_ERR_OOM = -7
 ST_ERR_STATE = -8
 ST_F32, ST_F64 = 0, 1
-ST_DIRICHLET, ST_PERIODIC = 0, 1
+ST_DIRICHLET, ST_PERIODIC, ST_NEUMANN = 0, 1, 2
 ST_FLAG_GENERIC = 1
 ST_FLAG_TWO_STEP = 2
 ST_FLAG_CALLER_GHOSTS = 4

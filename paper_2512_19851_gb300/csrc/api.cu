@@ -154,7 +154,7 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     if (ndim != 2 && ndim != 3) return fail(ST_ERR_ARG, "stencil_create: ndim must be 2 or 3");
     if (!dims || !offsets || !alpha) return fail(ST_ERR_ARG, "stencil_create: NULL dims/offsets/alpha");
     if (npts < 1 || npts > ST_MAX_POINTS) return fail(ST_ERR_ARG, "stencil_create: npts out of range");
-    if (bc != ST_DIRICHLET && bc != ST_PERIODIC) return fail(ST_ERR_ARG, "stencil_create: bad bc");
+    if (bc != ST_DIRICHLET && bc != ST_PERIODIC && bc != ST_NEUMANN) return fail(ST_ERR_ARG, "stencil_create: bad bc");
     if (dtype != ST_F32 && dtype != ST_F64) return fail(ST_ERR_ARG, "stencil_create: bad dtype");
     if (time_levels != 1 && time_levels != 2) return fail(ST_ERR_ARG, "stencil_create: time_levels must be 1 or 2");
     if (flags & ~(ST_FLAG_GENERIC | ST_FLAG_TWO_STEP | ST_FLAG_CALLER_GHOSTS))
@@ -186,6 +186,12 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     }
     if (radius == 0) radius = derived;
     if (radius < derived) return fail(ST_ERR_ARG, "stencil_create: radius smaller than the largest offset");
+    if (bc == ST_NEUMANN && (time_levels != 1 || beta))
+        return fail(ST_ERR_UNSUPPORTED, "stencil_create: ST_NEUMANN with one time level and constant weights only");
+    if (bc == ST_NEUMANN)
+        for (int i = 0; i < ndim; ++i)
+            if (dims[i] < radius)
+                return fail(ST_ERR_ARG, "stencil_create: a Neumann ghost's mirror image must be interior (extent >= radius)");
     if (bc == ST_DIRICHLET) {
         // the paper's limitation (Sec. III-D): dependence distance within the domain
         for (int i = 0; i < ndim; ++i)
@@ -213,7 +219,7 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     g->caller_ghosts = (flags & ST_FLAG_CALLER_GHOSTS) != 0;
     // the two-step 3D pass substitutes bc_value for ghost reads, so caller
     // ghosts keep single sweeps
-    g->pairs = (flags & ST_FLAG_TWO_STEP) != 0 && !g->caller_ghosts;
+    g->pairs = (flags & ST_FLAG_TWO_STEP) != 0 && !g->caller_ghosts && bc != ST_NEUMANN;
     FamilyDesc d{};
     d.g = g->g;
     d.npts = npts;
@@ -226,7 +232,7 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     d.star = is_star(g->off, npts, ndim);
     d.force_generic = (flags & ST_FLAG_GENERIC) != 0;
     g->fam = select_family(d);
-    if (g->fam.kind == FAM_2D_TILE && g->caller_ghosts) {
+    if (g->fam.kind == FAM_2D_TILE && (g->caller_ghosts || bc == ST_NEUMANN)) {
         // the persistent 2D tile kernel substitutes bc_value for points
         // outside the interior; the one-thread-per-point kernel reads the
         // ghost cells themselves
@@ -513,7 +519,7 @@ static st_status check_ready(st_grid_t g, const char* who)
 // term needs its step index per sweep, so it keeps single sweeps.
 static bool use_pairs(st_grid_t g)
 {
-    return g->pairs && !g->caller_ghosts && g->src < 0 && star3d_pair_supported(g->fam);
+    return g->pairs && !g->caller_ghosts && g->bc != ST_NEUMANN && g->src < 0 && star3d_pair_supported(g->fam);
 }
 
 // Slot of the newest level after n steps from slot `cur`: every launch (one
@@ -534,6 +540,9 @@ static st_status enqueue_steps(st_grid_t g, int cur, int64_t step0, int n, cudaS
             ST_CUDA_TRY(launch_star3d_pair(g->fam, a, g->bc_value, s));
             i += 2;
         } else {
+            // zero-flux boundary: the input's ghosts mirror its interior
+            // before every sweep (the device-local ghost exchange)
+            if (g->bc == ST_NEUMANN) ST_CUDA_TRY(launch_mirror_ghosts(g->g.esize, g->buf[cur], g->g, s));
             ST_CUDA_TRY(launch_family(g->fam, a, s));
             i += 1;
         }
@@ -630,7 +639,7 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
     rc = refresh_ghosts(g, s);
     if (rc != ST_OK) return rc;
     if ((!g->plan || !g->plan_bound) && g->levels == 1 && g->src < 0 && !g->caller_ghosts &&
-        star3d_pair_supported(g->fam)) {
+        g->bc != ST_NEUMANN && star3d_pair_supported(g->fam)) {
         // single sweeps or two-step passes: time both on the bound data, keep
         // the faster, and put the current level back
         const size_t bytes = (size_t)g->g.elems * g->g.esize;
@@ -828,6 +837,7 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stre
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_step_ckpt: nsteps >= 0, ckpt_every >= 1");
     if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_step_ckpt: one time level only");
     if (g->caller_ghosts) return fail(ST_ERR_UNSUPPORTED, "stencil_step_ckpt: not with ST_FLAG_CALLER_GHOSTS");
+    if (g->bc == ST_NEUMANN) return fail(ST_ERR_UNSUPPORTED, "stencil_step_ckpt: not with ST_NEUMANN");
     if (((uintptr_t)ws & 15u) != 0) return fail(ST_ERR_ARG, "stencil_step_ckpt: workspace not 16-byte aligned");
     st_status rc = check_ready(g, "stencil_step_ckpt");
     if (rc != ST_OK) return rc;
@@ -874,6 +884,7 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_adjoint: nsteps >= 0, ckpt_every >= 1");
     if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: one time level only");
     if (g->caller_ghosts) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: not with ST_FLAG_CALLER_GHOSTS");
+    if (g->bc == ST_NEUMANN) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: not with ST_NEUMANN");
     if (lambda == lambda_tmp) return fail(ST_ERR_ALIAS, "stencil_adjoint: lambda and lambda_tmp alias");
     if ((((uintptr_t)ws) | ((uintptr_t)lambda) | ((uintptr_t)lambda_tmp) | ((uintptr_t)grad)) & 15u)
         return fail(ST_ERR_ARG, "stencil_adjoint: buffers must be 16-byte aligned");

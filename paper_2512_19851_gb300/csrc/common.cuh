@@ -69,6 +69,7 @@ cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_i
                                    const void* kappa, double* gk, const GenParams& P,
                                    cudaStream_t s);
 cudaError_t launch_fill_ghosts(int esize, void* buf, const Geom& g, double value, cudaStream_t s);
+cudaError_t launch_mirror_ghosts(int esize, void* buf, const Geom& g, cudaStream_t s);
 cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int dir, cudaStream_t s);
 cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g, double* partials,
                           int nblocks, double* out, int mode, void* lam_out, cudaStream_t s);

@@ -125,6 +125,52 @@ __global__ void __launch_bounds__(256) k_fill_ghosts(T* __restrict__ buf, Geom g
     }
 }
 
+// Zero-flux (Neumann) boundary: every ghost cell within the ghost width takes
+// the value of its mirror image across the boundary face, axis by axis
+// (interior index i < 0 reads -1 - i, i >= n reads 2n - 1 - i).  Mirror images
+// are interior cells, which this kernel never writes, so the order of the
+// writes does not matter.  The same shell walk as k_fill_ghosts; padding
+// columns beyond the ghost width are left alone.
+__device__ __forceinline__ int64_t mirror(int64_t i, int64_t n) { return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mirror_ghosts(T* __restrict__ buf, Geom g)
+{
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t zrows = 2 * g.rz * g.pny;
+    const int64_t yrows = g.nz * 2 * g.r;
+    const int64_t w = g.nx + 2 * g.r;        // columns [xl - r, xl + nx + r)
+    const int64_t full = (zrows + yrows) * w;
+    auto src = [&](int64_t pz, int64_t py, int64_t x) {
+        const int64_t zi = mirror(pz - g.rz, g.nz), yi = mirror(py - g.r, g.ny), xi = mirror(x - g.xl, g.nx);
+        return buf[(g.rz + zi) * g.plane + (g.r + yi) * g.pitch + g.xl + xi];
+    };
+    for (int64_t i = tid; i < full; i += nthr) {
+        const int64_t row = i / w, x = g.xl - g.r + (i - row * w);
+        int64_t pz, py;
+        if (row < zrows) {
+            const int64_t zp = row / g.pny;
+            py = row - zp * g.pny;
+            pz = zp < g.rz ? zp : zp + g.nz;
+        } else {
+            const int64_t k = row - zrows;
+            const int64_t zi = k / (2 * g.r), yk = k - zi * 2 * g.r;
+            pz = g.rz + zi;
+            py = yk < g.r ? yk : yk + g.ny;
+        }
+        buf[pz * g.plane + py * g.pitch + x] = src(pz, py, x);
+    }
+    const int64_t side = 2 * g.r;  // ghost columns of an interior row
+    const int64_t nside = g.nz * g.ny * side;
+    for (int64_t i = tid; i < nside; i += nthr) {
+        const int64_t row = i / side, c = i - row * side;
+        const int64_t zi = row / g.ny, yi = row - zi * g.ny;
+        const int64_t x = c < g.r ? g.xl - g.r + c : g.xl + g.nx + (c - g.r);
+        buf[(g.rz + zi) * g.plane + (g.r + yi) * g.pitch + x] = src(g.rz + zi, g.r + yi, x);
+    }
+}
+
 // Deterministic block reduction of (sum, sum of squares, max) in double.
 struct Red3 {
     double s, q, m;
@@ -445,6 +491,18 @@ cudaError_t launch_fill_ghosts(int esize, void* buf, const Geom& g, double value
         k_fill_ghosts<double><<<blocks, 256, 0, s>>>((double*)buf, g, value);
     else
         k_fill_ghosts<float><<<blocks, 256, 0, s>>>((float*)buf, g, (float)value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_ghosts(int esize, void* buf, const Geom& g, cudaStream_t s)
+{
+    const int64_t cells = (2 * g.rz * g.pny + g.nz * 2 * g.r) * (g.nx + 2 * g.r) + g.nz * g.ny * 2 * g.r;
+    const int64_t want = (cells + 255) / 256;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
+    if (esize == 8)
+        k_mirror_ghosts<double><<<blocks, 256, 0, s>>>((double*)buf, g);
+    else
+        k_mirror_ghosts<float><<<blocks, 256, 0, s>>>((float*)buf, g);
     return cudaGetLastError();
 }
 

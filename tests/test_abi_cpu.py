@@ -184,3 +184,23 @@ def test_snapshot_needs_bound_buffers():
     h = _create(time_levels=2)
     assert abi.stencil_snapshot_bytes(h) == 2 * abi.stencil_layout(h, 3)[2] * 4
     abi.stencil_destroy(h)
+
+
+def test_neumann_arguments():
+    star = [(0, 0, 0), (0, 0, 1), (0, 0, -1), (0, 1, 0), (0, -1, 0), (1, 0, 0), (-1, 0, 0)]
+    h = _create(bc=abi.ST_NEUMANN, offsets=star, alpha=[0.4] + [0.1] * 6)
+    assert abi.stencil_info(h)[2].startswith("star3d")
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_step_ckpt(h, 2, 1, 16)
+    assert e.value.code == abi.ST_ERR_UNSUPPORTED
+    abi.stencil_destroy(h)
+    with pytest.raises(abi.StencilError) as e:       # mirror image outside the interior
+        _create(bc=abi.ST_NEUMANN, dims=(8, 1, 10), offsets=[(0, 0, 0), (0, 2, 0)], alpha=[0.5, 0.5])
+    assert e.value.code == abi.ST_ERR_ARG
+    with pytest.raises(abi.StencilError) as e:
+        _create(bc=abi.ST_NEUMANN, time_levels=2)
+    assert e.value.code == abi.ST_ERR_UNSUPPORTED
+    h = abi.stencil_create(2, (64, 64), 0, [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)], [0.2] * 5,
+                           bc=abi.ST_NEUMANN, dtype=abi.ST_F32)
+    assert abi.stencil_info(h)[2] == "generic_point"
+    abi.stencil_destroy(h)

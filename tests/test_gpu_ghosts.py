@@ -107,3 +107,46 @@ def test_caller_ghost_errors():
         abi.stencil_step_ckpt(g.h, 2, 1, ws.data_ptr())
     assert e.value.code == abi.ST_ERR_UNSUPPORTED
     g.close()
+
+
+# ---------------------------------------------------------------- zero-flux (Neumann) boundary
+def run_neumann(u0, offsets, weights, dtype, chunks):
+    g = Grid(u0.shape, offsets, weights, dtype=dtype, neumann=True)
+    g.set_field(u0)
+    for n in chunks:
+        g.step(n)
+    g.sync()
+    out = g.current().double().cpu().numpy()
+    kern = g.kernel
+    g.close()
+    return out, kern
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape,stencil", [
+    ((70, 45), (inputs.OFFSETS_5PT, [0.2] * 5)),
+    ((37, 61), ASYM2),
+    ((20, 36, 52), (inputs.OFFSETS_7PT, [0.4] + [0.1] * 6)),
+    ((9, 17, 131), (inputs.OFFSETS_7PT, [0.4] + [0.1] * 6)),
+])
+def test_neumann_matches_oracle(dtype, shape, stencil):
+    """Mirror-image ghosts refreshed before every sweep; 21 steps split 8 + 13."""
+    rng = np.random.default_rng(33)
+    u0 = rng.random(shape)
+    offs, w = stencil
+    ref = oracle.sweep_neumann(u0, offs, w, 21)
+    got, kern = run_neumann(u0, offs, w, dtype, [8, 13])
+    assert rel_err(got, ref) <= TOL[dtype], kern
+
+
+def test_neumann_conserves_heat_at_size():
+    """Zero flux: 100 FP64 sweeps of the 7-point heat step on 128 x 192 x 256
+    keep sum(u) to rounding, and a cosine mode decays by its eigenvalue."""
+    shape, k, a = (128, 192, 256), (2, 3, 5), 0.1
+    grids = np.meshgrid(*[np.arange(n) + 0.5 for n in shape], indexing="ij")
+    u0 = 1.0 + np.prod([np.cos(np.pi * kk * gg / n) for kk, gg, n in zip(k, grids, shape)], axis=0)
+    del grids
+    lam = 1 - 4 * a * sum(np.sin(np.pi * kk / (2 * n)) ** 2 for kk, n in zip(k, shape))
+    got, kern = run_neumann(u0, inputs.OFFSETS_7PT, [1 - 6 * a] + [a] * 6, torch.float64, [100])
+    assert abs(got.sum() - u0.sum()) <= 1e-12 * u0.sum(), kern
+    assert np.max(np.abs(got - (1.0 + lam ** 100 * (u0 - 1.0)))) <= 1e-12, kern

@@ -114,7 +114,7 @@ def test_unmutated_oracle_passes_the_same_pins():
         fn()
 
 
-# ------------------------------------------------ the numpy ghost-ring sweep
+# ------------------------------------------------ the numpy ghost-ring and Neumann sweeps
 GHOST_SRC = os.path.join(os.path.dirname(oracle.__file__), "ghosts.py")
 
 GHOST_MUTANTS = {
@@ -122,7 +122,10 @@ GHOST_MUTANTS = {
     "ghost sweep reads the offset with the wrong sign": ("slice(r + c, r + c + m)", "slice(r - c, r - c + m)"),
     "ghost sweep transposes the offset axes": ("for c, m in zip(o, n))", "for c, m in zip(o[::-1], n))"),
     "ghost sweep never swaps the arrays": ("u, tmp = tmp, u", "tmp = tmp"),
-    "ghost sweep reads the output array": ("acc = acc + wk * u[src]", "acc = acc + wk * tmp[src]"),
+    "ghost sweep reads the output array": ("tmp[inner] = _sweep_once(u,", "tmp[inner] = _sweep_once(tmp,"),
+    "Neumann mirror skips the edge cell (reflect)": ('mode="symmetric"', 'mode="reflect"'),
+    "Neumann ghosts wrap around (periodic)": ('mode="symmetric"', 'mode="wrap"'),
+    "Neumann ghosts held at zero (Dirichlet)": ('mode="symmetric"', 'mode="constant"'),
 }
 
 GHOST_PINS = [
@@ -131,6 +134,9 @@ GHOST_PINS = [
         ((8, 9), [(0, 0), (-2, 1), (1, -2), (0, 2), (2, 0)], [0.3, 0.1, 0.25, -0.15, 0.2], 2)]],
     pins.test_ghost_sweep_converges_to_the_discrete_dirichlet_solution,
     pins.test_ghost_sweep_vs_assembled_operator,
+    lambda: pins.test_neumann_cosine_mode_decay((12, 9), (3, 2), 0.2, 15),
+    pins.test_neumann_conserves_the_sum_and_constants,
+    pins.test_neumann_vs_assembled_operator,
 ]
 
 
@@ -142,6 +148,7 @@ def test_ghost_pins_catch_planted_mistake(name, monkeypatch):
     ns = {}
     exec(compile(src.replace(old, new), "ghosts_mutant", "exec"), ns)
     monkeypatch.setattr(oracle, "sweep_ghosts", ns["sweep_ghosts"])
+    monkeypatch.setattr(oracle, "sweep_neumann", ns["sweep_neumann"])
     caught = []
     for fn in GHOST_PINS:
         try:

@@ -530,3 +530,64 @@ def test_ghost_sweep_vs_assembled_operator():
     got = oracle.sweep_ghosts(u, r, offsets, weights, 3)
     assert np.max(np.abs(got[r:-r, r:-r].reshape(-1) - x)) <= 1e-14
     assert np.array_equal(got[:r], u[:r]) and np.array_equal(got[:, -r:], u[:, -r:])
+
+
+# ---------------------------------------------------------------- zero-flux (Neumann) boundary
+def _mirror(i, n):
+    return -1 - i if i < 0 else (2 * n - 1 - i if i >= n else i)
+
+
+@pytest.mark.parametrize("shape,k,a,steps", [((12, 9), (3, 2), 0.2, 15), ((7, 10), (0, 4), 0.15, 30)])
+def test_neumann_cosine_mode_decay(shape, k, a, steps):
+    """cos(pi k (i + 1/2) / n) per axis is an eigenvector of the 5-point
+    operator with mirror-image ghosts; eigenvalue
+    1 - 4a (sin^2(pi ky / (2 ny)) + sin^2(pi kx / (2 nx)))."""
+    ny, nx = shape
+    y = (np.arange(ny) + 0.5)[:, None]
+    x = (np.arange(nx) + 0.5)[None, :]
+    u0 = np.cos(np.pi * k[0] * y / ny) * np.cos(np.pi * k[1] * x / nx)
+    lam = 1 - 4 * a * (np.sin(np.pi * k[0] / (2 * ny)) ** 2 + np.sin(np.pi * k[1] / (2 * nx)) ** 2)
+    got = oracle.sweep_neumann(u0, inputs.OFFSETS_5PT, [1 - 4 * a] + [a] * 4, steps)
+    assert np.max(np.abs(got - lam ** steps * u0)) <= 1e-13
+
+
+def test_neumann_3d_cosine_mode_decay():
+    shape, k, a, steps = (6, 9, 11), (1, 3, 5), 0.1, 12
+    grids = np.meshgrid(*[np.arange(n) + 0.5 for n in shape], indexing="ij")
+    u0 = np.prod([np.cos(np.pi * kk * g / n) for kk, g, n in zip(k, grids, shape)], axis=0)
+    lam = 1 - 4 * a * sum(np.sin(np.pi * kk / (2 * n)) ** 2 for kk, n in zip(k, shape))
+    got = oracle.sweep_neumann(u0, inputs.OFFSETS_7PT, [1 - 6 * a] + [a] * 6, steps)
+    assert np.max(np.abs(got - lam ** steps * u0)) <= 1e-13
+
+
+def test_neumann_conserves_the_sum_and_constants():
+    """Zero flux through the boundary: symmetric weights summing to 1 keep
+    sum(u); a constant field stays constant."""
+    rng = np.random.default_rng(23)
+    u0 = rng.random((9, 14, 11))
+    got = oracle.sweep_neumann(u0, inputs.OFFSETS_7PT, [0.4] + [0.1] * 6, 40)
+    assert abs(got.sum() - u0.sum()) <= 1e-12 * u0.sum()
+    c = oracle.sweep_neumann(np.full((5, 8), 0.3), inputs.OFFSETS_5PT, [0.2] * 5, 25)
+    assert np.max(np.abs(c - 0.3)) <= 1e-15
+
+
+def test_neumann_vs_assembled_operator():
+    """Brute force with asymmetric radius-2 offsets: the matrix assembled
+    point by point with mirrored neighbour indices."""
+    rng = np.random.default_rng(24)
+    shape = (5, 6)
+    offsets = [(0, 0), (-2, 1), (1, -2), (0, 2), (2, 0), (-1, -1)]
+    weights = [0.3, 0.1, 0.25, -0.15, 0.2, 0.05]
+    n = shape[0] * shape[1]
+    A = np.zeros((n, n))
+    for p in np.ndindex(*shape):
+        ip = np.ravel_multi_index(p, shape)
+        for o, w in zip(offsets, weights):
+            q = (_mirror(p[0] + o[0], shape[0]), _mirror(p[1] + o[1], shape[1]))
+            A[ip, np.ravel_multi_index(q, shape)] += w
+    u0 = rng.random(shape)
+    x = u0.reshape(-1)
+    for _ in range(4):
+        x = A @ x
+    got = oracle.sweep_neumann(u0, offsets, weights, 4)
+    assert np.max(np.abs(got.reshape(-1) - x)) <= 1e-14
