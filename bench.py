@@ -396,6 +396,37 @@ def extra_configs(dev, hbm_peak):
     g.close()
     del p
     torch.cuda.empty_cache()
+    # the same diffusion in conservative face-averaged form (one thread per
+    # point), 256^3 FP32, 200 steps, checkpoint every 20
+    v = inputs.varcoef3d(n=256)
+    g = Grid((256,) * 3, None, None, dtype=torch.float32, device=dev, conservative=True)
+    p = VarCoefProblem(g, 200, 20)
+    g.set_field(v.u0)
+    g.set_coeff(v.kappa)
+    t_fwd = _time(lambda: abi.stencil_step(g.h, 200, s), 3, s)
+    tgt = g.new_field()
+    g.interior(tgt).copy_(torch.as_tensor(v.target, dtype=torch.float32))
+    del v
+
+    def fwd_ckpt_c():
+        abi.stencil_set_current(g.h, 0)
+        abi.stencil_step_ckpt(g.h, 200, 20, p.ws.data_ptr(), s)
+
+    def adj_c():
+        cur = g.bufs[g.current_slot()]
+        abi.stencil_residual(g.h, cur.data_ptr(), tgt.data_ptr(), p.lam.data_ptr(), p.loss.data_ptr(), s)
+        abi.stencil_adjoint(g.h, 200, 20, p.ws.data_ptr(), p.lam.data_ptr(), p.lam_tmp.data_ptr(),
+                            p.gk.data_ptr(), s)
+
+    fwd_ckpt_c()
+    t_adj = _time(adj_c, 2, s)
+    out["conservative3d_f32"] = {"fwd_glups": n4 * 200 / t_fwd / 1e9, "fwd_us_per_step": t_fwd / 200 * 1e6,
+                                 "fwd_hbm_frac": 12 * n4 / (t_fwd / 200) / 1e9 / hbm_peak,
+                                 "adj_us_per_step": t_adj / 200 * 1e6, "adj_over_fwd": t_adj / t_fwd,
+                                 "ckpt_every": 20, "kernel": g.kernel}
+    g.close()
+    del p
+    torch.cuda.empty_cache()
     # batched 512 grids, FP32, 50 steps
     b = inputs.batch2d()
     bt = Batch(b.shapes, inputs.OFFSETS_BOX9, b.weights, periodic=True, dtype=torch.float32, device=dev)
@@ -619,6 +650,22 @@ def run_profile(case: str, launches: int = 3):
             p = VarCoefProblem(g, 2 + launches, 2 + launches)
             p.forward(v.u0, v.kappa)
             p.backward_from(target=v.target)
+    elif case in ("cons_fwd", "cons_adj"):
+        # the conservative face-averaged operator, 256 x 512 x 512 FP32
+        shape = (256, 512, 512)
+        rng = np.random.default_rng(3)
+        u0 = rng.random(shape, dtype=np.float32)
+        kappa = np.clip(0.05 * np.exp(0.5 * rng.standard_normal(shape, dtype=np.float32)), 0, 0.16)
+        g = Grid(shape, None, None, dtype=torch.float32, conservative=True)
+        g.set_field(u0)
+        g.set_coeff(kappa)
+        if case == "cons_fwd":
+            for _ in range(2 + launches):
+                abi.stencil_step(g.h, 1, s)
+        else:
+            p = VarCoefProblem(g, 2 + launches, 2 + launches)
+            p.forward(u0, kappa)
+            p.backward_from(target=u0)
     elif case == "batch":
         from paper_2512_19851_gb300.grid import Batch
         b = inputs.batch2d()
@@ -640,7 +687,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--headline-only", action="store_true")
-    ap.add_argument("--profile", default=None, help="run one small case for ncu (heat3d_f32, heat3d_f32_512, heat3d_f64, laplace2d_f64, wave, "
+    ap.add_argument("--profile", default=None, help="run one small case for ncu (heat3d_f32, heat3d_f32_512, heat3d_f64, laplace2d_f64, cons_fwd, cons_adj, wave, "
                                                       "varcoef_fwd, varcoef_adj) and exit")
     args = ap.parse_args()
     if args.profile:

@@ -156,6 +156,24 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
                          st_bc bc, double bc_value, st_dtype dtype, int time_levels,
                          uint32_t flags);
 
+/*
+ * Create a grid handle for per-cell diffusion in conservative (face-averaged)
+ * form, the variable-coefficient operator of (1)-(2) written with face
+ * coefficients so that a periodic grid conserves sum(u) whatever kappa is:
+ *     u_{t+1}[p] = u_t[p] + sum over the 2*ndim axis neighbours q of p of
+ *                  k_pq (u_t[q] - u_t[p]),
+ *     k_pq = (kappa[p] + kappa[q]) / 2 for an interior (or wrapped) q,
+ *     k_pq = kappa[p] for a Dirichlet ghost q (u_t[q] = bc_value).
+ * Radius 1; the coefficient field is bound at ST_SLOT_COEFF.  Everything
+ * else (bind, step, stencil_step_ckpt, stencil_adjoint, run_host, reductions)
+ * works as for a stencil_create handle; the adjoint's gradient is dL/dkappa
+ * of this operator (its matrix is symmetric, so a transposed step is the
+ * same sweep on lambda).  One thread per point.  bc: ST_DIRICHLET or
+ * ST_PERIODIC (ST_ERR_ARG otherwise); flags must be 0.
+ */
+st_status stencil_create_conservative(st_grid_t* out, int ndim, const int64_t* dims, st_bc bc, double bc_value,
+                                      st_dtype dtype, uint32_t flags);
+
 /* Release the handle and its scratch (not the borrowed buffers).  NULL is a no-op. */
 st_status stencil_destroy(st_grid_t g);
 

@@ -28,6 +28,10 @@ Functions and the passage each follows:
   III-A), plain numpy; :func:`sweep_neumann` the same update with a
   zero-flux boundary (mirror-image ghosts refreshed before every step, the
   ghost exchange of Sec. III-C on one domain).
+* :func:`cons_forward`, :func:`cons_transpose`, :func:`cons_loss_gradient`
+  (in :mod:`oracle.conservative`) -- the per-cell diffusion in conservative
+  face-averaged form, its transpose and the coefficient gradient, plain
+  numpy (forward by gather, transpose and gradient by scatter).
 * :func:`taylor_second_derivative_coeffs` (in :mod:`oracle.taylor`) -- the
   8th-order central coefficients from the Taylor conditions.
 
@@ -42,6 +46,7 @@ import sys
 
 import numpy as np
 
+from .conservative import cons_forward, cons_loss_gradient, cons_step, cons_transpose  # noqa: F401
 from .ghosts import sweep_ghosts, sweep_neumann  # noqa: F401
 from .taylor import taylor_second_derivative_coeffs  # noqa: F401
 

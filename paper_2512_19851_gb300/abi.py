@@ -47,6 +47,7 @@ SIGNATURES = {
     "stencil_version": (_CP, []),
     "stencil_last_error": (_CP, []),
     "stencil_create": (_I, [_PVP, _I, _PI64, _I, _I, _PI32, _PD, _PD, _I, _D, _I, _I, _U32]),
+    "stencil_create_conservative": (_I, [_PVP, _I, _PI64, _I, _D, _I, _U32]),
     "stencil_destroy": (_I, [_VP]),
     "stencil_layout": (_I, [_VP, _PI64, _PI64, _PI64]),
     "stencil_info": (_I, [_VP, _PI, _PI, ctypes.POINTER(_CP)]),
@@ -142,6 +143,15 @@ def stencil_create(ndim, dims, radius, offsets, alpha, beta=None, bc=ST_DIRICHLE
     o = _arr([int(v) for v in off], ctypes.c_int32)
     _check(lib().stencil_create(ctypes.byref(h), int(ndim), d, int(radius), int(npts), o, a, b, int(bc),
                                 float(bc_value), int(dtype), int(time_levels), int(flags)), "stencil_create")
+    return h.value
+
+
+def stencil_create_conservative(ndim, dims, bc=ST_DIRICHLET, bc_value=0.0, dtype=ST_F64, flags=0):
+    """Handle of the conservative face-averaged per-cell diffusion (opaque int)."""
+    h = ctypes.c_void_p()
+    d = _arr([int(v) for v in dims], ctypes.c_int64)
+    _check(lib().stencil_create_conservative(ctypes.byref(h), int(ndim), d, int(bc), float(bc_value), int(dtype),
+                                             int(flags)), "stencil_create_conservative")
     return h.value
 
 

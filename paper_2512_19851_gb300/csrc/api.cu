@@ -263,6 +263,37 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     return ST_OK;
 }
 
+st_status stencil_create_conservative(st_grid_t* out, int ndim, const int64_t* dims, st_bc bc, double bc_value,
+                                      st_dtype dtype, uint32_t flags)
+{
+    if (!out) return fail(ST_ERR_ARG, "stencil_create_conservative: out is NULL");
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return fail(ST_ERR_ARG, "stencil_create_conservative: ndim must be 2 or 3");
+    if (bc != ST_DIRICHLET && bc != ST_PERIODIC)
+        return fail(ST_ERR_ARG, "stencil_create_conservative: Dirichlet or periodic boundary");
+    if (flags != 0) return fail(ST_ERR_ARG, "stencil_create_conservative: no flags are defined");
+    // centre, then -z, +z, -y, +y, -x, +x (2D: -y, +y, -x, +x); the weights
+    // of the non-conservative form w = 1 - 2 ndim kappa, kappa only mark the
+    // operator as per-cell (the conservative kernel builds its own)
+    int32_t off[7 * 3] = {};
+    double alpha[7] = {}, beta[7] = {};
+    int n = 1;
+    alpha[0] = 1.0;
+    beta[0] = -2.0 * ndim;
+    for (int ax = 0; ax < ndim; ++ax)
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            off[n * ndim + ax] = sgn;
+            beta[n] = 1.0;
+            ++n;
+        }
+    st_status rc = stencil_create(out, ndim, dims, 1, n, off, alpha, beta, bc, bc_value, dtype, 1, ST_FLAG_GENERIC);
+    if (rc != ST_OK) return rc;
+    st_grid_t g = *out;
+    g->fam.kind = FAM_CONS;
+    g->fam.name = "cons_face_avg_point";
+    return ST_OK;
+}
+
 st_status stencil_destroy(st_grid_t g)
 {
     if (!g) return ST_OK;

@@ -87,6 +87,8 @@ cudaError_t launch_family(const Family& f, const SweepArgs& a, cudaStream_t s)
         return launch_tile2d(f, a, s);
     case FAM_WAVE:
         return launch_wave(f, a, s);
+    case FAM_CONS:
+        return launch_cons_sweep(f, a, s);
     default: {
         GenParams P = f.gp;
         P.src = a.src;
@@ -100,6 +102,7 @@ cudaError_t launch_family(const Family& f, const SweepArgs& a, cudaStream_t s)
 
 cudaError_t launch_family_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s)
 {
+    if (f.kind == FAM_CONS) return launch_cons_adjoint(f, a, s);
     if (f.kind == FAM_STAR3D && star3d_adjoint_fuse(f) >= a.steps) return launch_star3d_adjoint(f, a, s);
     if (a.steps != 1) return cudaErrorInvalidValue;  // callers fuse only what the family supports
     return launch_generic_adjoint(f.g.esize, a.u, a.lam_in, a.lam_out, a.kappa, a.gk, f.gp, s);

@@ -13,6 +13,7 @@ enum FamilyKind {
     FAM_STAR3D = 1,     // 3D star, z-streaming with bulk-copy staged planes (k_star3d.cu)
     FAM_2D_TILE = 2,    // 2D tile kernel (k_2d.cu)
     FAM_WAVE = 3,       // 3D radius-4 leapfrog star (k_wave.cu)
+    FAM_CONS = 4,       // conservative face-averaged per-cell diffusion, one thread per point (k_cons.cu)
 };
 
 struct FamilyDesc {
@@ -89,6 +90,8 @@ cudaError_t launch_tile2d(const Family& f, const SweepArgs& a, cudaStream_t s);
 bool wave_supports(const FamilyDesc& d);
 cudaError_t launch_wave(const Family& f, const SweepArgs& a, cudaStream_t s);
 bool tile2d_supports(const FamilyDesc& d, int* variant, const char** name);
+cudaError_t launch_cons_sweep(const Family& f, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_cons_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Batched plan (k_batch.cu)

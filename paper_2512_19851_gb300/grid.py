@@ -26,18 +26,24 @@ class Grid:
 
     def __init__(self, shape, offsets, alpha, beta=None, periodic=False, bc_value=0.0, dtype=torch.float64,
                  time_levels=1, radius=0, generic=False, device=None, two_step=False, caller_ghosts=False,
-                 neumann=False):
+                 neumann=False, conservative=False):
+        """conservative=True: the face-averaged per-cell diffusion of
+        stencil_create_conservative (offsets, alpha and beta are ignored)."""
         self.shape = tuple(int(s) for s in shape)
         self.ndim = len(self.shape)
         self.dtype = dtype
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.periodic = bool(periodic)
         bc = ST_PERIODIC if periodic else (abi.ST_NEUMANN if neumann else ST_DIRICHLET)
-        self.h = abi.stencil_create(self.ndim, self.shape, radius, offsets, alpha, beta,
-                                    bc, bc_value, _ST_DTYPE[dtype],
-                                    time_levels, (ST_FLAG_GENERIC if generic else 0) |
-                                    (abi.ST_FLAG_TWO_STEP if two_step else 0) |
-                                    (abi.ST_FLAG_CALLER_GHOSTS if caller_ghosts else 0))
+        if conservative:
+            self.h = abi.stencil_create_conservative(self.ndim, self.shape, bc, bc_value, _ST_DTYPE[dtype])
+            beta = True
+        else:
+            self.h = abi.stencil_create(self.ndim, self.shape, radius, offsets, alpha, beta,
+                                        bc, bc_value, _ST_DTYPE[dtype],
+                                        time_levels, (ST_FLAG_GENERIC if generic else 0) |
+                                        (abi.ST_FLAG_TWO_STEP if two_step else 0) |
+                                        (abi.ST_FLAG_CALLER_GHOSTS if caller_ghosts else 0))
         self.padded, self.origin, self.elems = abi.stencil_layout(self.h, self.ndim)
         self.radius, self.npts, self.kernel = abi.stencil_info(self.h)
         self.bufs = [torch.zeros(self.padded, dtype=dtype, device=self.device) for _ in range(2)]

@@ -204,3 +204,19 @@ def test_neumann_arguments():
                            bc=abi.ST_NEUMANN, dtype=abi.ST_F32)
     assert abi.stencil_info(h)[2] == "generic_point"
     abi.stencil_destroy(h)
+
+
+def test_conservative_create():
+    h = abi.stencil_create_conservative(3, (8, 9, 10), abi.ST_PERIODIC, 0.0, abi.ST_F64)
+    r, n, name = abi.stencil_info(h)
+    assert (r, n, name) == (1, 7, "cons_face_avg_point")
+    abi.stencil_destroy(h)
+    h = abi.stencil_create_conservative(2, (8, 9), abi.ST_DIRICHLET, 0.5, abi.ST_F32)
+    assert abi.stencil_info(h)[1] == 5
+    abi.stencil_destroy(h)
+    for kw in (dict(ndim=4, dims=(2, 2, 2, 2)), dict(bc=abi.ST_NEUMANN), dict(flags=1)):
+        args = dict(ndim=3, dims=(8, 9, 10), bc=abi.ST_DIRICHLET, bc_value=0.0, dtype=abi.ST_F64, flags=0)
+        args.update(kw)
+        with pytest.raises(abi.StencilError) as e:
+            abi.stencil_create_conservative(**args)
+        assert e.value.code == abi.ST_ERR_ARG

@@ -1,0 +1,100 @@
+"""GPU parity of the conservative (face-averaged) per-cell diffusion
+(stencil_create_conservative), its transpose and the coefficient gradient,
+against the numpy oracle (oracle/conservative.py).
+
+Tolerances as for the affine per-cell operator: FP64 <= 1e-12 normwise;
+FP32 forward and lambda <= 1e-5, FP32 gradient <= 1e-3 (the gradient sums
+products of differences of a smoothed field, which cancel most digits).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import rel_err, require_cuda, torch
+from paper_2512_19851_gb300 import inputs
+from paper_2512_19851_gb300.grid import Grid, VarCoefProblem
+
+pytestmark = pytest.mark.gpu
+
+
+def setup_module(_):
+    require_cuda()
+
+
+def make(shape, dtype, periodic, bc):
+    return Grid(shape, None, None, periodic=periodic, bc_value=bc, dtype=dtype, conservative=True)
+
+
+def fields(shape, seed):
+    rng = np.random.default_rng(seed)
+    u0 = rng.random(shape)
+    kappa = np.clip(0.05 * np.exp(0.5 * rng.standard_normal(shape)), 0.0, 0.16)
+    return u0, kappa, rng.random(shape)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
+@pytest.mark.parametrize("shape,periodic,bc", [((30, 27, 45), False, 0.3), ((30, 27, 45), True, 0.0),
+                                                ((64, 50), False, 0.7), ((33, 70), True, 0.0)])
+def test_forward_matches_oracle(dtype, tol, shape, periodic, bc):
+    u0, kappa, _ = fields(shape, 51)
+    g = make(shape, dtype, periodic, bc)
+    g.set_field(u0)
+    g.set_coeff(kappa)
+    g.step(17)
+    g.step(23)
+    g.sync()
+    ref = oracle.cons_forward(u0, kappa, periodic, bc, 40)
+    assert rel_err(g.current().double().cpu().numpy(), ref) <= tol, g.kernel
+    g.close()
+
+
+def test_periodic_sum_conserved_at_size():
+    """Any coefficient field: 100 FP64 sweeps on 128 x 96 x 80 keep sum(u)."""
+    shape = (128, 96, 80)
+    u0, kappa, _ = fields(shape, 52)
+    g = make(shape, torch.float64, True, 0.0)
+    g.set_field(u0)
+    g.set_coeff(kappa)
+    g.step(100)
+    g.sync()
+    got = g.current().cpu().numpy()
+    assert abs(got.sum() - u0.sum()) <= 1e-12 * u0.sum()
+    g.close()
+
+
+def gpu_grad(shape, dtype, periodic, bc, steps, m, seed=53):
+    u0, kappa, tgt = fields(shape, seed)
+    g = make(shape, dtype, periodic, bc)
+    prob = VarCoefProblem(g, steps, m)
+    uT = prob.forward(u0, kappa).double().cpu().numpy()
+    lam0, gk, loss = prob.backward_from(target=tgt)
+    g.sync()
+    out = uT, lam0.double().cpu().numpy(), gk.cpu().numpy(), float(loss.cpu()[0])
+    g.close()
+    return out, oracle.cons_loss_gradient(u0, kappa, tgt, periodic, bc, steps)
+
+
+@pytest.mark.parametrize("periodic,bc", [(False, 0.3), (True, 0.0)])
+def test_gradient_fp64_matches_oracle(periodic, bc):
+    (uT, lam0, gk, loss), (loss_r, uT_r, lam_r, gk_r) = gpu_grad((20, 18, 22), torch.float64, periodic, bc, 30, 7)
+    assert rel_err(uT, uT_r) <= 1e-12
+    assert abs(loss - loss_r) <= 1e-12 * loss_r
+    assert rel_err(lam0, lam_r) <= 1e-12
+    assert rel_err(gk, gk_r) <= 1e-12
+
+
+def test_gradient_fp32_matches_fp64_oracle():
+    (uT, lam0, gk, loss), (loss_r, uT_r, lam_r, gk_r) = gpu_grad((40, 36, 44), torch.float32, False, 0.0, 60, 20)
+    assert rel_err(uT, uT_r) <= 1e-5
+    assert rel_err(lam0, lam_r) <= 1e-5
+    assert rel_err(gk, gk_r) <= 1e-3
+
+
+def test_gradient_2d_and_checkpoint_interval():
+    """2D, and m = 1, 6 and 25 give bitwise equal results (single-step
+    transposes: the same expressions in the same order whatever m is)."""
+    outs = [gpu_grad((48, 37), torch.float64, False, 0.2, 25, m)[0] for m in (25, 6, 1)]
+    for o in outs[1:]:
+        assert np.array_equal(o[1], outs[0][1]) and np.array_equal(o[2], outs[0][2])
+    (uT, lam0, gk, loss), (loss_r, uT_r, lam_r, gk_r) = gpu_grad((48, 37), torch.float64, False, 0.2, 25, 6)
+    assert rel_err(lam0, lam_r) <= 1e-12 and rel_err(gk, gk_r) <= 1e-12

@@ -161,3 +161,49 @@ def test_ghost_pins_catch_planted_mistake(name, monkeypatch):
 def test_unmutated_ghost_sweep_passes_the_same_pins():
     for fn in GHOST_PINS:
         fn()
+
+
+# ------------------------------------------------ the conservative operator
+CONS_SRC = os.path.join(os.path.dirname(oracle.__file__), "conservative.py")
+
+CONS_MUTANTS = {
+    "face coefficient is kappa[p] alone": ("w = (kappa + _shift(kp, o, u.shape)) / 2\n        acc",
+                                           "w = kappa + 0 * _shift(kp, o, u.shape)\n        acc"),
+    "ghost faces padded with zero kappa": ('return np.pad(a, 1, mode="edge")', 'return np.pad(a, 1, mode="constant")'),
+    "transpose forgets the diagonal": ("out -= w * lam", "out -= 0 * w * lam"),
+    "gradient sends nothing to the neighbour": ("_scatter_add(g, np.where(inner, 0.5 * t, 0.0), o, periodic)",
+                                                "pass"),
+    "gradient ghost face weighted one half": ("g += np.where(inner, 0.5 * t, t)", "g += 0.5 * t"),
+}
+
+CONS_PINS = [
+    lambda: [pins.test_cons_constant_kappa_is_the_heat_step(p) for p in (False, True)],
+    lambda: [pins.test_cons_matrix_is_symmetric_and_matches_the_face_rule(p) for p in (False, True)],
+    pins.test_cons_periodic_conserves_the_sum_for_any_kappa,
+    lambda: [pins.test_cons_transpose_equals_the_matrix_transpose(p) for p in (False, True)],
+    lambda: [pins.test_cons_gradient_central_differences(p, b) for p, b in ((False, 0.3), (True, 0.0))],
+]
+
+
+@pytest.mark.parametrize("name", sorted(CONS_MUTANTS))
+def test_conservative_pins_catch_planted_mistake(name, monkeypatch):
+    old, new = CONS_MUTANTS[name]
+    src = open(CONS_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    ns = {}
+    exec(compile(src.replace(old, new), "conservative_mutant", "exec"), ns)
+    for fn in ("cons_step", "cons_forward", "cons_transpose", "cons_loss_gradient"):
+        monkeypatch.setattr(oracle, fn, ns[fn])
+    caught = []
+    for pin in CONS_PINS:
+        try:
+            pin()
+        except Exception as e:
+            caught.append(type(e).__name__)
+    assert caught, f"no pin caught the planted mistake: {name}"
+
+
+def test_unmutated_conservative_oracle_passes_the_same_pins():
+    for pin in CONS_PINS:
+        pin()
+

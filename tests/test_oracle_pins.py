@@ -591,3 +591,106 @@ def test_neumann_vs_assembled_operator():
         x = A @ x
     got = oracle.sweep_neumann(u0, offsets, weights, 4)
     assert np.max(np.abs(got.reshape(-1) - x)) <= 1e-14
+
+
+# ---------------------------------------------------------------- conservative face-averaged operator
+def _cons_matrix(shape, kappa, periodic):
+    """S assembled column by column from the oracle's step (boundary value 0,
+    so the constant part vanishes)."""
+    n = int(np.prod(shape))
+    S = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        S[:, j] = oracle.cons_step(e.reshape(shape), kappa, periodic, 0.0).reshape(-1)
+    return S
+
+
+def _cons_rows(shape, kappa, periodic):
+    """The same matrix written out row by row from the face rule (brute force)."""
+    n = int(np.prod(shape))
+    S = np.zeros((n, n))
+    for p in np.ndindex(*shape):
+        ip = np.ravel_multi_index(p, shape)
+        S[ip, ip] += 1.0
+        for ax in range(len(shape)):
+            for s in (-1, 1):
+                q = list(p)
+                q[ax] += s
+                if periodic:
+                    q[ax] %= shape[ax]
+                inside = 0 <= q[ax] < shape[ax]
+                w = (kappa[p] + kappa[tuple(q)]) / 2 if inside else kappa[p]
+                S[ip, ip] -= w
+                if inside:
+                    S[ip, np.ravel_multi_index(tuple(q), shape)] += w
+    return S
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_cons_constant_kappa_is_the_heat_step(periodic):
+    """kappa = c everywhere: the 7-point heat step (1 - 6c) u + c sum(neighbours)."""
+    rng = np.random.default_rng(41)
+    u0 = rng.random((7, 6, 9))
+    got = oracle.cons_forward(u0, np.full(u0.shape, 0.11), periodic, 0.4, 12)
+    ref = oracle.sweep_const(u0, inputs.OFFSETS_7PT, [1 - 6 * 0.11] + [0.11] * 6, periodic, 0.4, 12)
+    assert np.max(np.abs(got - ref)) <= 1e-13
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_cons_matrix_is_symmetric_and_matches_the_face_rule(periodic):
+    rng = np.random.default_rng(42)
+    shape = (3, 4, 5)
+    kappa = rng.uniform(0.0, 0.16, shape)
+    S = _cons_matrix(shape, kappa, periodic)
+    assert np.max(np.abs(S - _cons_rows(shape, kappa, periodic))) <= 1e-15
+    assert np.max(np.abs(S - S.T)) <= 1e-15
+
+
+def test_cons_periodic_conserves_the_sum_for_any_kappa():
+    rng = np.random.default_rng(43)
+    u0 = rng.random((10, 12, 8))
+    kappa = np.clip(0.05 * np.exp(0.5 * rng.standard_normal(u0.shape)), 0, 0.16)
+    got = oracle.cons_forward(u0, kappa, True, 0.0, 50)
+    assert abs(got.sum() - u0.sum()) <= 1e-12 * u0.sum()
+    c = oracle.cons_forward(np.full((5, 6), 0.7), kappa[0, :5, :6], False, 0.7, 20)
+    assert np.max(np.abs(c - 0.7)) <= 1e-15
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_cons_transpose_equals_the_matrix_transpose(periodic):
+    rng = np.random.default_rng(44)
+    shape = (4, 3, 5)
+    kappa = rng.uniform(0.0, 0.16, shape)
+    lam = rng.standard_normal(shape)
+    S = _cons_matrix(shape, kappa, periodic)
+    got = oracle.cons_transpose(lam, kappa, periodic)
+    assert np.max(np.abs(got.reshape(-1) - S.T @ lam.reshape(-1))) <= 1e-14
+
+
+@pytest.mark.parametrize("periodic,bc", [(False, 0.3), (True, 0.0)])
+def test_cons_gradient_central_differences(periodic, bc):
+    """dL/du0 and dL/dkappa against central differences of the loss along
+    random directions and single coordinates (FP64, 5 x 4 x 6, 6 steps)."""
+    rng = np.random.default_rng(45)
+    shape, steps = (5, 4, 6), 6
+    u0 = rng.random(shape)
+    kappa = rng.uniform(0.02, 0.15, shape)
+    tgt = rng.random(shape)
+    loss, _, du0, dk = oracle.cons_loss_gradient(u0, kappa, tgt, periodic, bc, steps)
+
+    def L(u, k):
+        return 0.5 * float(np.sum((oracle.cons_forward(u, k, periodic, bc, steps) - tgt) ** 2))
+
+    for _ in range(4):
+        d = rng.standard_normal(shape)
+        eps = 1e-6
+        fd_u = (L(u0 + eps * d, kappa) - L(u0 - eps * d, kappa)) / (2 * eps)
+        fd_k = (L(u0, kappa + eps * d) - L(u0, kappa - eps * d)) / (2 * eps)
+        assert abs(fd_u - np.sum(du0 * d)) <= 1e-7 * max(1.0, abs(fd_u))
+        assert abs(fd_k - np.sum(dk * d)) <= 1e-7 * max(1.0, abs(fd_k))
+    for idx in [(0, 0, 0), (4, 3, 5), (2, 1, 3), (0, 2, 5)]:
+        e = np.zeros(shape)
+        e[idx] = 1.0
+        fd = (L(u0, kappa + 1e-6 * e) - L(u0, kappa - 1e-6 * e)) / 2e-6
+        assert abs(fd - dk[idx]) <= 1e-7 * max(1.0, abs(fd))
