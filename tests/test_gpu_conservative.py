@@ -34,8 +34,11 @@ def fields(shape, seed):
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
 @pytest.mark.parametrize("shape,periodic,bc", [((30, 27, 45), False, 0.3), ((30, 27, 45), True, 0.0),
-                                                ((64, 50), False, 0.7), ((33, 70), True, 0.0)])
+                                                ((24, 20, 32), False, 0.3), ((24, 20, 32), True, 0.0),
+                                                ((64, 50), False, 0.7), ((33, 70), True, 0.0), ((40, 64), True, 0.0)])
 def test_forward_matches_oracle(dtype, tol, shape, periodic, bc):
+    """Rows of 45 points take the one-point-per-thread kernels, rows of 32 and
+    64 the 16-byte-group kernels (50 and 70 the group kernels in FP64 only)."""
     u0, kappa, _ = fields(shape, 51)
     g = make(shape, dtype, periodic, bc)
     g.set_field(u0)
@@ -75,16 +78,18 @@ def gpu_grad(shape, dtype, periodic, bc, steps, m, seed=53):
 
 
 @pytest.mark.parametrize("periodic,bc", [(False, 0.3), (True, 0.0)])
-def test_gradient_fp64_matches_oracle(periodic, bc):
-    (uT, lam0, gk, loss), (loss_r, uT_r, lam_r, gk_r) = gpu_grad((20, 18, 22), torch.float64, periodic, bc, 30, 7)
+@pytest.mark.parametrize("shape", [(20, 18, 22), (20, 18, 23)])
+def test_gradient_fp64_matches_oracle(periodic, bc, shape):
+    (uT, lam0, gk, loss), (loss_r, uT_r, lam_r, gk_r) = gpu_grad(shape, torch.float64, periodic, bc, 30, 7)
     assert rel_err(uT, uT_r) <= 1e-12
     assert abs(loss - loss_r) <= 1e-12 * loss_r
     assert rel_err(lam0, lam_r) <= 1e-12
     assert rel_err(gk, gk_r) <= 1e-12
 
 
-def test_gradient_fp32_matches_fp64_oracle():
-    (uT, lam0, gk, loss), (loss_r, uT_r, lam_r, gk_r) = gpu_grad((40, 36, 44), torch.float32, False, 0.0, 60, 20)
+@pytest.mark.parametrize("shape,periodic", [((40, 36, 44), False), ((40, 36, 44), True), ((40, 36, 45), False)])
+def test_gradient_fp32_matches_fp64_oracle(shape, periodic):
+    (uT, lam0, gk, loss), (loss_r, uT_r, lam_r, gk_r) = gpu_grad(shape, torch.float32, periodic, 0.0, 60, 20)
     assert rel_err(uT, uT_r) <= 1e-5
     assert rel_err(lam0, lam_r) <= 1e-5
     assert rel_err(gk, gk_r) <= 1e-3
