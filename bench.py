@@ -459,6 +459,39 @@ def extra_configs(dev, hbm_peak):
     del bp, bt
     torch.cuda.empty_cache()
     out.update(frontend_laplace(dev, hbm_peak))
+    out.update(cavity_flow(dev, hbm_peak))
+    return out
+
+
+def cavity_flow(dev, hbm_peak, n=16384, steps=3, nit=50):
+    """The paper's cavity-flow benchmark at its per-GPU size: 16384^2 arrays,
+    50 pressure iterations per time step, unit lid velocity, rho = 1,
+    nu = 0.1 on [0, 2]^2, dt = 0.25 min(dx, dx^2 / (4 nu)) (stable at this
+    resolution); from rest.  One untimed step, then `steps` timed steps."""
+    import torch
+
+    from paper_2512_19851_gb300.grid import Cavity
+
+    out = {}
+    dx = 2.0 / (n - 1)
+    dt = 0.25 * min(dx, dx * dx / 0.4)
+    s = torch.cuda.Stream(device=dev)
+    for dtype, name in ((torch.float64, "cavity2d_f64"), (torch.float32, "cavity2d_f32")):
+        c = Cavity(n, n, dx, dx, dt, 1.0, 0.1, nit, 1.0, dtype=dtype, device=dev)
+        t = _time(lambda: c.step(steps, s), 1, s)
+        pts = (n - 2) ** 2
+        sweeps = steps * (nit + 2)
+        esz = 8 if dtype == torch.float64 else 4
+        # algorithmic bytes per sweep and point: pressure 2 reads (p, b) + 1 write;
+        # source 2 reads + 1 write; velocity 3 reads + 2 writes
+        bytes_step = esz * pts * (3 * nit + 3 + 5)
+        out[name] = {"glups": pts * sweeps / t / 1e9, "ms_per_time_step": t / steps * 1e3,
+                     "time_steps_per_s": steps / t, "grid": [n, n], "pressure_iterations": nit,
+                     "hbm_frac": bytes_step * steps / t / 1e9 / hbm_peak,
+                     "count": "interior points x (pressure iterations + 2) per time step"}
+        c.close()
+        del c
+        torch.cuda.empty_cache()
     return out
 
 
@@ -666,6 +699,15 @@ def run_profile(case: str, launches: int = 3):
             p = VarCoefProblem(g, 2 + launches, 2 + launches)
             p.forward(u0, kappa)
             p.backward_from(target=u0)
+    elif case in ("cavity_f32", "cavity_f64"):
+        # the cavity flow's kernels on 8192^2 arrays (268 or 537 MB each)
+        from paper_2512_19851_gb300.grid import Cavity
+        n = 8192
+        dx = 2.0 / (n - 1)
+        g = Cavity(n, n, dx, dx, 0.25 * min(dx, dx * dx / 0.4), 1.0, 0.1, 10,
+                   dtype=torch.float32 if case == "cavity_f32" else torch.float64)
+        g.kernel = "k_cav_*"
+        g.step(launches, s)
     elif case == "batch":
         from paper_2512_19851_gb300.grid import Batch
         b = inputs.batch2d()
@@ -687,7 +729,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--headline-only", action="store_true")
-    ap.add_argument("--profile", default=None, help="run one small case for ncu (heat3d_f32, heat3d_f32_512, heat3d_f64, laplace2d_f64, cons_fwd, cons_adj, wave, "
+    ap.add_argument("--profile", default=None, help="run one small case for ncu (heat3d_f32, heat3d_f32_512, heat3d_f64, laplace2d_f64, cons_fwd, cons_adj, cavity_f32, cavity_f64, wave, "
                                                       "varcoef_fwd, varcoef_adj) and exit")
     args = ap.parse_args()
     if args.profile:

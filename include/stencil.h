@@ -68,6 +68,7 @@ extern "C" {
 
 typedef struct st_grid_s* st_grid_t;
 typedef struct st_batch_s* st_batch_t;
+typedef struct st_cavity_s* st_cavity_t;
 
 typedef enum {
     ST_OK = 0,
@@ -419,6 +420,39 @@ st_status stencil_batch_sync(st_batch_t b);
  * kernel (ST_FLAG_GENERIC or offsets beyond the 3x3 neighbourhood).
  */
 st_status stencil_batch_selftest_barrier(st_batch_t b, uint64_t timeout_ns, void* stream);
+
+/* ----------------------------------------------------------------------------
+ * Lid-driven cavity flow: the paper's multi-field benchmark (Sec. V-B, a
+ * Navier-Stokes solver written as NumPy slice assignments over u, v, p and a
+ * pressure source b).  Arrays are dense (ny, nx), C order, boundary rows and
+ * columns included, y along axis 0 and x along axis 1; the lid is the last
+ * row.  One time step:
+ *   1. b = rho ((ux + vy) / dt - ux^2 - 2 uy vx - vy^2) at interior points,
+ *      central differences (ux = (u[j][i+1] - u[j][i-1]) / (2 dx), ...);
+ *   2. nit Jacobi iterations p = ((p_e + p_w) dy^2 + (p_n + p_s) dx^2
+ *      - b dx^2 dy^2) / (2 (dx^2 + dy^2)) at interior points, each followed
+ *      by the boundary rule: right column = its left neighbour, bottom row =
+ *      the row above, left column = its right neighbour, top row = 0;
+ *   3. u, v from the old velocities (backward differences for advection,
+ *      central for the pressure gradient and diffusion, viscosity nu,
+ *      density rho), then u = v = 0 on the walls and u = lid, v = 0 on the
+ *      top row.
+ * The momentum updates of u and v run fused in one kernel.
+ * --------------------------------------------------------------------------*/
+
+/* ny, nx in [3, 2^19] x [3, 2^24]; dx, dy, dt, rho > 0; nu >= 0; nit >= 0. */
+st_status stencil_cavity_create(st_cavity_t* out, int64_t ny, int64_t nx, double dx, double dy, double dt,
+                                double rho, double nu, int nit, double lid, st_dtype dtype);
+st_status stencil_cavity_destroy(st_cavity_t c);
+
+/* Borrow the caller's u, v and p (device, ny*nx elements of the handle's
+ * dtype each, element-aligned, not overlapping: ST_ERR_ALIAS).  The first
+ * bind allocates the handle's scratch (a second buffer per field and b). */
+st_status stencil_cavity_bind(st_cavity_t c, void* u, void* v, void* p);
+
+/* Advance nsteps time steps on `stream`; the bound buffers hold the result
+ * when the enqueued work completes. */
+st_status stencil_cavity_step(st_cavity_t c, int nsteps, void* stream);
 
 #ifdef __cplusplus
 }

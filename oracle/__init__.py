@@ -32,6 +32,9 @@ Functions and the passage each follows:
   (in :mod:`oracle.conservative`) -- the per-cell diffusion in conservative
   face-averaged form, its transpose and the coefficient gradient, plain
   numpy (forward by gather, transpose and gradient by scatter).
+* :mod:`oracle.cavity` -- the lid-driven cavity flow (pressure source,
+  Jacobi pressure iterations with their boundary rule, momentum updates),
+  the paper's multi-field benchmark (Sec. V-B), plain numpy.
 * :func:`taylor_second_derivative_coeffs` (in :mod:`oracle.taylor`) -- the
   8th-order central coefficients from the Taylor conditions.
 

@@ -72,6 +72,10 @@ SIGNATURES = {
     "stencil_adjoint_workspace": (_I, [_VP, _I, _I, _PSZ]),
     "stencil_step_ckpt": (_I, [_VP, _I, _I, _VP, _VP]),
     "stencil_adjoint": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP]),
+    "stencil_cavity_create": (_I, [_PVP, _I64, _I64, _D, _D, _D, _D, _D, _I, _D, _I]),
+    "stencil_cavity_destroy": (_I, [_VP]),
+    "stencil_cavity_bind": (_I, [_VP, _VP, _VP, _VP]),
+    "stencil_cavity_step": (_I, [_VP, _I, _VP]),
     "stencil_batch_create": (_I, [_PVP, _I, _PI64, _I, _PI32, _PD, _I, _D, _I, _U32]),
     "stencil_batch_destroy": (_I, [_VP]),
     "stencil_batch_layout": (_I, [_VP, _I, _PI64, _PI64, _PI64]),
@@ -345,3 +349,23 @@ def stencil_batch_sync(h) -> None:
 def stencil_batch_selftest_barrier(h, timeout_ns, stream=None) -> None:
     _check(lib().stencil_batch_selftest_barrier(h, int(timeout_ns), ctypes.c_void_p(_stream(stream))),
            "stencil_batch_selftest_barrier")
+
+
+def stencil_cavity_create(ny, nx, dx, dy, dt, rho=1.0, nu=0.1, nit=50, lid=1.0, dtype=ST_F64):
+    h = ctypes.c_void_p()
+    _check(lib().stencil_cavity_create(ctypes.byref(h), int(ny), int(nx), float(dx), float(dy), float(dt), float(rho),
+                                       float(nu), int(nit), float(lid), int(dtype)), "stencil_cavity_create")
+    return h.value
+
+
+def stencil_cavity_destroy(h) -> None:
+    _check(lib().stencil_cavity_destroy(h), "stencil_cavity_destroy")
+
+
+def stencil_cavity_bind(h, u_ptr, v_ptr, p_ptr) -> None:
+    _check(lib().stencil_cavity_bind(h, ctypes.c_void_p(int(u_ptr)), ctypes.c_void_p(int(v_ptr)),
+                                     ctypes.c_void_p(int(p_ptr))), "stencil_cavity_bind")
+
+
+def stencil_cavity_step(h, nsteps, stream=None) -> None:
+    _check(lib().stencil_cavity_step(h, int(nsteps), ctypes.c_void_p(_stream(stream))), "stencil_cavity_step")

@@ -10,6 +10,7 @@
 #include <utility>
 #include <vector>
 
+#include "cavity.cuh"
 #include "common.cuh"
 #include "families.cuh"
 
@@ -976,6 +977,107 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     }
     if (lin != lambda)
         ST_CUDA_TRY(cudaMemcpyAsync(lambda, lin, (size_t)g->g.elems * g->g.esize, cudaMemcpyDeviceToDevice, s));
+    return ST_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Lid-driven cavity flow (several fields per step)
+// ---------------------------------------------------------------------------
+struct st_cavity_s {
+    CavityParams P{};
+    CavityBufs B{};
+    void* scratch = nullptr;   // u, v, p second buffers and the pressure source
+};
+
+extern "C" {
+
+st_status stencil_cavity_create(st_cavity_t* out, int64_t ny, int64_t nx, double dx, double dy, double dt, double rho,
+                                double nu, int nit, double lid, st_dtype dtype)
+{
+    if (!out) return fail(ST_ERR_ARG, "stencil_cavity_create: out is NULL");
+    *out = nullptr;
+    if (ny < 3 || nx < 3 || ny > ((int64_t)1 << 19) || nx > ((int64_t)1 << 24))
+        return fail(ST_ERR_ARG, "stencil_cavity_create: extents must be in [3, 2^19] (ny) and [3, 2^24] (nx)");
+    if (!(dx > 0) || !(dy > 0) || !(dt > 0) || !(rho > 0) || !(nu >= 0))
+        return fail(ST_ERR_ARG, "stencil_cavity_create: dx, dy, dt, rho > 0 and nu >= 0");
+    if (nit < 0) return fail(ST_ERR_ARG, "stencil_cavity_create: nit >= 0");
+    if (dtype != ST_F32 && dtype != ST_F64) return fail(ST_ERR_ARG, "stencil_cavity_create: bad dtype");
+    st_cavity_t c = new (std::nothrow) st_cavity_s();
+    if (!c) return fail(ST_ERR_OOM, "stencil_cavity_create: out of host memory");
+    c->P = CavityParams{};
+    c->P.ny = ny;
+    c->P.nx = nx;
+    c->P.dx = dx;
+    c->P.dy = dy;
+    c->P.dt = dt;
+    c->P.rho = rho;
+    c->P.nu = nu;
+    c->P.lid = lid;
+    c->P.nit = nit;
+    c->P.esize = dtype == ST_F64 ? 8 : 4;
+    cavity_constants(c->P);
+    *out = c;
+    return ST_OK;
+}
+
+st_status stencil_cavity_destroy(st_cavity_t c)
+{
+    if (!c) return ST_OK;
+    if (c->scratch) cudaFree(c->scratch);
+    delete c;
+    return ST_OK;
+}
+
+st_status stencil_cavity_bind(st_cavity_t c, void* u, void* v, void* p)
+{
+    if (!c || !u || !v || !p) return fail(ST_ERR_ARG, "stencil_cavity_bind: NULL argument");
+    const size_t bytes = (size_t)c->P.ny * (size_t)c->P.nx * (size_t)c->P.esize;
+    const uintptr_t a[3] = {(uintptr_t)u, (uintptr_t)v, (uintptr_t)p};
+    for (int i = 0; i < 3; ++i) {
+        if (a[i] % (uintptr_t)c->P.esize) return fail(ST_ERR_ARG, "stencil_cavity_bind: misaligned buffer");
+        for (int k = i + 1; k < 3; ++k)
+            if (a[i] < a[k] + bytes && a[k] < a[i] + bytes)
+                return fail(ST_ERR_ALIAS, "stencil_cavity_bind: u, v and p overlap");
+    }
+    if (!c->scratch) {
+        const size_t stride = (bytes + 255) / 256 * 256;
+        if (cudaMalloc(&c->scratch, 4 * stride) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(ST_ERR_OOM, "stencil_cavity_bind: scratch allocation failed");
+        }
+        char* sc = (char*)c->scratch;
+        c->B.u[1] = sc;
+        c->B.v[1] = sc + stride;
+        c->B.p[1] = sc + 2 * stride;
+        c->B.b = sc + 3 * stride;
+    }
+    c->B.u[0] = u;
+    c->B.v[0] = v;
+    c->B.p[0] = p;
+    c->B.cu = c->B.cp = 0;
+    return ST_OK;
+}
+
+st_status stencil_cavity_step(st_cavity_t c, int nsteps, void* stream)
+{
+    if (!c) return fail(ST_ERR_ARG, "stencil_cavity_step: NULL handle");
+    if (nsteps < 0) return fail(ST_ERR_ARG, "stencil_cavity_step: negative step count");
+    if (!c->B.u[0]) return fail(ST_ERR_STATE, "stencil_cavity_step: buffers not bound");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < nsteps; ++k) ST_CUDA_TRY(cavity_step(c->P, c->B, s));
+    // the results go back to the caller's buffers
+    const size_t bytes = (size_t)c->P.ny * (size_t)c->P.nx * (size_t)c->P.esize;
+    if (c->B.cu == 1) {
+        ST_CUDA_TRY(cudaMemcpyAsync(c->B.u[0], c->B.u[1], bytes, cudaMemcpyDeviceToDevice, s));
+        ST_CUDA_TRY(cudaMemcpyAsync(c->B.v[0], c->B.v[1], bytes, cudaMemcpyDeviceToDevice, s));
+        c->B.cu = 0;
+    }
+    if (c->B.cp == 1) {
+        ST_CUDA_TRY(cudaMemcpyAsync(c->B.p[0], c->B.p[1], bytes, cudaMemcpyDeviceToDevice, s));
+        c->B.cp = 0;
+    }
     return ST_OK;
 }
 

@@ -207,6 +207,38 @@ class Batch:
             pass
 
 
+class Cavity:
+    """Lid-driven cavity flow on (ny, nx) arrays u, v, p (boundary included),
+    borrowed by the library's stencil_cavity_* handle."""
+
+    def __init__(self, ny, nx, dx, dy, dt, rho=1.0, nu=0.1, nit=50, lid=1.0, dtype=torch.float64, device=None):
+        self.shape = (int(ny), int(nx))
+        self.dtype = dtype
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.h = abi.stencil_cavity_create(ny, nx, dx, dy, dt, rho, nu, nit, lid, _ST_DTYPE[dtype])
+        self.u, self.v, self.p = (torch.zeros(self.shape, dtype=dtype, device=self.device) for _ in range(3))
+        abi.stencil_cavity_bind(self.h, self.u.data_ptr(), self.v.data_ptr(), self.p.data_ptr())
+
+    def set(self, u, v, p) -> None:
+        for t, x in ((self.u, u), (self.v, v), (self.p, p)):
+            t.copy_(_as_tensor(x, self.dtype, self.device))
+
+    def step(self, nsteps: int, stream=None) -> None:
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        abi.stencil_cavity_step(self.h, nsteps, s)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            abi.stencil_cavity_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------------------
 # Differentiation
 # ---------------------------------------------------------------------------

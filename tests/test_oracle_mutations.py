@@ -10,7 +10,9 @@ import contextlib
 import ctypes
 import os
 import subprocess
+import sys
 import tempfile
+import types
 
 import numpy as np
 import pytest
@@ -206,4 +208,40 @@ def test_conservative_pins_catch_planted_mistake(name, monkeypatch):
 def test_unmutated_conservative_oracle_passes_the_same_pins():
     for pin in CONS_PINS:
         pin()
+
+
+# ------------------------------------------------ the cavity flow
+CAV_SRC = os.path.join(os.path.dirname(oracle.__file__), "cavity.py")
+
+CAV_MUTANTS = {
+    "pressure iteration swaps dx and dy": ("((pe + pw) * dy2 + (pnn + ps) * dx2", "((pe + pw) * dx2 + (pnn + ps) * dy2"),
+    "pressure source drops the factor 2 of the cross term": ("- 2 * uy * vx", "- uy * vx"),
+    "pressure source takes uy along x": ("uy = (un - us) / (2 * P.dy)", "uy = (ue - uw) / (2 * P.dy)"),
+    "velocity pressure gradient with the wrong sign": ("- P.dt / (2 * P.rho * P.dx) * (pe - pw)",
+                                                       "+ P.dt / (2 * P.rho * P.dx) * (pe - pw)"),
+    "v advected by v along x": ("(vc - uc * cx * (vc - vw)", "(vc - vc * cx * (vc - vw)"),
+    "boundary rule: bottom row copies itself": ("p[0, :] = p[1, :]", "p[0, :] = p[0, :]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CAV_MUTANTS))
+def test_cavity_pins_catch_planted_mistake(name, monkeypatch):
+    old, new = CAV_MUTANTS[name]
+    src = open(CAV_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    mod = types.ModuleType("cavity_mutant")
+    monkeypatch.setitem(sys.modules, "cavity_mutant", mod)   # dataclasses look their module up
+    exec(compile(src.replace(old, new), "cavity_mutant", "exec"), mod.__dict__)
+    ns = mod.__dict__
+    for fn in ("pressure_source", "pressure_iterations", "velocity_update", "cavity_run", "pressure_boundary"):
+        monkeypatch.setattr(pins.cav, fn, ns[fn])
+    caught = []
+    for pin in (pins.test_cavity_vectorised_equals_point_loops, pins.test_cavity_pressure_source_of_linear_fields,
+                pins.test_cavity_pressure_iteration_solves_the_discrete_poisson_problem,
+                pins.test_cavity_velocity_update_of_simple_fields):
+        try:
+            pin()
+        except Exception as e:
+            caught.append(type(e).__name__)
+    assert caught, f"no pin caught the planted mistake: {name}"
 

@@ -694,3 +694,115 @@ def test_cons_gradient_central_differences(periodic, bc):
         e[idx] = 1.0
         fd = (L(u0, kappa + 1e-6 * e) - L(u0, kappa - 1e-6 * e)) / 2e-6
         assert abs(fd - dk[idx]) <= 1e-7 * max(1.0, abs(fd))
+
+
+# ---------------------------------------------------------------- lid-driven cavity flow
+from oracle import cavity as cav  # noqa: E402
+
+CAVP = cav.CavityParams(dx=0.05, dy=0.04, dt=0.001, rho=1.3, nu=0.1, nit=5, lid=1.0)
+
+
+def _cavity_loops(u0, v0, p0, P, nsteps):
+    """The same scheme written point by point with Python loops (brute force,
+    tiny grids only)."""
+    u, v, p = [np.array(a, dtype=np.float64) for a in (u0, v0, p0)]
+    ny, nx = u.shape
+    dx, dy, dt, rho, nu = P.dx, P.dy, P.dt, P.rho, P.nu
+    for _ in range(nsteps):
+        b = np.zeros_like(u)
+        for j in range(1, ny - 1):
+            for i in range(1, nx - 1):
+                ux = (u[j, i + 1] - u[j, i - 1]) / (2 * dx)
+                uy = (u[j + 1, i] - u[j - 1, i]) / (2 * dy)
+                vx = (v[j, i + 1] - v[j, i - 1]) / (2 * dx)
+                vy = (v[j + 1, i] - v[j - 1, i]) / (2 * dy)
+                b[j, i] = rho * ((ux + vy) / dt - ux * ux - 2 * uy * vx - vy * vy)
+        for _ in range(P.nit):
+            pn = p.copy()
+            for j in range(1, ny - 1):
+                for i in range(1, nx - 1):
+                    p[j, i] = ((pn[j, i + 1] + pn[j, i - 1]) * dy * dy + (pn[j + 1, i] + pn[j - 1, i]) * dx * dx
+                               - b[j, i] * dx * dx * dy * dy) / (2 * (dx * dx + dy * dy))
+            for j in range(ny):
+                p[j, nx - 1] = p[j, nx - 2]
+            for i in range(nx):
+                p[0, i] = p[1, i]
+            for j in range(ny):
+                p[j, 0] = p[j, 1]
+            for i in range(nx):
+                p[ny - 1, i] = 0.0
+        un, vn = u.copy(), v.copy()
+        for j in range(1, ny - 1):
+            for i in range(1, nx - 1):
+                c, w, s = un[j, i], un[j, i - 1], un[j - 1, i]
+                u[j, i] = (c - c * dt / dx * (c - w) - vn[j, i] * dt / dy * (c - s)
+                           - dt / (2 * rho * dx) * (p[j, i + 1] - p[j, i - 1])
+                           + nu * (dt / dx ** 2 * (un[j, i + 1] - 2 * c + w) + dt / dy ** 2 * (un[j + 1, i] - 2 * c + s)))
+                c, w, s = vn[j, i], vn[j, i - 1], vn[j - 1, i]
+                v[j, i] = (c - un[j, i] * dt / dx * (c - w) - c * dt / dy * (c - s)
+                           - dt / (2 * rho * dy) * (p[j + 1, i] - p[j - 1, i])
+                           + nu * (dt / dx ** 2 * (vn[j, i + 1] - 2 * c + w) + dt / dy ** 2 * (vn[j + 1, i] - 2 * c + s)))
+        u[0, :] = u[:, 0] = u[:, -1] = 0.0
+        u[-1, :] = P.lid
+        v[0, :] = v[-1, :] = v[:, 0] = v[:, -1] = 0.0
+    return u, v, p
+
+
+def test_cavity_vectorised_equals_point_loops():
+    rng = np.random.default_rng(61)
+    shape = (7, 9)
+    u0, v0, p0 = (0.2 * rng.standard_normal(shape) for _ in range(3))
+    got = cav.cavity_run(u0, v0, p0, CAVP, 3)
+    ref = _cavity_loops(u0, v0, p0, CAVP, 3)
+    for g, r in zip(got, ref):
+        assert np.max(np.abs(g - r)) <= 1e-12 * max(1.0, np.max(np.abs(r)))
+
+
+def test_cavity_rest_state_stays_at_rest():
+    z = np.zeros((11, 13))
+    P = cav.CavityParams(dx=0.1, dy=0.1, dt=0.001, lid=0.0, nit=20)
+    for a in cav.cavity_run(z, z, z, P, 5):
+        assert np.all(a == 0.0)
+
+
+def test_cavity_pressure_source_of_linear_fields():
+    """u = a x + c y, v = d x + e y: central differences are exact, so
+    b = rho ((a + e) / dt - a^2 - 2 c d - e^2) at every interior point."""
+    a, c, d, e = 0.7, -0.3, 0.4, 1.1
+    y, x = np.meshgrid(np.arange(8) * CAVP.dy, np.arange(10) * CAVP.dx, indexing="ij")
+    b = cav.pressure_source(a * x + c * y, d * x + e * y, CAVP)
+    want = CAVP.rho * ((a + e) / CAVP.dt - a * a - 2 * c * d - e * e)
+    assert np.max(np.abs(b[1:-1, 1:-1] - want)) <= 1e-9 * abs(want)
+    assert np.all(b[0] == 0) and np.all(b[:, -1] == 0)
+
+
+def test_cavity_pressure_iteration_solves_the_discrete_poisson_problem():
+    """At the fixed point of the Jacobi iteration, the five-point Laplacian of
+    p (spacings dx != dy) equals b at every interior point, and the boundary
+    rule holds."""
+    rng = np.random.default_rng(62)
+    shape = (9, 7)
+    b = np.zeros(shape)
+    b[1:-1, 1:-1] = rng.standard_normal((7, 5))
+    p = cav.pressure_iterations(np.zeros(shape), b, CAVP, nit=6000)
+    lap = ((p[1:-1, 2:] - 2 * p[1:-1, 1:-1] + p[1:-1, :-2]) / CAVP.dx ** 2
+           + (p[2:, 1:-1] - 2 * p[1:-1, 1:-1] + p[:-2, 1:-1]) / CAVP.dy ** 2)
+    assert np.max(np.abs(lap - b[1:-1, 1:-1])) <= 1e-8 * np.max(np.abs(b))
+    assert np.all(p[-1] == 0) and np.array_equal(p[1:-1, 0], p[1:-1, 1]) and np.array_equal(p[0, 1:-1], p[1, 1:-1])
+
+
+def test_cavity_velocity_update_of_simple_fields():
+    """Uniform u = U, v = V with p = g x + h y: advection and diffusion vanish
+    and the pressure gradient is exact, so u' = U - dt g / rho and
+    v' = V - dt h / rho inside.  u = a x with v = 0 and p = 0: the backward
+    difference of a linear field is exact, so u' = u - dt a u inside."""
+    y, x = np.meshgrid(np.arange(8) * CAVP.dy, np.arange(10) * CAVP.dx, indexing="ij")
+    U, V, g, h = 0.3, -0.2, 2.0, -1.5
+    u2, v2 = cav.velocity_update(np.full(x.shape, U), np.full(x.shape, V), g * x + h * y, CAVP)
+    assert np.max(np.abs(u2[1:-1, 1:-1] - (U - CAVP.dt * g / CAVP.rho))) <= 1e-14
+    assert np.max(np.abs(v2[1:-1, 1:-1] - (V - CAVP.dt * h / CAVP.rho))) <= 1e-14
+    assert np.all(u2[-1] == CAVP.lid) and np.all(u2[0] == 0) and np.all(v2[:, 0] == 0)
+    a = 0.8
+    u2, v2 = cav.velocity_update(a * x, np.zeros(x.shape), np.zeros(x.shape), CAVP)
+    assert np.max(np.abs(u2[1:-1, 1:-1] - (a * x - CAVP.dt * a * a * x)[1:-1, 1:-1])) <= 1e-14
+    assert np.all(v2 == 0)
