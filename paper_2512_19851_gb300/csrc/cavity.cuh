@@ -11,12 +11,32 @@ struct CavityParams {
     double dx, dy, dt, rho, nu, lid;
     int nit;          // pressure iterations per time step
     int esize;        // 4 or 8
-    // per-point constants computed once on the host in double precision, so
-    // the kernels multiply instead of dividing (a divide is an iterative
-    // sequence on the FP64 pipe)
-    double i2dx, i2dy, idt;                 // 1/(2 dx), 1/(2 dy), 1/dt
-    double dx2, dy2, dx2dy2, ipden;         // dx^2, dy^2, dx^2 dy^2, 1/(2 (dx^2 + dy^2))
-    double cx, cy, dxx, dyy, gx, gy;        // dt/dx, dt/dy, dt/dx^2, dt/dy^2, dt/(2 rho dx), dt/(2 rho dy)
+    // per-point constants computed once on the host in double precision and
+    // also rounded to float there, so the kernels neither divide (a divide is
+    // an iterative sequence on the FP64 pipe) nor convert (a double-to-float
+    // conversion runs on the FP64 pipe too, 2 lanes per clock per SM here)
+    double c64[16];
+    float c32[16];
+};
+
+// indices into CavityParams::c64 / c32
+enum CavityConst {
+    CV_I2DX = 0,  // 1/(2 dx)
+    CV_I2DY,      // 1/(2 dy)
+    CV_IDT,       // 1/dt
+    CV_DX2,       // dx^2
+    CV_DY2,       // dy^2
+    CV_DX2DY2,    // dx^2 dy^2
+    CV_IPDEN,     // 1/(2 (dx^2 + dy^2))
+    CV_CX,        // dt/dx
+    CV_CY,        // dt/dy
+    CV_DXX,       // dt/dx^2
+    CV_DYY,       // dt/dy^2
+    CV_GX,        // dt/(2 rho dx)
+    CV_GY,        // dt/(2 rho dy)
+    CV_RHO,
+    CV_NU,
+    CV_LID
 };
 
 void cavity_constants(CavityParams& P);

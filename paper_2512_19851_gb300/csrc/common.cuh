@@ -60,7 +60,14 @@ struct GenParams {
     int32_t dz[ST_MAX_POINTS], dy[ST_MAX_POINTS], dx[ST_MAX_POINTS];
     int64_t lin[ST_MAX_POINTS];  // linear offset in the padded layout
     double alpha[ST_MAX_POINTS], beta[ST_MAX_POINTS];
+    // the same weights rounded to float once on the host: an FP32 kernel that
+    // converted them per point would keep the FP64 pipe (where the
+    // conversion runs, 2 lanes per clock per SM on this GPU) busy
+    float alpha_f[ST_MAX_POINTS], beta_f[ST_MAX_POINTS];
 };
+
+// Fill alpha_f / beta_f from alpha / beta.
+void gen_params_floats(GenParams& P);
 
 // Kernel launchers (k_generic.cu) -------------------------------------------
 cudaError_t launch_generic_sweep(int esize, const void* in, void* out, const void* prev,

@@ -29,6 +29,7 @@ static GenParams make_gen_params(const FamilyDesc& d)
         P.alpha[k] = d.alpha[k];
         P.beta[k] = d.has_beta ? d.beta[k] : 0.0;
     }
+    gen_params_floats(P);
     return P;
 }
 

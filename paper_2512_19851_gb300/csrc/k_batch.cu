@@ -400,6 +400,7 @@ BatchPlan make_batch_plan(const std::vector<Geom>& geoms, int npts, const int32_
             P.lin[k] = (int64_t)P.dy[k] * g.pitch + P.dx[k];
             P.alpha[k] = weights[(size_t)i * npts + k];
         }
+        gen_params_floats(P);
         p.gp.push_back(P);
     }
     // default configuration (tile 128 x 32, 256 threads, 5 steps per pass)

@@ -29,6 +29,13 @@ namespace {
 __device__ __forceinline__ int64_t clampi(int64_t i, int64_t n) { return i < 1 ? 1 : (i > n - 2 ? n - 2 : i); }
 
 template <typename T>
+__device__ __forceinline__ T cv(const CavityParams& P, int k)
+{
+    if constexpr (sizeof(T) == 4) return P.c32[k];
+    else return P.c64[k];
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_cav_source(const T* __restrict__ u, const T* __restrict__ v,
                                                     T* __restrict__ b, const __grid_constant__ CavityParams P)
 {
@@ -36,14 +43,24 @@ __global__ void __launch_bounds__(256) k_cav_source(const T* __restrict__ u, con
     const int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y;
     if (i < 1 || j < 1 || i >= P.nx - 1 || j >= P.ny - 1) return;
     const int64_t c = j * P.nx + i;
-    const T i2dx = T(P.i2dx), i2dy = T(P.i2dy);
+    const T i2dx = cv<T>(P, CV_I2DX), i2dy = cv<T>(P, CV_I2DY);
     const T ux = (u[c + 1] - u[c - 1]) * i2dx;
     const T uy = (u[c + P.nx] - u[c - P.nx]) * i2dy;
     const T vx = (v[c + 1] - v[c - 1]) * i2dx;
     const T vy = (v[c + P.nx] - v[c - P.nx]) * i2dy;
-    b[c] = T(P.rho) * ((ux + vy) * T(P.idt) - ux * ux - T(2) * uy * vx - vy * vy);
+    b[c] = cv<T>(P, CV_RHO) * ((ux + vy) * cv<T>(P, CV_IDT) - ux * ux - T(2) * uy * vx - vy * vy);
 }
 
+// One Jacobi update from its inputs: a single expression for every caller,
+// so a boundary cell gets exactly its clamped interior cell's value.
+template <typename T>
+__device__ __forceinline__ T jacobi(T e, T w, T n, T s, T bb, const CavityParams& P)
+{
+    return ((e + w) * cv<T>(P, CV_DY2) + (n + s) * cv<T>(P, CV_DX2) - bb * cv<T>(P, CV_DX2DY2)) * cv<T>(P, CV_IPDEN);
+}
+
+// (Staging the block's cells and halo in shared memory instead of gathering
+// through L1 measured slower: 159 vs 274 GLUP/s in FP32 at 16384^2.)
 template <typename T>
 __global__ void __launch_bounds__(256) k_cav_pressure(const T* __restrict__ pin, T* __restrict__ pout,
                                                       const T* __restrict__ b, const __grid_constant__ CavityParams P)
@@ -57,9 +74,7 @@ __global__ void __launch_bounds__(256) k_cav_pressure(const T* __restrict__ pin,
         return;
     }
     const int64_t c = clampi(j, P.ny) * P.nx + clampi(i, P.nx);
-    pout[o] = ((pin[c + 1] + pin[c - 1]) * T(P.dy2) + (pin[c + P.nx] + pin[c - P.nx]) * T(P.dx2) -
-               b[c] * T(P.dx2dy2)) *
-              T(P.ipden);
+    pout[o] = jacobi(pin[c + 1], pin[c - 1], pin[c + P.nx], pin[c - P.nx], b[c], P);
 }
 
 template <typename T>
@@ -72,7 +87,7 @@ __global__ void __launch_bounds__(256) k_cav_velocity(const T* __restrict__ u, c
     if (i >= P.nx || j >= P.ny) return;
     const int64_t c = j * P.nx + i;
     if (j == P.ny - 1) {  // the lid
-        u2[c] = T(P.lid);
+        u2[c] = cv<T>(P, CV_LID);
         v2[c] = T(0);
         return;
     }
@@ -81,12 +96,13 @@ __global__ void __launch_bounds__(256) k_cav_velocity(const T* __restrict__ u, c
         v2[c] = T(0);
         return;
     }
-    const T nu = T(P.nu), cx = T(P.cx), cy = T(P.cy), dxx = T(P.dxx), dyy = T(P.dyy);
+    const T nu = cv<T>(P, CV_NU), cx = cv<T>(P, CV_CX), cy = cv<T>(P, CV_CY), dxx = cv<T>(P, CV_DXX),
+            dyy = cv<T>(P, CV_DYY);
     const T uc = u[c], ue = u[c + 1], uw = u[c - 1], un = u[c + P.nx], us = u[c - P.nx];
     const T vc = v[c], ve = v[c + 1], vw = v[c - 1], vn = v[c + P.nx], vs = v[c - P.nx];
-    u2[c] = uc - uc * cx * (uc - uw) - vc * cy * (uc - us) - T(P.gx) * (p[c + 1] - p[c - 1]) +
+    u2[c] = uc - uc * cx * (uc - uw) - vc * cy * (uc - us) - cv<T>(P, CV_GX) * (p[c + 1] - p[c - 1]) +
             nu * (dxx * (ue - T(2) * uc + uw) + dyy * (un - T(2) * uc + us));
-    v2[c] = vc - uc * cx * (vc - vw) - vc * cy * (vc - vs) - T(P.gy) * (p[c + P.nx] - p[c - P.nx]) +
+    v2[c] = vc - uc * cx * (vc - vw) - vc * cy * (vc - vs) - cv<T>(P, CV_GY) * (p[c + P.nx] - p[c - P.nx]) +
             nu * (dxx * (ve - T(2) * vc + vw) + dyy * (vn - T(2) * vc + vs));
 }
 
@@ -114,19 +130,24 @@ cudaError_t cav_step_t(const CavityParams& P, CavityBufs& B, cudaStream_t s)
 
 void cavity_constants(CavityParams& P)
 {
-    P.i2dx = 1.0 / (2.0 * P.dx);
-    P.i2dy = 1.0 / (2.0 * P.dy);
-    P.idt = 1.0 / P.dt;
-    P.dx2 = P.dx * P.dx;
-    P.dy2 = P.dy * P.dy;
-    P.dx2dy2 = P.dx2 * P.dy2;
-    P.ipden = 1.0 / (2.0 * (P.dx2 + P.dy2));
-    P.cx = P.dt / P.dx;
-    P.cy = P.dt / P.dy;
-    P.dxx = P.dt / P.dx2;
-    P.dyy = P.dt / P.dy2;
-    P.gx = P.dt / (2.0 * P.rho * P.dx);
-    P.gy = P.dt / (2.0 * P.rho * P.dy);
+    double* c = P.c64;
+    c[CV_I2DX] = 1.0 / (2.0 * P.dx);
+    c[CV_I2DY] = 1.0 / (2.0 * P.dy);
+    c[CV_IDT] = 1.0 / P.dt;
+    c[CV_DX2] = P.dx * P.dx;
+    c[CV_DY2] = P.dy * P.dy;
+    c[CV_DX2DY2] = c[CV_DX2] * c[CV_DY2];
+    c[CV_IPDEN] = 1.0 / (2.0 * (c[CV_DX2] + c[CV_DY2]));
+    c[CV_CX] = P.dt / P.dx;
+    c[CV_CY] = P.dt / P.dy;
+    c[CV_DXX] = P.dt / c[CV_DX2];
+    c[CV_DYY] = P.dt / c[CV_DY2];
+    c[CV_GX] = P.dt / (2.0 * P.rho * P.dx);
+    c[CV_GY] = P.dt / (2.0 * P.rho * P.dy);
+    c[CV_RHO] = P.rho;
+    c[CV_NU] = P.nu;
+    c[CV_LID] = P.lid;
+    for (int k = 0; k < 16; ++k) P.c32[k] = (float)c[k];
 }
 
 cudaError_t cavity_step(const CavityParams& P, CavityBufs& B, cudaStream_t s)

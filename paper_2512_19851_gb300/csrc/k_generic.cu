@@ -13,6 +13,20 @@ namespace st {
 
 namespace {
 
+template <typename T>
+__device__ __forceinline__ T alpha_of(const GenParams& P, int k)
+{
+    if constexpr (sizeof(T) == 4) return P.alpha_f[k];
+    else return P.alpha[k];
+}
+
+template <typename T>
+__device__ __forceinline__ T beta_of(const GenParams& P, int k)
+{
+    if constexpr (sizeof(T) == 4) return P.beta_f[k];
+    else return P.beta[k];
+}
+
 __device__ __forceinline__ int64_t wrap1(int64_t i, int64_t n)
 {
     // |offset| < n is validated on the host, so one correction suffices
@@ -42,8 +56,8 @@ k_sweep_generic(const T* __restrict__ in, T* out, const T* prev, const T* __rest
         } else {
             v = in[p + P.lin[k]];
         }
-        T w = T(P.alpha[k]);
-        if (P.has_kappa) w = fma(T(P.beta[k]), kap, w);
+        T w = alpha_of<T>(P, k);
+        if (P.has_kappa) w = fma(beta_of<T>(P, k), kap, w);
         acc = fma(w, v, acc);
     }
     if (P.leapfrog) acc = acc - prev[p];
@@ -79,10 +93,10 @@ k_adjoint_generic(const T* __restrict__ u, const T* __restrict__ lam, T* __restr
             pm = q - P.lin[k];
             pp = q + P.lin[k];
         }
-        T w = T(P.alpha[k]);
-        if (P.has_kappa) w = fma(T(P.beta[k]), kappa[pm], w);
+        T w = alpha_of<T>(P, k);
+        if (P.has_kappa) w = fma(beta_of<T>(P, k), kappa[pm], w);
         acc = fma(w, lam[pm], acc);
-        if (gk) s = fma(T(P.beta[k]), u[pp], s);
+        if (gk) s = fma(beta_of<T>(P, k), u[pp], s);
     }
     lout[q] = acc;
     if (gk) gk[q] += (double)lam[q] * (double)s;
@@ -431,6 +445,14 @@ dim3 point_grid(const GenParams& P)
 }
 
 }  // namespace
+
+void gen_params_floats(GenParams& P)
+{
+    for (int k = 0; k < ST_MAX_POINTS; ++k) {
+        P.alpha_f[k] = (float)P.alpha[k];
+        P.beta_f[k] = (float)P.beta[k];
+    }
+}
 
 cudaError_t launch_generic_sweep(int esize, const void* in, void* out, const void* prev,
                                  const void* kappa, const GenParams& P, cudaStream_t s)

@@ -64,6 +64,16 @@ def test_non_square_random_start_odd_iterations():
     check(P, shape, 12, u0, v0, p0)
 
 
+def test_many_tiles():
+    """97 x 130: interior blocks, blocks on every edge and ragged last blocks
+    of the pressure kernel's 32 x 8 tiles."""
+    rng = np.random.default_rng(73)
+    shape = (97, 130)
+    P = cav.CavityParams(dx=0.02, dy=0.025, dt=0.0002, rho=1.0, nu=0.05, nit=20, lid=1.0)
+    u0, v0, p0 = (0.1 * rng.standard_normal(shape) for _ in range(3))
+    check(P, shape, 6, u0, v0, p0)
+
+
 def test_split_calls_equal_one_call_and_no_pressure_iterations():
     rng = np.random.default_rng(72)
     shape = (29, 34)
