@@ -220,3 +220,24 @@ def test_conservative_create():
         with pytest.raises(abi.StencilError) as e:
             abi.stencil_create_conservative(**args)
         assert e.value.code == abi.ST_ERR_ARG
+
+
+def test_cavity_arguments():
+    for kw in (dict(ny=2), dict(nx=2), dict(dx=0.0), dict(dt=-1.0), dict(rho=0.0), dict(nu=-0.1), dict(nit=-1),
+               dict(dtype=5)):
+        args = dict(ny=41, nx=41, dx=0.05, dy=0.05, dt=0.001, rho=1.0, nu=0.1, nit=50, lid=1.0, dtype=abi.ST_F64)
+        args.update(kw)
+        with pytest.raises(abi.StencilError) as e:
+            abi.stencil_cavity_create(**args)
+        assert e.value.code == abi.ST_ERR_ARG
+    h = abi.stencil_cavity_create(41, 41, 0.05, 0.05, 0.001)
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_cavity_step(h, 1)
+    assert e.value.code == abi.ST_ERR_STATE
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_cavity_bind(h, 0, 16, 32)
+    assert e.value.code == abi.ST_ERR_ARG
+    with pytest.raises(abi.StencilError) as e:          # u and v overlap (checked before any allocation)
+        abi.stencil_cavity_bind(h, 1 << 20, (1 << 20) + 8, 1 << 24)
+    assert e.value.code == abi.ST_ERR_ALIAS
+    abi.stencil_cavity_destroy(h)
