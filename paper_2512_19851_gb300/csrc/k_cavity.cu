@@ -6,8 +6,9 @@
 // C order, boundary rows and columns included (y along axis 0, x along
 // axis 1).
 //
-// GB300 design: one thread per cell of the whole array, so each kernel also
-// writes its boundary cells and no separate boundary pass runs:
+// GB300 design: every cell of the whole array has a thread (the pressure
+// kernel: a thread per column walking 16 rows), so each kernel also writes
+// its boundary cells and no separate boundary pass runs:
 //  * the pressure iteration's boundary rule (right column copies its left
 //    neighbour, bottom row the row above, left column its right neighbour,
 //    then the top row is set to 0) leaves every boundary cell below the top
@@ -18,8 +19,7 @@
 //  * the two momentum updates are fused in one kernel (the paper's node
 //    fusion of updates with the same output shape): both read the same
 //    neighbourhoods of u, v and p.
-// Each kernel is a gather over 5-point neighbourhoods through L1/L2; FP64 is
-// bound by the FP64 pipe, FP32 by memory.
+// FP64 is bound by the FP64 pipe, FP32 by memory latency and bandwidth.
 #include "cavity.cuh"
 
 namespace st {
@@ -59,22 +59,42 @@ __device__ __forceinline__ T jacobi(T e, T w, T n, T s, T bb, const CavityParams
     return ((e + w) * cv<T>(P, CV_DY2) + (n + s) * cv<T>(P, CV_DX2) - bb * cv<T>(P, CV_DX2DY2)) * cv<T>(P, CV_IPDEN);
 }
 
-// (Staging the block's cells and halo in shared memory instead of gathering
-// through L1 measured slower: 159 vs 274 GLUP/s in FP32 at 16384^2.)
+// (Measured forms not kept, FP32 at 16384^2: one thread per cell gathering
+// its four neighbours through L1, 274 GLUP/s; the block's cells and halo
+// staged in shared memory, 159 GLUP/s.)
+// A thread owns a column and walks RY rows of it, keeping the input pressure
+// of the rows below, at and above its (clamped) centre in registers, so a
+// cell costs one new row load, its two x neighbours (L1 hits: the warp
+// loaded that row one step earlier) and its source value.  Boundary columns
+// walk the clamped column (1 or nx - 2), boundary row 0 the clamped row 1.
+constexpr int RY = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_cav_pressure(const T* __restrict__ pin, T* __restrict__ pout,
                                                       const T* __restrict__ b, const __grid_constant__ CavityParams P)
 {
-    const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
-    const int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y;
-    if (i >= P.nx || j >= P.ny) return;
-    const int64_t o = j * P.nx + i;
-    if (j == P.ny - 1) {  // the lid row: p = 0
-        pout[o] = T(0);
-        return;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= P.nx) return;
+    const int64_t j0 = (int64_t)blockIdx.y * RY, j1 = j0 + RY < P.ny ? j0 + RY : P.ny;
+    const int64_t ci = clampi(i, P.nx);
+    int64_t r = clampi(j0, P.ny);              // centre row of the window
+    T s = pin[(r - 1) * P.nx + ci], c = pin[r * P.nx + ci], n = pin[(r + 1) * P.nx + ci];
+    for (int64_t j = j0; j < j1; ++j) {
+        const int64_t o = j * P.nx + i;
+        if (j == P.ny - 1) {  // the lid row: p = 0
+            pout[o] = T(0);
+            continue;
+        }
+        const int64_t rj = clampi(j, P.ny);
+        if (rj != r) {  // advance the window by one row (rj == r + 1 here)
+            r = rj;
+            s = c;
+            c = n;
+            n = pin[(r + 1) * P.nx + ci];
+        }
+        const int64_t cc = r * P.nx + ci;
+        pout[o] = jacobi(pin[cc + 1], pin[cc - 1], n, s, b[cc], P);
     }
-    const int64_t c = clampi(j, P.ny) * P.nx + clampi(i, P.nx);
-    pout[o] = jacobi(pin[c + 1], pin[c - 1], pin[c + P.nx], pin[c - P.nx], b[c], P);
 }
 
 template <typename T>
@@ -115,9 +135,10 @@ template <typename T>
 cudaError_t cav_step_t(const CavityParams& P, CavityBufs& B, cudaStream_t s)
 {
     const dim3 g = cav_grid(P), blk(32, 8);
+    const dim3 gp((unsigned)((P.nx + 255) / 256), (unsigned)((P.ny + RY - 1) / RY), 1);
     k_cav_source<T><<<g, blk, 0, s>>>((const T*)B.u[B.cu], (const T*)B.v[B.cu], (T*)B.b, P);
     for (int k = 0; k < P.nit; ++k) {
-        k_cav_pressure<T><<<g, blk, 0, s>>>((const T*)B.p[B.cp], (T*)B.p[1 - B.cp], (const T*)B.b, P);
+        k_cav_pressure<T><<<gp, 256, 0, s>>>((const T*)B.p[B.cp], (T*)B.p[1 - B.cp], (const T*)B.b, P);
         B.cp = 1 - B.cp;
     }
     k_cav_velocity<T><<<g, blk, 0, s>>>((const T*)B.u[B.cu], (const T*)B.v[B.cu], (const T*)B.p[B.cp],
