@@ -197,3 +197,45 @@ def test_fill_values_and_host_data_before_execution():
     host[0, 2] = 3
     assert fe._ring_value(host, 1) is None
     assert [n.kind for n in p.nodes] == ["fill", "fill", "fill"]
+
+
+class _Buf:
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def data_ptr(self):
+        return self.ptr
+
+
+def test_settle_puts_the_newest_level_where_the_program_expects_it():
+    """After n alternating sweeps from src into dst the program expects level
+    n in dst (n odd) or src (n even); if the library left it in the other
+    buffer, the two arrays exchange buffers, otherwise nothing moves."""
+    for n, newest_in, swapped in ((3, "dst", False), (3, "src", True), (4, "src", False), (4, "dst", True)):
+        p = Program()
+        src, dst = p.create_array((4, 4)), p.create_array((4, 4))
+        src.dev, dst.dev = _Buf(100), _Buf(200)
+        src.view, dst.view = "view-a", "view-b"
+        fe._settle(src, dst, 200 if newest_in == "dst" else 100, n)
+        assert (src.dev.ptr == 200) == swapped and (dst.dev.ptr == 100) == swapped
+        assert (src.view == "view-b") == swapped
+
+
+def test_fused_3d_members_run_one_after_another():
+    """Fusion groups members of any dimension; 3D members are not batchable
+    (the batched kernel is 2D), so the plan still has one run of the group."""
+    p = Program()
+    a1, a2 = p.create_array((5, 6, 7)), p.create_array((5, 6, 7))
+    b1, b2 = p.create_array((5, 6, 7)), p.create_array((5, 6, 7))
+    i = slice(1, -1)
+    for _ in range(3):
+        a2[i, i, i] = 0.5 * (a1[:-2, i, i] + a1[2:, i, i])
+        b2[i, i, i] = 0.5 * (b1[i, :-2, i] + b1[i, 2:, i])
+        a1, a2 = a2, a1
+        b1, b2 = b2, b1
+    assert p.plan() == [("run", [0, 1], 3)]
+    members = [p.nodes[0], p.nodes[1]]
+    for m in members:
+        for arr in m.args:
+            arr.boundary = 0.0
+    assert not fe._batchable(members)
