@@ -292,8 +292,17 @@ def _time(fn, reps, stream):
     return a.elapsed_time(b) / reps * 1e-3
 
 
+def normwise(x, ref) -> float:
+    """max |x - ref| / max |ref| of two device tensors, in double precision."""
+    d = (x.double() - ref.double()).abs().max()
+    return float(d / ref.double().abs().max())
+
+
 def extra_configs(dev, hbm_peak):
-    """The other workloads, each timed with CUDA events (seconds per call)."""
+    """The other workloads, each timed with CUDA events (seconds per call),
+    and the measured error of each FP32 workload: its FP32 result against
+    the FP64 run of the same workload on the GPU (whose kernels match the
+    FP64 oracle to 1e-12 in the parity tests), normwise."""
     import numpy as np
     import torch
 
@@ -306,7 +315,6 @@ def extra_configs(dev, hbm_peak):
     h = inputs.heat3d(n=N3)
     g = Grid((N3,) * 3, inputs.OFFSETS_7PT, [0.4] + [0.1] * 6, periodic=True, dtype=torch.float64, device=dev)
     g.set_field(h.u0)
-    del h
     t = _time(lambda: abi.stencil_step(g.h, SWEEPS, s), 2, s)
     per = t / SWEEPS
     glups = N3 ** 3 * SWEEPS / t / 1e9
@@ -314,7 +322,18 @@ def extra_configs(dev, hbm_peak):
                          "hbm_gbs": 16 * N3 ** 3 / per / 1e9, "hbm_frac": 16 * N3 ** 3 / per / 1e9 / hbm_peak,
                          "bound": "alu", "alu_peak_glups": FP64_INSTR_PER_S / 7 / 1e9,
                          "alu_frac": glups / (FP64_INSTR_PER_S / 7 / 1e9), "kernel": g.kernel}
+    # FP32 error of the workload (100 sweeps from u0) against FP64
+    g.set_field(h.u0)
+    g.step(SWEEPS, s)
+    g32 = Grid((N3,) * 3, inputs.OFFSETS_7PT, [0.4] + [0.1] * 6, periodic=True, dtype=torch.float32, device=dev)
+    g32.set_field(h.u0)
+    g32.step(SWEEPS, s)
+    torch.cuda.synchronize()
+    out["heat3d_f32_error"] = {"normwise_vs_fp64": normwise(g32.current(), g.current()), "steps": SWEEPS,
+                               "grid": [N3] * 3, "bound_tested": 1e-5}
+    g32.close()
     g.close()
+    del h
     torch.cuda.empty_cache()
     # heat2d FP64 256^2 Dirichlet, 100 steps
     u0 = inputs.heat2d()
@@ -346,6 +365,22 @@ def extra_configs(dev, hbm_peak):
     out["wave3d_f32"] = {"glups": N3 ** 3 * 1000 / t / 1e9, "us_per_step": per * 1e6,
                          "hbm_gbs": 16 * N3 ** 3 / per / 1e9, "hbm_frac": 16 * N3 ** 3 / per / 1e9 / hbm_peak,
                          "kernel": g.kernel, "bytes_per_point": 16}
+    # FP32 error of the full run (1000 steps from rest) against FP64
+    wv = inputs.wave3d(n=N3, steps=1000)
+    z = np.zeros((N3,) * 3, dtype=np.float32)
+    g.set_levels(z, z)
+    g.set_step_index(0)
+    g.step(1000, s)
+    g64 = Grid((N3,) * 3, offs, alpha, beta, periodic=False, dtype=torch.float64, time_levels=2, device=dev)
+    g64.set_coeff(wv.m)
+    g64.set_levels(z, z)
+    g64.set_source(wv.src, wv.amps)
+    del wv, z
+    g64.step(1000, s)
+    torch.cuda.synchronize()
+    out["wave3d_f32_error"] = {"normwise_vs_fp64": normwise(g.current(), g64.current()), "steps": 1000,
+                               "grid": [N3] * 3, "bound_tested": 1e-3, "fp64_kernel": g64.kernel}
+    g64.close()
     g.close()
     torch.cuda.empty_cache()
     # variable-coefficient forward + adjoint, 256^3, 200 steps, ckpt 20
@@ -395,6 +430,31 @@ def extra_configs(dev, hbm_peak):
                             "kernel": g.kernel}
     g.close()
     del p
+    torch.cuda.empty_cache()
+    # FP32 errors of the forward, lambda_0 and the gradient (200 steps,
+    # checkpoint every 20) against FP64
+    v = inputs.varcoef3d(n=256)
+    res = {}
+    for dt in (torch.float32, torch.float64):
+        gg = Grid((256,) * 3, inputs.OFFSETS_7PT, [1.0] + [0.0] * 6, [-6.0] + [1.0] * 6, dtype=dt, device=dev)
+        pp = VarCoefProblem(gg, 200, 20)
+        pp.forward(v.u0, v.kappa, s)
+        torch.cuda.synchronize()
+        uT = gg.current().clone()
+        lam0, gk, loss = pp.backward_from(target=v.target, stream=s)
+        torch.cuda.synchronize()
+        res[dt] = (uT, lam0.clone(), gk.clone(), float(loss[0]))
+        gg.close()
+        del pp
+    del v
+    a32, a64 = res[torch.float32], res[torch.float64]
+    out["varcoef3d_f32_error"] = {"forward_normwise_vs_fp64": normwise(a32[0], a64[0]),
+                                  "lambda0_normwise_vs_fp64": normwise(a32[1], a64[1]),
+                                  "gradient_normwise_vs_fp64": normwise(a32[2], a64[2]),
+                                  "loss_rel_vs_fp64": abs(a32[3] - a64[3]) / abs(a64[3]),
+                                  "steps": 200, "ckpt_every": 20, "grid": [256] * 3,
+                                  "bounds_tested": {"forward": 1e-5, "lambda0": 1e-3, "gradient": 1e-3}}
+    del res, a32, a64
     torch.cuda.empty_cache()
     # the same diffusion in conservative face-averaged form (one thread per
     # point), 256^3 FP32, 200 steps, checkpoint every 20
@@ -454,6 +514,14 @@ def extra_configs(dev, hbm_peak):
         err = max(err, float((a32 - a64).abs().max() / a64.abs().max()))
     out["batch2d_f32"].update({"plain_f64_ms_per_run": t64 * 1e3, "speedup_vs_plain_f64": t64 / t,
                                "max_normwise_err_vs_plain_f64": err})
+    # actual DRAM bytes of one 50-step launch (ncu counters of the committed
+    # capture, valid while k_batch.cu is unchanged): temporal blocking keeps
+    # tiles in shared memory for several steps, so they are far below the
+    # nominal 8 bytes per point and step
+    tr = ncu_traffic("batch2d_f32", source_sha("k_batch.cu"))
+    out["batch2d_f32"].update({"nominal_bytes_per_run": 8 * npts * 50, "dram_bytes_per_run": tr,
+                               "dram_gbs": tr / t / 1e9 if tr else None,
+                               "dram_frac": tr / t / 1e9 / hbm_peak if tr else None})
     bp.close()
     bt.close()
     del bp, bt
@@ -563,54 +631,80 @@ def _fe_config(p):
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(target_s: float = 15.0):
-    """The oracle on the host cores: 7-point periodic sweeps of a slab of the
-    512^3 workload (all 512x512 points of nz planes), double precision."""
+def cpu_baseline(target_s: float = 12.0, single_s: float = 6.0):
+    """The oracle on the host cores: 7-point periodic sweeps of the 512^3
+    workload field, double precision, on resident arrays (no copies in the
+    timed region), with OpenMP over every core in the affinity mask; and the
+    same oracle single-threaded on a slab of the field (all 512x512 points of
+    a few planes), whose result must equal the multi-threaded one bit for bit
+    (the sweep has no reductions, so the thread count cannot change it)."""
     import numpy as np
 
     import oracle
     from paper_2512_19851_gb300 import inputs
 
     cores = oracle.default_threads()
-    u = inputs.heat3d(n=N3).u0
+    u = np.ascontiguousarray(inputs.heat3d(n=N3).u0, dtype=np.float64)
+    tmp = np.empty_like(u)
     w = [0.4] + [0.1] * 6
     t = time.perf_counter()
-    oracle.sweep_const(u, inputs.OFFSETS_7PT, w, True, 0.0, 1, threads=cores)
-    rate = u.size / (time.perf_counter() - t)
-    sweeps = int(max(2, min(100, target_s * rate / u.size)))
+    oracle.sweep_const_into(u, tmp, inputs.OFFSETS_7PT, w, True, 0.0, 2, threads=cores)
+    rate = 2 * u.size / (time.perf_counter() - t)
+    sweeps = int(max(2, min(100, target_s * rate / u.size))) // 2 * 2
     t = time.perf_counter()
-    oracle.sweep_const(u, inputs.OFFSETS_7PT, w, True, 0.0, sweeps, threads=cores)
+    oracle.sweep_const_into(u, tmp, inputs.OFFSETS_7PT, w, True, 0.0, sweeps, threads=cores)
     dt = time.perf_counter() - t
-    del np
+    # single thread on a slab sized from the multi-threaded rate
+    nz = int(max(2, min(N3, single_s * rate / cores / (N3 * N3) / 2)))
+    slab = np.ascontiguousarray(u[:nz])
+    one = slab.copy()
+    t1 = np.empty_like(slab)
+    t = time.perf_counter()
+    oracle.sweep_const_into(one, t1, inputs.OFFSETS_7PT, w, True, 0.0, 2, threads=1)
+    dt1 = time.perf_counter() - t
+    many = slab.copy()
+    oracle.sweep_const_into(many, t1, inputs.OFFSETS_7PT, w, True, 0.0, 2, threads=cores)
     return {"value": u.size * sweeps / dt / 1e9, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
-            "sample": f"{sweeps} periodic 7-point sweeps of the 512^3 heat3d field, FP64, {dt:.1f} s"}
+            "sample": f"{sweeps} periodic 7-point sweeps of the 512^3 heat3d field, FP64, resident arrays, "
+                      f"{cores} OpenMP threads, {dt:.1f} s",
+            "single_thread": {"value": 2 * slab.size / dt1 / 1e9, "unit": "GLUP/s", "cores": 1,
+                              "sample": f"2 periodic sweeps of a {nz}x512x512 slab, FP64, {dt1:.1f} s",
+                              "bitwise_equal_to_multithread": bool(np.array_equal(one, many))}}
 
 
 def run_reference(args):
-    """The CPU oracle as the reference arm, on rank 0 only."""
+    """The CPU oracle as the reference arm, on rank 0 only: per step, two
+    periodic 7-point sweeps of a slab of the 512^3 workload (all 512x512
+    points of nz planes, nz sized so the whole run takes about two minutes),
+    on resident arrays, OpenMP over every core."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    import numpy as np
+
     import oracle
     from paper_2512_19851_gb300 import inputs
 
     cores = oracle.default_threads()
     w = [0.4] + [0.1] * 6
-    probe = inputs.heat3d(shape=(8, N3, N3)).u0
+    probe = np.ascontiguousarray(inputs.heat3d(shape=(16, N3, N3)).u0)
+    ptmp = np.empty_like(probe)
     t = time.perf_counter()
-    oracle.sweep_const(probe, inputs.OFFSETS_7PT, w, True, 0.0, 1, threads=cores)
-    rate = probe.size / (time.perf_counter() - t)
+    oracle.sweep_const_into(probe, ptmp, inputs.OFFSETS_7PT, w, True, 0.0, 2, threads=cores)
+    rate = 2 * probe.size / (time.perf_counter() - t)
     budget = 120.0 / max(1, args.steps + args.warmup)  # seconds per step
-    nz = int(max(1, min(N3, budget * rate / (N3 * N3))))
-    slab = inputs.heat3d(shape=(nz, N3, N3)).u0
+    nz = int(max(2, min(N3, budget * rate / (2 * N3 * N3))))
+    slab = np.ascontiguousarray(inputs.heat3d(shape=(nz, N3, N3)).u0)
+    tmp = np.empty_like(slab)
     for _ in range(args.warmup):
-        oracle.sweep_const(slab, inputs.OFFSETS_7PT, w, True, 0.0, 1, threads=cores)
+        oracle.sweep_const_into(slab, tmp, inputs.OFFSETS_7PT, w, True, 0.0, 2, threads=cores)
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle.sweep_const(slab, inputs.OFFSETS_7PT, w, True, 0.0, 1, threads=cores)
+        oracle.sweep_const_into(slab, tmp, inputs.OFFSETS_7PT, w, True, 0.0, 2, threads=cores)
     dt = time.perf_counter() - t
-    val = slab.size * args.steps / dt / 1e9
-    sample = f"per step: 1 periodic 7-point sweep of a {nz}x512x512 slab of the 512^3 workload, FP64"
+    val = 2 * slab.size * args.steps / dt / 1e9
+    sample = (f"per step: 2 periodic 7-point sweeps of a {nz}x512x512 slab of the 512^3 workload, FP64, "
+              f"resident arrays")
     line = {"impl": "reference", "metric": "grid-point updates/s (GLUP/s) and % of HBM roofline, forward and adjoint",
             "value": val, "unit": "GLUP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",

@@ -210,6 +210,9 @@ st_status stencil_current(st_grid_t g, int* slot);
 st_status stencil_set_current(st_grid_t g, int slot);
 
 /*
+ * Defined by: the leapfrog acoustic-wave workload (a Ricker-wavelet point
+ * source injected at the centre cell every step), which extends (1) to the
+ * two-level form (3); the paper's own workloads have no source term.
  * Point source of the leapfrog form (3): amplitudes[t] is added at interior
  * point `index` (ndim int64, C order) by the step that computes level t+1,
  * where t is the handle's step counter.  Steps past `count` add nothing.
@@ -246,6 +249,11 @@ st_status stencil_snapshot(st_grid_t g, void* dst, int64_t* step_out, void* stre
 st_status stencil_restore(st_grid_t g, const void* src, int64_t step, void* stream);
 
 /*
+ * Defined by: Sec. III-A, Example 1 (the loop that applies one stencil
+ * expression per iteration and swaps the two arrays, `u1, u2 = u2, u1`) and
+ * Sec. III-C "DAG execution" (a node runs in two phases: the ghost data of
+ * its input arrays is brought up to date, only where the generation epochs
+ * differ, then the kernel runs).  nsteps steps are nsteps such nodes.
  * Advance nsteps >= 0 steps on `stream`: refresh stale ghosts, then sweep,
  * each launch writing the other slot.  When stencil_tune chose two-step
  * passes (the constant symmetric 7-point star, FP32, no source) a launch
@@ -290,11 +298,19 @@ st_status stencil_tune_config(st_grid_t g, int* cfg);
 st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* host_uT,
                            void* stream);
 
-/* Synchronise the last stream used by this handle and report device-side
+/* Defined by: Sec. III-B "Execution graph" (the frontend's sync call hands
+ * the recorded work to the backend and returns when it has run) and Sec.
+ * II-A "Asynchronous detection of kernel completion" (the host learns of a
+ * kernel's completion without blocking other work until it asks).
+ * Synchronise the last stream used by this handle and report device-side
  * errors (ST_ERR_DEVICE_TIMEOUT, ST_ERR_BOUNDS); clears the status word. */
 st_status stencil_sync(st_grid_t g);
 
 /*
+ * Defined by: the FP64 residual and norm reductions that the workloads keep
+ * in double precision on the GPU (sums and error norms of a field, the
+ * loss of the adjoint workload); the paper's Laplace and cavity programs
+ * read results back with get() and have no reduction of their own.
  * Interior reductions in double precision over a (and b, if not NULL), two
  * buffers in this grid's layout and dtype:
  *   dev_out[0] = sum (a - b), dev_out[1] = sum (a - b)^2, dev_out[2] = max |a - b|.
@@ -317,9 +333,10 @@ st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_
  * other allocating routine.
  *   Same arguments and results as stencil_reduce (a, b: field-layout buffers
  *   of the grid's dtype, b may be NULL; dev_out: 3 doubles in device memory).
- *   Limit: at most 2^28 = 268435456 interior points (one partial per 65536
- *   points, 4096 partials = 96 KB held by every GPU that loads the library
- *   until the process exits); larger grids get ST_ERR_ARG and a message.
+ *   Scratch: a static array of 4096 block partials (96 KB, held by every
+ *   GPU that loads the library until the process exits).  The blocks walk
+ *   the interior rows in a grid-stride loop, so grids of every size fit it
+ *   and none is rejected.
  *   The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.
@@ -331,6 +348,9 @@ st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_
 st_status stencil_reduce_noalloc(st_grid_t g, const void* a, const void* b, double* dev_out, void* stream);
 
 /*
+ * Defined by: the adjoint workload's loss L = 0.5 ||u_T - u_target||^2, whose
+ * gradient dL/du_T = u_T - u_target seeds the transpose sweep; no
+ * counterpart in the paper.
  * Loss residual: lambda = u - target on the interior (lambda's ghosts set to
  * 0) and dev_loss[0] = 0.5 * sum (u - target)^2 in double precision.
  */
@@ -338,6 +358,11 @@ st_status stencil_residual(st_grid_t g, const void* u, const void* target, void*
                            double* dev_loss, void* stream);
 
 /*
+ * Defined by: the adjoint workload (a hand-written transposed-stencil sweep
+ * giving the gradients of a loss of u_T with respect to u_0 and to the
+ * per-cell coefficients of (2), with the forward states checkpointed every
+ * m steps and recomputed segment by segment); the paper differentiates
+ * nothing, so the operation is the exact transpose of the linear map (1)-(2).
  * Adjoint with checkpoint-every-m recomputation (one time level only).
  * Workspace bytes for a run of nsteps with checkpoints every ckpt_every steps:
  * ceil(nsteps/ckpt_every) checkpoints, ckpt_every-1 levels for the
@@ -347,13 +372,16 @@ st_status stencil_residual(st_grid_t g, const void* u, const void* target, void*
  */
 st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int ckpt_every, size_t* bytes);
 
-/* Forward nsteps from the current level, storing u at t = 0, m, 2m, ... and
+/* Defined by: the adjoint workload's checkpoint-every-m forward run (see
+ * stencil_adjoint_workspace); each step is the sweep of stencil_step.
+ * Forward nsteps from the current level, storing u at t = 0, m, 2m, ... and
  * the inner levels of the last segment in `workspace` (device,
  * >= stencil_adjoint_workspace bytes, 16-byte aligned). */
 st_status stencil_step_ckpt(st_grid_t g, int nsteps, int ckpt_every, void* workspace,
                             void* stream);
 
 /*
+ * Defined by: the adjoint workload (see stencil_adjoint_workspace).
  * Reverse pass of a run recorded by stencil_step_ckpt with the same nsteps
  * and ckpt_every (it reads the workspace and never writes the checkpoints or
  * the kept levels, so it may run again on the same record).  lambda (in: dL/du_T, out: dL/du_0) and lambda_tmp are
@@ -373,6 +401,13 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int ckpt_every, const void* w
 /* ----------------------------------------------------------------------------
  * Batched form: many independent 2D grids with the same neighbour offsets,
  * their own sizes and weights, advanced by one persistent launch per call.
+ * Defined by: the batched workload (many independent grids of uneven sizes
+ * swept in one persistent launch under a captured CUDA graph, with the tile
+ * shape, threads per block and temporal-blocking depth picked by an
+ * autotuner); its nearest counterpart in the paper is node fusion (Sec.
+ * III-B "Node fusion": independent updates of arrays of one output shape
+ * compiled into one kernel to save launches), which the frontend lowers
+ * onto this form.
  * --------------------------------------------------------------------------*/
 
 /*

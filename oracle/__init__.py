@@ -137,6 +137,28 @@ def sweep_const(u0, offsets, weights, periodic: bool, bc_value: float, nsteps: i
     return u
 
 
+def sweep_const_into(u, tmp, offsets, weights, periodic: bool, bc_value: float, nsteps: int,
+                     threads: int | None = None):
+    """:func:`sweep_const` on caller-owned arrays, for timing the oracle on a
+    resident field: ``u`` (C-contiguous float64 or float32) holds u_0 on entry
+    and u_nsteps on return, ``tmp`` (same shape and dtype) is scratch.  The
+    arithmetic is the same C loop; only the copies of the wrapper are left
+    out (an even nsteps also skips the C loop's final copy)."""
+    if not (u.flags.c_contiguous and tmp.flags.c_contiguous) or u.dtype != tmp.dtype or u.shape != tmp.shape:
+        raise ValueError("u and tmp: C-contiguous arrays of one shape and dtype")
+    dt = u.dtype.type
+    nz, ny, nx = _shape3(u.shape)
+    off = _off3(offsets, u.ndim)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    if w.shape[0] != off.shape[0] or off.shape[0] > 64:
+        raise ValueError("one weight per offset, at most 64 points")
+    f = _fn(dt, "orc_sweep_const")
+    f.argtypes = [I64, I64, I64, INT, VP, VP, INT, DBL, INT, VP, VP, INT]
+    f(nz, ny, nx, off.shape[0], _ptr(off), _ptr(w), int(bool(periodic)), float(bc_value),
+      int(nsteps), _ptr(u), _ptr(tmp), int(threads or default_threads()))
+    return u
+
+
 def varcoef7_forward(u0, kappa, periodic: bool, bc_value: float, nsteps: int,
                      store_states: bool = False, dtype=np.float64, threads: int | None = None):
     """Per-cell 7-point diffusion; returns u_nsteps (and u_0..u_nsteps if asked)."""

@@ -116,8 +116,7 @@ static st_status ensure_scratch(st_grid_t g)
 {
     if (g->scratch) return ST_OK;
     ST_CUDA_TRY(cudaGetDevice(&g->device));
-    const int64_t rows = g->g.nz * g->g.ny;
-    g->red_blocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, rows));
+    g->red_blocks = reduce_blocks(g->g, 4096);
     if (cudaMalloc(&g->d_status, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&g->d_partials, sizeof(double) * 3 * g->red_blocks) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -292,6 +291,12 @@ st_status stencil_create_conservative(st_grid_t* out, int ndim, const int64_t* d
     st_grid_t g = *out;
     g->fam.kind = FAM_CONS;
     g->fam.name = "cons_face_avg_point";
+    // 3D grids sweep on the staged pipeline (variant 1), 2D grids and the
+    // transposed step on the one-thread-per-column kernels
+    if (star3d_cons_supported(g->g)) {
+        g->fam.variant = 1;
+        g->fam.name = "cons_face_avg_bulk";
+    }
     return ST_OK;
 }
 
@@ -525,13 +530,24 @@ static SweepArgs sweep_args(st_grid_t g, const void* in, void* out, int64_t step
     return a;
 }
 
+// Ghost cells of the coefficient field: 0, except for the conservative
+// operator, whose staged kernel reads a Dirichlet ghost face's coefficient
+// as (kappa_p + kappa_ghost) / 2 and so needs each ghost to mirror its
+// interior neighbour (then the face takes kappa_p exactly).
+static cudaError_t coeff_ghosts(st_grid_t g, cudaStream_t s)
+{
+    if (g->fam.kind == FAM_CONS) return launch_mirror_ghosts(g->g.esize, g->buf[ST_SLOT_COEFF], g->g, s);
+    return launch_fill_ghosts(g->g.esize, g->buf[ST_SLOT_COEFF], g->g, 0.0, s);
+}
+
 static st_status refresh_ghosts(st_grid_t g, cudaStream_t s)
 {
     for (int slot = 0; slot < 3; ++slot) {
         if (!g->stale[slot] || !g->buf[slot]) continue;
-        if ((g->bc == ST_DIRICHLET && !g->caller_ghosts) || slot == ST_SLOT_COEFF) {
-            const double v = (slot == ST_SLOT_COEFF) ? 0.0 : g->bc_value;
-            ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, g->buf[slot], g->g, v, s));
+        if (slot == ST_SLOT_COEFF) {
+            ST_CUDA_TRY(coeff_ghosts(g, s));
+        } else if (g->bc == ST_DIRICHLET && !g->caller_ghosts) {
+            ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, g->buf[slot], g->g, g->bc_value, s));
         }
         g->stale[slot] = false;
     }
@@ -927,7 +943,7 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     cudaStream_t s = (cudaStream_t)stream;
     g->last = s;
     if (g->stale[ST_SLOT_COEFF] && g->buf[ST_SLOT_COEFF]) {
-        ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, g->buf[ST_SLOT_COEFF], g->g, 0.0, s));
+        ST_CUDA_TRY(coeff_ghosts(g, s));
         g->stale[ST_SLOT_COEFF] = false;
     }
     ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, lambda, g->g, 0.0, s));

@@ -24,6 +24,27 @@ st_status cuda_fail(cudaError_t e, const char* what);
         if (_e != cudaSuccess) return ::st::cuda_fail(_e, #expr); \
     } while (0)
 
+// Launch kernel k on stream s with a programmatic dependency on the previous
+// kernel of the stream: k's CTAs may be scheduled (and run their prologue)
+// while that kernel finishes, which hides the launch gap between the
+// dependent sweeps of a step sequence.  k must call ptx::griddep_wait()
+// before touching global memory that earlier work reads or writes.
+template <typename... KP, typename... A>
+cudaError_t launch_dependent(void (*k)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // ---------------------------------------------------------------------------
 // Padded-grid geometry.  2D grids are stored as one plane: nz = 1, no z ghosts.
 // ---------------------------------------------------------------------------
@@ -78,6 +99,9 @@ cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_i
 cudaError_t launch_fill_ghosts(int esize, void* buf, const Geom& g, double value, cudaStream_t s);
 cudaError_t launch_mirror_ghosts(int esize, void* buf, const Geom& g, cudaStream_t s);
 cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int dir, cudaStream_t s);
+// Grid size of the reduction kernels for grid g: the blocks resident at once
+// on this GPU, at most max_blocks and at most one per eight interior rows.
+int reduce_blocks(const Geom& g, int max_blocks);
 cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g, double* partials,
                           int nblocks, double* out, int mode, void* lam_out, cudaStream_t s);
 

@@ -91,6 +91,11 @@ bool wave_supports(const FamilyDesc& d);
 cudaError_t launch_wave(const Family& f, const SweepArgs& a, cudaStream_t s);
 bool tile2d_supports(const FamilyDesc& d, int* variant, const char** name);
 cudaError_t launch_cons_sweep(const Family& f, const SweepArgs& a, cudaStream_t s);
+// The conservative operator's 3D forward on the staged pipeline of k_star1
+// (variant 1 of FAM_CONS); its coefficient field's ghosts must mirror the
+// interior (see stencil_create_conservative).
+bool star3d_cons_supported(const Geom& g);
+cudaError_t launch_star3d_cons(const Family& f, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_cons_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

@@ -321,6 +321,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
     if (K == 2)
         for (size_t i = threadIdx.x; i < (size_t)A_RING * P.ring_elems; i += blockDim.x) mring[i] = T(0);
     __syncthreads();
+    ptx::griddep_wait();  // earlier kernels of the stream wrote our inputs / read our outputs
+    ptx::griddep_trigger();
     const uint32_t rowb = (uint32_t)(P.pitch * sizeof(T));
     const bool grad = P.grad != 0;
 
@@ -910,9 +912,8 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
         attr = true;
     }
     const int grid = (int)std::min<int64_t>(P.flat ? (int64_t)P.nyt * P.nz : P.units, adj_sm_count());
-    fn<<<grid, (c.CW + 1) * 32, smem, s>>>((const T*)a.lam_in, (T*)a.lam_out, (const T*)a.kappa, (const T*)a.u,
-                                           (const T*)a.u2, a.gk, P);
-    return cudaGetLastError();
+    return launch_dependent(fn, dim3(grid), dim3((c.CW + 1) * 32), smem, s, (const T*)a.lam_in, (T*)a.lam_out,
+                            (const T*)a.kappa, (const T*)a.u, (const T*)a.u2, a.gk, P);
 }
 
 }  // namespace

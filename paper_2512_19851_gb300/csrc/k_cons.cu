@@ -19,6 +19,7 @@
 // in-plane neighbours coming through L1/L2, so DRAM sees about one read of u
 // and kappa and one write per point.
 #include "families.cuh"
+#include "ptx.cuh"
 
 namespace st {
 
@@ -80,6 +81,8 @@ template <typename T, bool PER, bool THREE>
 __global__ void __launch_bounds__(256) k_cons_sweep(const T* __restrict__ in, T* __restrict__ out,
                                                     const T* __restrict__ kap, const __grid_constant__ GenParams P)
 {
+    ptx::griddep_wait();
+    ptx::griddep_trigger();
     const int64_t x = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int64_t y = (int64_t)blockIdx.y * 8 + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
@@ -139,6 +142,8 @@ __global__ void __launch_bounds__(256) k_cons_adjoint(const T* __restrict__ u, c
                                                       T* __restrict__ lout, const T* __restrict__ kap,
                                                       double* __restrict__ gk, const __grid_constant__ GenParams P)
 {
+    ptx::griddep_wait();
+    ptx::griddep_trigger();
     const int64_t x = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int64_t y = (int64_t)blockIdx.y * 8 + threadIdx.y;
     if (x >= P.nx || y >= P.ny) return;
@@ -211,12 +216,10 @@ cudaError_t sweep_t(const Family& f, const SweepArgs& a, cudaStream_t s)
     T* o = (T*)a.out;
     const bool three = f.g.ndim == 3;
     if (f.periodic)
-        three ? k_cons_sweep<T, true, true><<<g, b, 0, s>>>(in, o, k, P)
-              : k_cons_sweep<T, true, false><<<g, b, 0, s>>>(in, o, k, P);
-    else
-        three ? k_cons_sweep<T, false, true><<<g, b, 0, s>>>(in, o, k, P)
-              : k_cons_sweep<T, false, false><<<g, b, 0, s>>>(in, o, k, P);
-    return cudaGetLastError();
+        return three ? launch_dependent(k_cons_sweep<T, true, true>, g, b, 0, s, in, o, k, P)
+                     : launch_dependent(k_cons_sweep<T, true, false>, g, b, 0, s, in, o, k, P);
+    return three ? launch_dependent(k_cons_sweep<T, false, true>, g, b, 0, s, in, o, k, P)
+                 : launch_dependent(k_cons_sweep<T, false, false>, g, b, 0, s, in, o, k, P);
 }
 
 template <typename T>
@@ -230,12 +233,10 @@ cudaError_t adjoint_t(const Family& f, const AdjointArgs& a, cudaStream_t s)
     T* o = (T*)a.lam_out;
     const bool three = f.g.ndim == 3;
     if (f.periodic)
-        three ? k_cons_adjoint<T, true, true><<<g, b, 0, s>>>(u, l, o, k, a.gk, P)
-              : k_cons_adjoint<T, true, false><<<g, b, 0, s>>>(u, l, o, k, a.gk, P);
-    else
-        three ? k_cons_adjoint<T, false, true><<<g, b, 0, s>>>(u, l, o, k, a.gk, P)
-              : k_cons_adjoint<T, false, false><<<g, b, 0, s>>>(u, l, o, k, a.gk, P);
-    return cudaGetLastError();
+        return three ? launch_dependent(k_cons_adjoint<T, true, true>, g, b, 0, s, u, l, o, k, a.gk, P)
+                     : launch_dependent(k_cons_adjoint<T, true, false>, g, b, 0, s, u, l, o, k, a.gk, P);
+    return three ? launch_dependent(k_cons_adjoint<T, false, true>, g, b, 0, s, u, l, o, k, a.gk, P)
+                 : launch_dependent(k_cons_adjoint<T, false, false>, g, b, 0, s, u, l, o, k, a.gk, P);
 }
 
 }  // namespace
@@ -244,6 +245,7 @@ cudaError_t launch_cons_sweep(const Family& f, const SweepArgs& a, cudaStream_t 
 {
     const GenParams& P = f.gp;
     if (P.nz * P.ny * P.nx == 0) return cudaSuccess;
+    if (f.variant == 1) return launch_star3d_cons(f, a, s);
     return f.g.esize == 8 ? sweep_t<double>(f, a, s) : sweep_t<float>(f, a, s);
 }
 

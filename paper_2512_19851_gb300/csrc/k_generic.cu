@@ -8,6 +8,7 @@
 // stencil the specialised families do not cover and the "plain launch"
 // baseline of the batched workload.
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace st {
 
@@ -39,6 +40,8 @@ __global__ void __launch_bounds__(256)
 k_sweep_generic(const T* __restrict__ in, T* out, const T* prev, const T* __restrict__ kappa,
                 const __grid_constant__ GenParams P)
 {
+    ptx::griddep_wait();  // the previous sweep wrote `in` and read `out`
+    ptx::griddep_trigger();
     const int64_t x = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int64_t y = (int64_t)blockIdx.y * 8 + threadIdx.y;
     const int64_t z = blockIdx.z;
@@ -75,6 +78,8 @@ k_adjoint_generic(const T* __restrict__ u, const T* __restrict__ lam, T* __restr
                   const T* __restrict__ kappa, double* __restrict__ gk,
                   const __grid_constant__ GenParams P)
 {
+    ptx::griddep_wait();
+    ptx::griddep_trigger();
     const int64_t x = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int64_t y = (int64_t)blockIdx.y * 8 + threadIdx.y;
     const int64_t z = blockIdx.z;
@@ -109,6 +114,8 @@ k_adjoint_generic(const T* __restrict__ u, const T* __restrict__ lam, T* __restr
 template <typename T>
 __global__ void __launch_bounds__(256) k_fill_ghosts(T* __restrict__ buf, Geom g, T value)
 {
+    ptx::griddep_wait();
+    ptx::griddep_trigger();
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t zrows = 2 * g.rz * g.pny;  // rows of the z ghost planes
@@ -150,6 +157,8 @@ __device__ __forceinline__ int64_t mirror(int64_t i, int64_t n) { return i < 0 ?
 template <typename T>
 __global__ void __launch_bounds__(256) k_mirror_ghosts(T* __restrict__ buf, Geom g)
 {
+    ptx::griddep_wait();
+    ptx::griddep_trigger();
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t zrows = 2 * g.rz * g.pny;
@@ -226,10 +235,6 @@ __device__ Red3 block_red(Red3 v)
 // per-element work of an FP32 reduction stays on the FP32 pipe, because the
 // FP64 rate of this GPU is 1/64 of FP32.  Error-free transformations:
 // TwoSum (Knuth) for additions, fma for the exact product error.
-struct F2 {
-    float hi, lo;
-};
-
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
     s = a + b;
@@ -237,18 +242,29 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = (a - (s - bb)) + (b - bb);
 }
 
-__device__ __forceinline__ void f2_add(F2& acc, float x, float xlo)
+// The sum and the sum of squares are two independent compensated pairs that
+// take the same operations, so they run side by side in packed FP32x2
+// instructions (one instruction per pair; each lane rounds exactly as the
+// scalar operation would).  a - b is formed as fma(b, -1, a), which rounds
+// a - b once, as a subtraction does.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// (hi, lo) += x + xlo for both pairs at once: lane 0 is the sum, lane 1 the
+// sum of squares.  TwoSum of hi and x, then lo += err + xlo.
+__device__ __forceinline__ void f2_add2(float2& hi, float2& lo, float2 x, float2 xlo)
 {
-    float s, e;
-    two_sum(acc.hi, x, s, e);
-    acc.hi = s;
-    acc.lo += e + xlo;
+    const float2 s = p_add(hi, x);
+    const float2 bb = p_sub(s, hi);
+    const float2 e = p_add(p_sub(hi, p_sub(s, bb)), p_sub(x, bb));
+    hi = s;
+    lo = p_add(lo, p_add(e, xlo));
 }
 
 // Per-element accumulation: FP32 inputs use the compensated float pair,
 // FP64 inputs plain double.
 struct AccF {
-    F2 S{0.f, 0.f}, Q{0.f, 0.f};
+    float2 H{0.f, 0.f}, L{0.f, 0.f};  // (sum, sum of squares): high and low parts
     // max |d| kept exactly in single precision: |d| = |dh| + sign(dh) dl with
     // |dl| at most half the float spacing around dh, so ordering by |dh| first
     // and sign(dh) dl second orders the exact |d| (a rounding interval never
@@ -258,10 +274,9 @@ struct AccF {
     {
         float dh, dl;
         two_sum(av, -bv, dh, dl);  // d = dh + dl exactly
-        f2_add(S, dh, dl);
         const float p = dh * dh;
         const float pe = fmaf(dh, dh, -p);  // dh^2 = p + pe exactly
-        f2_add(Q, p, pe + 2.f * dh * dl);
+        f2_add2(H, L, make_float2(dh, p), make_float2(dl, pe + 2.f * dh * dl));
         const float A = fabsf(dh);
         const float sg = dh < 0.f ? -dl : dl;
         const bool gt = A > mA || (A == mA && sg > mS);
@@ -273,15 +288,14 @@ struct AccF {
     // same results
     __device__ __forceinline__ float add1(float av)
     {
-        f2_add(S, av, 0.f);
         const float p = av * av;
-        f2_add(Q, p, fmaf(av, av, -p));
+        f2_add2(H, L, make_float2(av, p), make_float2(0.f, fmaf(av, av, -p)));
         mA = fmaxf(mA, fabsf(av));
         return av;
     }
     __device__ __forceinline__ Red3 result() const
     {
-        return Red3{(double)S.hi + (double)S.lo, (double)Q.hi + (double)Q.lo, (double)mA + (double)mS};
+        return Red3{(double)H.x + (double)L.x, (double)H.y + (double)L.y, (double)mA + (double)mS};
     }
 };
 
@@ -317,9 +331,11 @@ struct VecOf<double> {
 // mode 0: d = a - b (b may be null); mode 1: also lam_out = d on the interior.
 // Each warp walks whole interior rows; each lane loads 16-byte vectors, four
 // per trip, so several loads are in flight (interior rows start 16-byte
-// aligned).  partials[3*block + {0,1,2}].
+// aligned).  The grid is sized to the blocks that are resident at once
+// (reduce_blocks), so there is no partial second wave.  partials[3*block +
+// {0,1,2}].
 template <typename T, bool HAS_B>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, HAS_B ? 3 : 4)
 k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b, Geom g, double* __restrict__ partials,
                  int mode, T* __restrict__ lam_out)
 {
@@ -331,13 +347,19 @@ k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b, Geom g, doubl
     const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t nxv = g.nx / N * N;  // vector part of a row
     typename VecOf<T>::Acc acc;
-    // rows < 2^32 (nz <= 65535, ny <= 2^24 ... checked on the host): 32-bit
-    // division, which does not go through the FP64 pipe as 64-bit division does
-    const uint32_t ny32 = (uint32_t)g.ny;
-    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; row < rows; row += wstride) {
-        const uint32_t z = (uint32_t)row / ny32;
-        const uint32_t y = (uint32_t)row - z * ny32;
-        const int64_t base = g.origin + (int64_t)z * g.plane + (int64_t)y * g.pitch;
+    // (z, y) of the warp's row, advanced by the stride's whole planes and
+    // remaining rows (no division inside the loop)
+    const int64_t row0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    int64_t z = row0 / g.ny, y = row0 - z * g.ny;
+    const int64_t sz = wstride / g.ny, sy = wstride - sz * g.ny;
+    for (int64_t row = row0; row < rows; row += wstride) {
+        const int64_t base = g.origin + z * g.plane + y * g.pitch;
+        z += sz;
+        y += sy;
+        if (y >= g.ny) {
+            y -= g.ny;
+            ++z;
+        }
         const T* ra = a + base;
         const T* rb = HAS_B ? b + base : nullptr;
         for (int64_t x0 = (int64_t)lane * N; x0 < nxv; x0 += (int64_t)32 * N * U) {
@@ -458,14 +480,12 @@ cudaError_t launch_generic_sweep(int esize, const void* in, void* out, const voi
                                  const void* kappa, const GenParams& P, cudaStream_t s)
 {
     if (P.nz * P.ny * P.nx == 0) return cudaSuccess;
-    dim3 grid = point_grid(P), block(32, 8);
+    const dim3 grid = point_grid(P), block(32, 8);
     if (esize == 8)
-        k_sweep_generic<double><<<grid, block, 0, s>>>((const double*)in, (double*)out,
-                                                       (const double*)prev, (const double*)kappa, P);
-    else
-        k_sweep_generic<float><<<grid, block, 0, s>>>((const float*)in, (float*)out,
-                                                      (const float*)prev, (const float*)kappa, P);
-    return cudaGetLastError();
+        return launch_dependent(k_sweep_generic<double>, grid, block, 0, s, (const double*)in, (double*)out,
+                                (const double*)prev, (const double*)kappa, P);
+    return launch_dependent(k_sweep_generic<float>, grid, block, 0, s, (const float*)in, (float*)out,
+                            (const float*)prev, (const float*)kappa, P);
 }
 
 cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_in, void* lam_out,
@@ -473,14 +493,12 @@ cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_i
                                    cudaStream_t s)
 {
     if (P.nz * P.ny * P.nx == 0) return cudaSuccess;
-    dim3 grid = point_grid(P), block(32, 8);
+    const dim3 grid = point_grid(P), block(32, 8);
     if (esize == 8)
-        k_adjoint_generic<double><<<grid, block, 0, s>>>((const double*)u_t, (const double*)lam_in,
-                                                         (double*)lam_out, (const double*)kappa, gk, P);
-    else
-        k_adjoint_generic<float><<<grid, block, 0, s>>>((const float*)u_t, (const float*)lam_in,
-                                                        (float*)lam_out, (const float*)kappa, gk, P);
-    return cudaGetLastError();
+        return launch_dependent(k_adjoint_generic<double>, grid, block, 0, s, (const double*)u_t,
+                                (const double*)lam_in, (double*)lam_out, (const double*)kappa, gk, P);
+    return launch_dependent(k_adjoint_generic<float>, grid, block, 0, s, (const float*)u_t, (const float*)lam_in,
+                            (float*)lam_out, (const float*)kappa, gk, P);
 }
 
 cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int dir, cudaStream_t s)
@@ -510,10 +528,8 @@ cudaError_t launch_fill_ghosts(int esize, void* buf, const Geom& g, double value
     const int64_t want = (cells + 255) / 256;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
     if (esize == 8)
-        k_fill_ghosts<double><<<blocks, 256, 0, s>>>((double*)buf, g, value);
-    else
-        k_fill_ghosts<float><<<blocks, 256, 0, s>>>((float*)buf, g, (float)value);
-    return cudaGetLastError();
+        return launch_dependent(k_fill_ghosts<double>, dim3(blocks), dim3(256), 0, s, (double*)buf, g, value);
+    return launch_dependent(k_fill_ghosts<float>, dim3(blocks), dim3(256), 0, s, (float*)buf, g, (float)value);
 }
 
 cudaError_t launch_mirror_ghosts(int esize, void* buf, const Geom& g, cudaStream_t s)
@@ -522,15 +538,54 @@ cudaError_t launch_mirror_ghosts(int esize, void* buf, const Geom& g, cudaStream
     const int64_t want = (cells + 255) / 256;
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
     if (esize == 8)
-        k_mirror_ghosts<double><<<blocks, 256, 0, s>>>((double*)buf, g);
-    else
-        k_mirror_ghosts<float><<<blocks, 256, 0, s>>>((float*)buf, g);
-    return cudaGetLastError();
+        return launch_dependent(k_mirror_ghosts<double>, dim3(blocks), dim3(256), 0, s, (double*)buf, g);
+    return launch_dependent(k_mirror_ghosts<float>, dim3(blocks), dim3(256), 0, s, (float*)buf, g);
+}
+
+namespace {
+// Blocks of one reduction kernel instance resident at once on this GPU.
+int resident_blocks(const void* fn)
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, 0) != cudaSuccess || occ <= 0) {
+        (void)cudaGetLastError();
+        occ = 1;
+    }
+    return nsm * occ;
+}
+
+int64_t blocks_by_rows(const Geom& g) { return std::max<int64_t>(1, (g.nz * g.ny + 7) / 8); }
+}  // namespace
+
+int reduce_blocks(const Geom& g, int max_blocks)
+{
+    static int resident = 0;  // the most blocks any reduction kernel instance keeps resident
+    if (resident == 0)
+        for (const void* f : {(const void*)k_reduce_partial<float, true>, (const void*)k_reduce_partial<float, false>,
+                              (const void*)k_reduce_partial<double, true>, (const void*)k_reduce_partial<double, false>})
+            resident = std::max(resident, resident_blocks(f));
+    return (int)std::min<int64_t>(std::min<int64_t>(resident, max_blocks), blocks_by_rows(g));
 }
 
 cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g, double* partials,
                           int nblocks, double* out, int mode, void* lam_out, cudaStream_t s)
 {
+    // the grid: the blocks of this kernel instance that are resident at once
+    // (no partial second wave), within the caller's partials
+    static int res[2][2] = {{0, 0}, {0, 0}};
+    const int di = esize == 8, bi = b != nullptr;
+    if (res[di][bi] == 0) {
+        const void* fns[2][2] = {{(const void*)k_reduce_partial<float, false>, (const void*)k_reduce_partial<float, true>},
+                                 {(const void*)k_reduce_partial<double, false>, (const void*)k_reduce_partial<double, true>}};
+        res[di][bi] = resident_blocks(fns[di][bi]);
+    }
+    nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(nblocks, res[di][bi]), blocks_by_rows(g)));
     if (esize == 8) {
         if (b)
             k_reduce_partial<double, true><<<nblocks, 256, 0, s>>>((const double*)a, (const double*)b, g, partials,

@@ -140,6 +140,8 @@ k_star2(const float* __restrict__ in, float* __restrict__ out, const __grid_cons
     const float ghost = PERIODIC ? 0.f : P.bcv;
     for (size_t i = threadIdx.x; i < (size_t)P2_RING * P.ring_elems; i += blockDim.x) ring[i] = ghost;
     __syncthreads();
+    ptx::griddep_wait();  // earlier kernels of the stream wrote our inputs / read our outputs
+    ptx::griddep_trigger();
     const uint32_t rowb = (uint32_t)(P.pitch * sizeof(float));
 
     if (warp == P.CW) {
@@ -506,8 +508,7 @@ cudaError_t launch_star3d_pair(const Family& f, const SweepArgs& a, double bc_va
         attr[f.periodic ? 1 : 0] = true;
     }
     const int grid = (int)std::min<int64_t>(P.units, p2_sm_count());
-    fn<<<grid, (c.CW + 1) * 32, smem, s>>>((const float*)a.in, (float*)a.out, P);
-    return cudaGetLastError();
+    return launch_dependent(fn, dim3(grid), dim3((c.CW + 1) * 32), smem, s, (const float*)a.in, (float*)a.out, P);
 }
 
 }  // namespace st

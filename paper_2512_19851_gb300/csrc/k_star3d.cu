@@ -29,8 +29,12 @@ namespace st {
 
 namespace {
 
-constexpr int CONSUMER_WARPS = 16;
-constexpr int THREADS = (CONSUMER_WARPS + 1) * 32;
+// Consumer warps per CTA: 16, or 12 for the conservative form, whose thread
+// carries twice the planes (u and kappa) and needs up to 128 registers.
+template <bool CONS>
+__host__ __device__ constexpr int consumer_warps() { return CONS ? 12 : 16; }
+template <bool CONS>
+__host__ __device__ constexpr int block_threads() { return (consumer_warps<CONS>() + 1) * 32; }
 
 struct Star1Params {
     int64_t nz, ny, nx, pitch, plane, origin;
@@ -131,13 +135,35 @@ __device__ __forceinline__ T point(const Star1Params& P, T c, T xm, T xp, T ym, 
     }
 }
 
+// One output point of the conservative face-averaged form: each face's
+// coefficient is the mean of the two cells' kappa, and a Dirichlet ghost
+// face takes kappa of the cell itself, which the kernel gets by the same
+// expression because the coefficient field's ghost cells mirror their
+// interior neighbours ((k + k) / 2 = k exactly).  Faces in the order -z, +z,
+// -y, +y, -x, +x.
+template <typename T>
+__device__ __forceinline__ T cons_point(T c, T k, T xm, T kxm, T xp, T kxp, T ym, T kym, T yp, T kyp, T zm, T kzm,
+                                        T zp, T kzp)
+{
+    const T h = T(0.5);
+    T acc = ((k + kzm) * h) * (zm - c);
+    acc = fma((k + kzp) * h, zp - c, acc);
+    acc = fma((k + kym) * h, ym - c, acc);
+    acc = fma((k + kyp) * h, yp - c, acc);
+    acc = fma((k + kxm) * h, xm - c, acc);
+    acc = fma((k + kxp) * h, xp - c, acc);
+    return c + acc;
+}
+
 __device__ __forceinline__ void set_timeout(int* status)
 {
     if (status) atomicCAS(status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
 }
 
-template <typename T, bool KAPPA, bool SYM, bool PERIODIC, int G>
-__global__ void __launch_bounds__(THREADS, 1)
+// CONS: the conservative face-averaged operator (KAPPA set): the coefficient
+// tile carries the same halo rows as u and is staged for every plane.
+template <typename T, bool KAPPA, bool SYM, bool PERIODIC, int G, bool CONS = false>
+__global__ void __launch_bounds__(block_threads<CONS>(), 1)
 k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kappa, const __grid_constant__ Star1Params P)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -150,15 +176,17 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.NS; ++s) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&empty[s], CONSUMER_WARPS);
+            ptx::mbar_init(&empty[s], consumer_warps<CONS>());
         }
         ptx::fence_barrier_init();
     }
     __syncthreads();
+    ptx::griddep_wait();  // earlier kernels of the stream wrote our inputs / read our outputs
+    ptx::griddep_trigger();
 
     const uint32_t rowb = (uint32_t)(P.pitch * sizeof(T));
 
-    if (warp == CONSUMER_WARPS) {
+    if (warp == consumer_warps<CONS>()) {
         // ------------------------------------------------------------ producer
         if (lane != 0) return;
         uint32_t gq = 0;
@@ -174,25 +202,32 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                     return;
                 }
                 const int64_t zi = z0 - 1 + q;
-                const bool need_k = KAPPA && q >= 1 && q <= zce;
-                const uint32_t bytes = (uint32_t)(tye + 2) * rowb + (need_k ? (uint32_t)tye * rowb : 0u);
+                const bool need_k = KAPPA && (CONS || (q >= 1 && q <= zce));
+                const uint32_t krows = CONS ? (uint32_t)(tye + 2) : (uint32_t)tye;
+                const uint32_t bytes = (uint32_t)(tye + 2) * rowb + (need_k ? krows * rowb : 0u);
                 T* dst = ring + (size_t)s * P.stage_elems;
                 ptx::mbar_arrive_expect_tx(&full[s], bytes);
-                if (!PERIODIC) {
-                    const T* src = in + (zi + P.rz) * P.plane + (y0 - 1 + P.r) * P.pitch;
-                    ptx::bulk_g2s(dst, src, (uint32_t)(tye + 2) * rowb, &full[s]);
-                } else {
-                    const T* pl = in + (wrapi(zi, P.nz) + P.rz) * P.plane + (int64_t)P.r * P.pitch;
-                    int j = 0;
-                    while (j < tye + 2) {
-                        int64_t row = y0 - 1 + j;
-                        row = ((row % P.ny) + P.ny) % P.ny;
-                        const int run = (int)imin64(tye + 2 - j, P.ny - row);
-                        ptx::bulk_g2s(dst + (size_t)j * P.pitch, pl + row * P.pitch, (uint32_t)run * rowb, &full[s]);
-                        j += run;
+                // the tile rows y0 - 1 .. y0 + tye of plane zi of a field
+                auto tile = [&](const T* fld, T* d) {
+                    if (!PERIODIC) {
+                        const T* src = fld + (zi + P.rz) * P.plane + (y0 - 1 + P.r) * P.pitch;
+                        ptx::bulk_g2s(d, src, (uint32_t)(tye + 2) * rowb, &full[s]);
+                    } else {
+                        const T* pl = fld + (wrapi(zi, P.nz) + P.rz) * P.plane + (int64_t)P.r * P.pitch;
+                        int j = 0;
+                        while (j < tye + 2) {
+                            int64_t row = y0 - 1 + j;
+                            row = ((row % P.ny) + P.ny) % P.ny;
+                            const int run = (int)imin64(tye + 2 - j, P.ny - row);
+                            ptx::bulk_g2s(d + (size_t)j * P.pitch, pl + row * P.pitch, (uint32_t)run * rowb, &full[s]);
+                            j += run;
+                        }
                     }
-                }
-                if (need_k) {
+                };
+                tile(in, dst);
+                if constexpr (CONS) {
+                    tile(kappa, dst + P.u_elems);
+                } else if (need_k) {
                     const T* ks = kappa + (zi + P.rz) * P.plane + (y0 + P.r) * P.pitch;
                     ptx::bulk_g2s(dst + P.u_elems, ks, (uint32_t)tye * rowb, &full[s]);
                 }
@@ -213,7 +248,7 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
     // its inner y neighbours (y reuse); only the plane above, the pair's outer
     // y neighbours and the x edges are read from shared memory.
     const int ct = threadIdx.x;
-    const int NC = CONSUMER_WARPS * 32;
+    const int NC = consumer_warps<CONS>() * 32;
     const int ngx = (int)((P.nx + VN - 1) / VN);
     const unsigned FULLM = 0xffffffffu;
     uint32_t gq = 0;
@@ -246,6 +281,8 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
             if (lane == 0) ptx::mbar_arrive(&empty[(base + q) % P.NS]);
         };
         T bel[G][2][VN], cen[G][2][VN], abv[G][2][VN];
+        // CONS: the coefficient's planes below, at and above (same layout as u)
+        T kbl[CONS ? G : 1][2][VN], kcn[CONS ? G : 1][2][VN], kab[CONS ? G : 1][2][VN];
         if (!wait_q(0) || !wait_q(1)) {
             set_timeout(P.status);
             return;
@@ -257,6 +294,10 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                 const int off = (trow[g] + r + 1) * (int)P.pitch + tgx[g] * VN;
                 ldv(stage(0) + off, bel[g][r]);
                 ldv(stage(1) + off, cen[g][r]);
+                if constexpr (CONS) {
+                    ldv(stage(0) + P.u_elems + off, kbl[g][r]);
+                    ldv(stage(1) + P.u_elems + off, kcn[g][r]);
+                }
             }
         release(0);
         // running ring slots of the centre plane (i + 1) and the plane above
@@ -278,12 +319,17 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                 // periodic only: the row end falls inside this group (ragged last group)
                 const bool wrap_in_group = PERIODIC && x + VN > P.nx;
                 const int rbase = trow[g] * (int)P.pitch + x;  // smem offset of row trow - 1
-                T up[VN], dn[VN], kv[2][VN];
+                T up[VN], dn[VN], kv[2][VN], kup[VN], kdn[VN];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) ldv(sa + rbase + (r + 1) * (int)P.pitch, abv[g][r]);
                 ldv(sc + rbase, up);
                 ldv(sc + rbase + 3 * (int)P.pitch, dn);
-                if constexpr (KAPPA) {
+                if constexpr (CONS) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) ldv(sa + P.u_elems + rbase + (r + 1) * (int)P.pitch, kab[g][r]);
+                    ldv(sk + rbase, kup);
+                    ldv(sk + rbase + 3 * (int)P.pitch, kdn);
+                } else if constexpr (KAPPA) {
                     ldv(sk + rbase, kv[0]);
                     ldv(sk + rbase + (int)P.pitch, kv[1]);
                 }
@@ -298,13 +344,37 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                     const T* yl = r == 0 ? up : cen[g][0];
                     const T* yh = r == 0 ? cen[g][1] : dn;
                     T o[VN];
+                    if constexpr (CONS) {
+                        const T* krow = crow + P.u_elems;
+                        T kleft = __shfl_up_sync(FULLM, kcn[g][r][VN - 1], 1);
+                        T kright = __shfl_down_sync(FULLM, kcn[g][r][0], 1);
+                        if (lane == 0 || tgx[g] == 0) kleft = (PERIODIC && x == 0) ? krow[P.nx - 1] : krow[x - 1];
+                        if (lane == 31 || tgx[g] == ngx - 1)
+                            kright = (PERIODIC && x + VN >= P.nx) ? krow[0] : krow[x + VN];
+                        const T* kyl = r == 0 ? kup : kcn[g][0];
+                        const T* kyh = r == 0 ? kcn[g][1] : kdn;
 #pragma unroll
-                    for (int j = 0; j < VN; ++j) {
-                        const T xm = j == 0 ? left : cen[g][r][j - 1];
-                        T xp = j == VN - 1 ? right : cen[g][r][j + 1];
-                        if (PERIODIC && wrap_in_group && x + j + 1 == P.nx) xp = crow[0];
-                        o[j] = point<T, KAPPA, SYM>(P, cen[g][r][j], xm, xp, yl[j], yh[j], bel[g][r][j], abv[g][r][j],
-                                                    KAPPA ? kv[r][j] : T(0));
+                        for (int j = 0; j < VN; ++j) {
+                            const T xm = j == 0 ? left : cen[g][r][j - 1];
+                            const T kxm = j == 0 ? kleft : kcn[g][r][j - 1];
+                            T xp = j == VN - 1 ? right : cen[g][r][j + 1];
+                            T kxp = j == VN - 1 ? kright : kcn[g][r][j + 1];
+                            if (PERIODIC && wrap_in_group && x + j + 1 == P.nx) {
+                                xp = crow[0];
+                                kxp = krow[0];
+                            }
+                            o[j] = cons_point<T>(cen[g][r][j], kcn[g][r][j], xm, kxm, xp, kxp, yl[j], kyl[j], yh[j],
+                                                 kyh[j], bel[g][r][j], kbl[g][r][j], abv[g][r][j], kab[g][r][j]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < VN; ++j) {
+                            const T xm = j == 0 ? left : cen[g][r][j - 1];
+                            T xp = j == VN - 1 ? right : cen[g][r][j + 1];
+                            if (PERIODIC && wrap_in_group && x + j + 1 == P.nx) xp = crow[0];
+                            o[j] = point<T, KAPPA, SYM>(P, cen[g][r][j], xm, xp, yl[j], yh[j], bel[g][r][j],
+                                                        abv[g][r][j], KAPPA ? kv[r][j] : T(0));
+                        }
                     }
                     if (tact[g] && trow[g] + r < tye) {
                         T* op = oplane + (int64_t)(trow[g] + r) * P.pitch + x;
@@ -321,6 +391,10 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                     for (int j = 0; j < VN; ++j) {
                         bel[g][r][j] = cen[g][r][j];
                         cen[g][r][j] = abv[g][r][j];
+                        if constexpr (CONS) {
+                            kbl[g][r][j] = kcn[g][r][j];
+                            kcn[g][r][j] = kab[g][r][j];
+                        }
                     }
             }
             __syncwarp();
@@ -353,18 +427,23 @@ int sm_count()
 
 constexpr size_t SMEM_BUDGET = 200 * 1024;
 
-size_t stage_bytes(const Geom& g, int TY, bool kappa)
+// Coefficient rows staged per plane: none, the tile rows, or (the
+// conservative form) the tile rows with their y halo.
+enum KMode { K_NONE = 0, K_TILE = 1, K_HALO = 2 };
+
+size_t stage_bytes(const Geom& g, int TY, int kappa)
 {
-    size_t e = (size_t)(TY + 2) * g.pitch + (kappa ? (size_t)TY * g.pitch : 0);
+    const size_t krows = kappa == K_HALO ? (size_t)TY + 2 : (kappa == K_TILE ? (size_t)TY : 0);
+    size_t e = (size_t)(TY + 2) * g.pitch + krows * g.pitch;
     e = (e * g.esize + 127) / 128 * 128;
     return e;
 }
 
 // Tile rows TY (even), z-chunk ZC, ring stages NS, tasks per thread G.
-bool pick_cfg(const Geom& g, bool kappa, Cfg* c)
+bool pick_cfg(const Geom& g, int kappa, Cfg* c)
 {
     const int VN = 16 / g.esize;
-    const int NC = CONSUMER_WARPS * 32;
+    const int NC = consumer_warps<false>() * 32 * (kappa == K_HALO ? 3 : 4) / 4;
     const int ngx = (int)((g.nx + VN - 1) / VN);
     int TY = 2 * std::max(1, (NC + ngx - 1) / ngx);  // row pairs x groups ~ one task per thread
     TY = std::min(TY, 16);
@@ -408,12 +487,13 @@ bool pick_cfg(const Geom& g, bool kappa, Cfg* c)
     return true;
 }
 
-template <typename T, bool KAPPA, bool SYM, bool PERIODIC>
+template <typename T, bool KAPPA, bool SYM, bool PERIODIC, bool CONS = false>
 cudaError_t launch_t(const Family& f, const SweepArgs& a, cudaStream_t s)
 {
     const Geom& g = f.g;
+    const int kmode = CONS ? K_HALO : (KAPPA ? K_TILE : K_NONE);
     Cfg c;
-    if (!pick_cfg(g, KAPPA, &c)) return cudaErrorNotSupported;
+    if (!pick_cfg(g, kmode, &c)) return cudaErrorNotSupported;
     Star1Params P;
     std::memset(&P, 0, sizeof(P));
     P.nz = g.nz;
@@ -432,7 +512,7 @@ cudaError_t launch_t(const Family& f, const SweepArgs& a, cudaStream_t s)
     P.nzc = (int)((g.nz + c.ZC - 1) / c.ZC);
     P.units = P.nyt * P.nzc;
     P.u_elems = (uint32_t)((c.TY + 2) * g.pitch);
-    P.stage_elems = (uint32_t)(stage_bytes(g, c.TY, KAPPA) / sizeof(T));
+    P.stage_elems = (uint32_t)(stage_bytes(g, c.TY, kmode) / sizeof(T));
     const StarCoef& k = f.sc;
     P.wc = k.c_a;
     P.bc = k.c_b;
@@ -451,15 +531,15 @@ cudaError_t launch_t(const Family& f, const SweepArgs& a, cudaStream_t s)
     P.status = a.status;
     const size_t smem = (size_t)c.NS * P.stage_elems * sizeof(T) + 2 * sizeof(uint64_t) * c.NS;
     static bool attr_set[2] = {false, false};
-    auto fn = c.G == 1 ? k_star1<T, KAPPA, SYM, PERIODIC, 1> : k_star1<T, KAPPA, SYM, PERIODIC, 2>;
+    auto fn = c.G == 1 ? k_star1<T, KAPPA, SYM, PERIODIC, 1, CONS> : k_star1<T, KAPPA, SYM, PERIODIC, 2, CONS>;
     if (!attr_set[c.G - 1]) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         attr_set[c.G - 1] = true;
     }
     const int grid = (int)std::min<int64_t>(P.units, sm_count());
-    fn<<<grid, THREADS, smem, s>>>((const T*)a.in, (T*)a.out, (const T*)a.kappa, P);
-    return cudaGetLastError();
+    return launch_dependent(fn, dim3(grid), dim3(block_threads<CONS>()), smem, s, (const T*)a.in, (T*)a.out,
+                            (const T*)a.kappa, P);
 }
 
 }  // namespace
@@ -471,7 +551,7 @@ bool star3d_supports(const FamilyDesc& d, int* variant, const char** name)
         for (int i = 0; i < 3; ++i)
             if (d.off[3 * k + i] > 1 || d.off[3 * k + i] < -1) return false;
     Cfg c;
-    if (!pick_cfg(d.g, d.has_beta, &c)) return false;
+    if (!pick_cfg(d.g, d.has_beta ? K_TILE : K_NONE, &c)) return false;
     *variant = 1;
     *name = d.has_beta ? "star3d_r1_bulk_kappa" : "star3d_r1_bulk";
     return true;
@@ -493,5 +573,19 @@ cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s)
 #undef ST_DISPATCH
 }
 
+// The conservative face-averaged operator (3D) on the staged pipeline.
+bool star3d_cons_supported(const Geom& g)
+{
+    Cfg c;
+    return g.ndim == 3 && pick_cfg(g, K_HALO, &c);
+}
+
+cudaError_t launch_star3d_cons(const Family& f, const SweepArgs& a, cudaStream_t s)
+{
+    if (f.g.esize == 8)
+        return f.periodic ? launch_t<double, true, true, true, true>(f, a, s)
+                          : launch_t<double, true, true, false, true>(f, a, s);
+    return f.periodic ? launch_t<float, true, true, true, true>(f, a, s) : launch_t<float, true, true, false, true>(f, a, s);
+}
 
 }  // namespace st

@@ -88,6 +88,8 @@ k_wave(const float* __restrict__ un, float* uprev_out, const float* __restrict__
         ptx::fence_barrier_init();
     }
     __syncthreads();
+    ptx::griddep_wait();  // earlier kernels of the stream wrote our inputs / read our outputs
+    ptx::griddep_trigger();
     const uint32_t rowb = (uint32_t)(P.pitch * sizeof(float));
     const int H = 2 * WR;  // halo rows per tile
 
@@ -518,8 +520,8 @@ cudaError_t launch_wave(const Family& f, const SweepArgs& a, cudaStream_t s)
         attr[pi][ai] = true;
     }
     const int grid = (int)std::min<int64_t>(P.units, wave_sm_count());
-    table[pi][ai]<<<grid, W_THREADS, smem, s>>>((const float*)a.in, (float*)a.out, (const float*)a.kappa, P);
-    return cudaGetLastError();
+    return launch_dependent(table[pi][ai], dim3(grid), dim3(W_THREADS), smem, s, (const float*)a.in, (float*)a.out,
+                            (const float*)a.kappa, P);
 }
 
 }  // namespace st

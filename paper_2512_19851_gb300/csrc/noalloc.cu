@@ -14,12 +14,11 @@ using namespace st;
 
 namespace {
 
-// One partial (sum, sum of squares, max) per block, one block per 65536
-// interior points: 4096 blocks cover grids of up to 2^28 points with 96 KB
-// of device memory, held by every GPU that loads the library until exit.
+// One partial (sum, sum of squares, max) per block and at most 4096 blocks:
+// 96 KB of device memory, held by every GPU that loads the library until
+// exit.  The blocks walk the interior rows in a grid-stride loop, so a grid
+// of any size needs no more partials than that.
 constexpr int NOALLOC_MAX_BLOCKS = 4096;
-constexpr int64_t NOALLOC_POINTS_PER_BLOCK = 65536;
-constexpr int64_t NOALLOC_MAX_POINTS = NOALLOC_MAX_BLOCKS * NOALLOC_POINTS_PER_BLOCK;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[3 * NOALLOC_MAX_BLOCKS];
@@ -54,18 +53,15 @@ extern "C" st_status stencil_reduce_noalloc(st_grid_t g, const void* a, const vo
 {
     if (!g || !a || !dev_out) return fail(ST_ERR_ARG, "stencil_reduce_noalloc: NULL argument");
     const Geom& G = *grid_geom(g);
-    if (G.npoints > NOALLOC_MAX_POINTS)
-        return fail(ST_ERR_ARG,
-                    "stencil_reduce_noalloc: the interior has " + std::to_string(G.npoints) +
-                        " points, more than the 268435456 its static scratch covers; use stencil_reduce");
     double* partials = nullptr;
     st_status rc = noalloc_scratch(&partials);
     if (rc != ST_OK) return rc;
-    int64_t nb = (G.npoints + NOALLOC_POINTS_PER_BLOCK - 1) / NOALLOC_POINTS_PER_BLOCK;
-    if (nb < 1) nb = 1;
+    // as many blocks as are resident at once (at most the array's 4096), the
+    // grid stencil_reduce uses as well
+    const int nb = reduce_blocks(G, NOALLOC_MAX_BLOCKS);
     cudaStream_t s = (cudaStream_t)stream;
     // every block overwrites its own partial, so nothing needs clearing first
-    ST_CUDA_TRY(launch_reduce(G.esize, a, b, G, partials, (int)nb, dev_out, 0, nullptr, s));
+    ST_CUDA_TRY(launch_reduce(G.esize, a, b, G, partials, nb, dev_out, 0, nullptr, s));
     grid_note_stream(g, s);
     return ST_OK;
 }

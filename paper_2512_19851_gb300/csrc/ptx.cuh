@@ -100,5 +100,17 @@ __device__ __forceinline__ void cp_async_elem(void* dst, const void* src)
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Programmatic dependent launch.  A kernel launched with a programmatic
+// dependency on the previous kernel of its stream (launch_dependent) may be
+// scheduled while that kernel still runs; griddep_wait() blocks until every
+// grid it depends on has completed and its memory operations are visible (it
+// returns at once for a kernel launched without such a dependency), so it
+// must come before the first access to global memory that earlier work in
+// the stream reads or writes.  griddep_trigger() lets the dependent grid be
+// scheduled once every CTA of this grid has issued it or exited; the
+// dependent still waits for this grid's completion in its own griddep_wait.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace ptx
 }  // namespace st

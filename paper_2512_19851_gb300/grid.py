@@ -15,6 +15,27 @@ from .abi import ST_DIRICHLET, ST_F32, ST_F64, ST_FLAG_GENERIC, ST_PERIODIC, ST_
 _ST_DTYPE = {torch.float32: ST_F32, torch.float64: ST_F64}
 
 
+def _before_torch_copies(stream, device):
+    """torch writes a call's input copies on its current stream: when the
+    library works on another `stream`, the current stream first waits for
+    that stream's earlier work on the same buffers."""
+    cur = torch.cuda.current_stream(device)
+    if stream is not None and stream != cur:
+        cur.wait_stream(stream)
+
+
+def _after_torch_copies(stream, device):
+    """The stream library work goes to: `stream`, or torch's current stream.
+    A different stream first waits for the copies torch made on its current
+    stream."""
+    cur = torch.cuda.current_stream(device)
+    if stream is None:
+        return cur
+    if stream != cur:
+        stream.wait_stream(cur)
+    return stream
+
+
 def _as_tensor(x, dtype, device):
     if isinstance(x, torch.Tensor):
         return x.to(device=device, dtype=dtype)
@@ -50,6 +71,9 @@ class Grid:
         abi.stencil_bind(self.h, ST_SLOT_A, self.bufs[0].data_ptr())
         abi.stencil_bind(self.h, ST_SLOT_B, self.bufs[1].data_ptr())
         self.coeff = None
+        # bumped by every set_coeff: a recorded adjoint is valid only for the
+        # coefficient field its forward run used
+        self.coeff_generation = 0
         if beta is not None:
             self.coeff = torch.zeros(self.padded, dtype=dtype, device=self.device)
             abi.stencil_bind(self.h, ST_SLOT_COEFF, self.coeff.data_ptr())
@@ -92,6 +116,7 @@ class Grid:
     def set_coeff(self, kappa) -> None:
         self.interior(self.coeff).copy_(_as_tensor(kappa, self.dtype, self.device))
         abi.stencil_mark_dirty(self.h, ST_SLOT_COEFF)
+        self.coeff_generation += 1
 
     def set_source(self, index, amplitudes) -> None:
         abi.stencil_set_source(self.h, index, amplitudes)
@@ -260,31 +285,48 @@ class VarCoefProblem:
         self.lam_tmp = grid.new_field()
         self.gk = grid.new_field(torch.float64)
         self.loss = torch.zeros(1, dtype=torch.float64, device=grid.device)
+        # One workspace records one forward run: `generation` counts the runs,
+        # and `recorded` is (run, coefficient generation of the grid) of the
+        # run the workspace now holds.
+        self.generation = 0
+        self.recorded = None
 
     def forward(self, u0, kappa=None, stream=None):
         g = self.grid
+        _before_torch_copies(stream, g.device)
         abi.stencil_set_current(g.h, ST_SLOT_A)
         g.set_field(u0, ST_SLOT_A)
         if kappa is not None:
             g.set_coeff(kappa)
-        s = stream if stream is not None else torch.cuda.current_stream(g.device)
+        s = _after_torch_copies(stream, g.device)
         abi.stencil_step_ckpt(g.h, self.nsteps, self.m, self.ws.data_ptr(), s)
+        self.generation += 1
+        self.recorded = (self.generation, g.coeff_generation)
         return g.current()
+
+    def record_valid(self, record) -> bool:
+        """True while the workspace and the bound coefficients still belong to
+        the forward run identified by `record` (a value of `recorded`)."""
+        return record is not None and record == self.recorded and record[1] == self.grid.coeff_generation
 
     def backward_from(self, lam_T=None, target=None, stream=None):
         """Reverse pass.  Either lam_T (dL/du_T) or target (then the library
         forms lambda_T = u_T - target and the loss) must be given."""
         g = self.grid
-        s = stream if stream is not None else torch.cuda.current_stream(g.device)
+        _before_torch_copies(stream, g.device)
         if target is not None:
             tgt = g.new_field()
             g.interior(tgt).copy_(_as_tensor(target, g.dtype, g.device))
+            s = _after_torch_copies(stream, g.device)
             cur = g.bufs[g.current_slot()]
             abi.stencil_residual(g.h, cur.data_ptr(), tgt.data_ptr(), self.lam.data_ptr(), self.loss.data_ptr(), s)
+            if s != torch.cuda.current_stream(g.device):
+                tgt.record_stream(s)  # freed here, still read by the residual on s
         else:
             self.lam.zero_()
             g.interior(self.lam).copy_(_as_tensor(lam_T, g.dtype, g.device))
         self.gk.zero_()
+        s = _after_torch_copies(stream, g.device)
         abi.stencil_adjoint(g.h, self.nsteps, self.m, self.ws.data_ptr(), self.lam.data_ptr(),
                             self.lam_tmp.data_ptr(), self.gk.data_ptr() if g.coeff is not None else 0, s)
         return g.interior(self.lam), g.interior(self.gk), self.loss
@@ -295,6 +337,13 @@ class StencilFn(torch.autograd.Function):
 
     forward(u0, kappa, problem) -> u_T ; backward returns (dL/du0, dL/dkappa)
     computed by the library's transpose sweep with checkpoint recomputation.
+
+    The checkpoints live in the problem's one workspace and the coefficients
+    in its grid, so a problem records one forward run at a time: applying it
+    again, or calling set_coeff on its grid, before the backward of an earlier
+    application makes that backward raise RuntimeError instead of returning
+    the gradient of another trajectory (use one problem per live graph node).
+    The gradients returned are copies, never views of the problem's buffers.
     """
 
     @staticmethod
@@ -303,9 +352,13 @@ class StencilFn(torch.autograd.Function):
         ctx.u0_dtype = u0.dtype
         ctx.kappa_dtype = kappa.dtype
         out = problem.forward(u0, kappa)
+        ctx.record = problem.recorded
         return out.clone()
 
     @staticmethod
     def backward(ctx, grad_out):
+        if not ctx.problem.record_valid(ctx.record):
+            raise RuntimeError("StencilFn.backward: the problem's workspace or coefficient field was overwritten "
+                               "by a later forward run or set_coeff; use one VarCoefProblem per node")
         lam0, gk, _ = ctx.problem.backward_from(lam_T=grad_out)
-        return lam0.to(ctx.u0_dtype, copy=True), gk.to(ctx.kappa_dtype), None
+        return lam0.to(ctx.u0_dtype, copy=True), gk.to(ctx.kappa_dtype, copy=True), None

@@ -209,10 +209,10 @@ def test_neumann_arguments():
 def test_conservative_create():
     h = abi.stencil_create_conservative(3, (8, 9, 10), abi.ST_PERIODIC, 0.0, abi.ST_F64)
     r, n, name = abi.stencil_info(h)
-    assert (r, n, name) == (1, 7, "cons_face_avg_point")
+    assert (r, n, name) == (1, 7, "cons_face_avg_bulk")  # 3D: the staged pipeline
     abi.stencil_destroy(h)
     h = abi.stencil_create_conservative(2, (8, 9), abi.ST_DIRICHLET, 0.5, abi.ST_F32)
-    assert abi.stencil_info(h)[1] == 5
+    assert abi.stencil_info(h)[1:] == (5, "cons_face_avg_point")  # 2D: a thread per column
     abi.stencil_destroy(h)
     for kw in (dict(ndim=4, dims=(2, 2, 2, 2)), dict(bc=abi.ST_NEUMANN), dict(flags=1)):
         args = dict(ndim=3, dims=(8, 9, 10), bc=abi.ST_DIRICHLET, bc_value=0.0, dtype=abi.ST_F64, flags=0)

@@ -107,6 +107,22 @@ def test_gradient_full_size_fused_pass():
     assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
 
 
+def test_gradient_full_size_two_segments():
+    """256^3 FP32 Dirichlet with the benchmark's checkpoint interval: 40
+    steps, a checkpoint every 20, so the reverse pass recomputes one segment
+    and reads the other from the forward run, in the benchmark's launch
+    configuration; every point of lambda_0 and of the gradient against the
+    FP64 oracle (which recomputes its own segments)."""
+    v = inputs.varcoef3d(n=256)
+    steps, m = 40, 20
+    loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, False, 0.0, steps, m)
+    uT, lam0, gk, loss, kern = gpu_grad(v, steps, m, torch.float32)
+    assert rel_err(uT, uT_r) <= TOL32_FWD, kern
+    assert abs(loss - loss_r) <= TOL32_FWD * loss_r
+    assert rel_err(lam0, lam_r) <= TOL32_FWD, kern
+    assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
+
+
 @pytest.mark.parametrize("periodic,bc", [(False, 0.0), (False, 0.3), (True, 0.0)])
 def test_gradient_fp32_ragged_matches_fp64_oracle(periodic, bc):
     """FP32 transpose on rows that end inside a 16-byte group (nx = 45), a
@@ -279,4 +295,41 @@ def test_adjoint_argument_errors():
     with pytest.raises(abi.StencilError) as e:
         abi.stencil_bind(g.h, abi.ST_SLOT_B, g.bufs[0].data_ptr())
     assert e.value.code == abi.ST_ERR_ALIAS
+    g.close()
+
+
+def test_autograd_second_application_invalidates_first():
+    """One problem applied twice before backward: the first node's backward
+    raises (its checkpoints were overwritten) instead of returning the
+    gradient of the second trajectory; the second node's backward is right.
+    set_coeff on the grid also invalidates a recorded run.  The returned
+    gradients are copies: a later reverse pass does not change them."""
+    shape = (10, 12, 16)
+    v = inputs.varcoef3d(shape=shape)
+    steps, m = 6, 3
+    _, _, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, False, 0.0, steps, m)
+    g = make(shape, torch.float64)
+    prob = VarCoefProblem(g, steps, m)
+    tgt = torch.as_tensor(v.target, device="cuda")
+    u0a = torch.tensor(v.u0 * 0.5, device="cuda", requires_grad=True)
+    ka = torch.tensor(v.kappa, device="cuda", requires_grad=True)
+    la = 0.5 * ((StencilFn.apply(u0a, ka, prob) - tgt) ** 2).sum()
+    u0 = torch.tensor(v.u0, device="cuda", requires_grad=True)
+    kappa = torch.tensor(v.kappa, device="cuda", requires_grad=True)
+    lb = 0.5 * ((StencilFn.apply(u0, kappa, prob) - tgt) ** 2).sum()
+    with pytest.raises(RuntimeError):
+        la.backward()
+    lb.backward()
+    assert rel_err(u0.grad.cpu().numpy(), lam_r) <= TOL64
+    assert rel_err(kappa.grad.cpu().numpy(), gk_r) <= TOL64
+    keep = kappa.grad.clone()
+    prob.backward_from(lam_T=np.zeros(shape))  # zeroes and rewrites prob.gk
+    torch.cuda.synchronize()
+    assert torch.equal(kappa.grad, keep)
+    u0c = torch.tensor(v.u0, device="cuda", requires_grad=True)
+    kc = torch.tensor(v.kappa, device="cuda", requires_grad=True)
+    lc = 0.5 * ((StencilFn.apply(u0c, kc, prob) - tgt) ** 2).sum()
+    g.set_coeff(v.kappa)
+    with pytest.raises(RuntimeError):
+        lc.backward()
     g.close()

@@ -109,6 +109,37 @@ def test_wave_full_size_sampled():
     assert rel_err(cur, ref) <= 1e-5, kern
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_wave_1000_steps_matches_oracle(dtype):
+    """The workload's full step count at 96^3 (its recipe scaled: unit cube,
+    8 layers, Ricker source at the centre, CFL 0.4): every point of both
+    levels after 1000 steps against the FP64 oracle."""
+    n, steps = 96, 1000
+    w = inputs.wave3d(n=n, steps=steps)
+    z = np.zeros((n, n, n))
+    ref, ref_prev = oracle.wave25(z, z, w.m, a8(), w.src, w.amps, False, 0.0, steps)
+    cur, prev, kern = run_wave(w, n, steps, dtype)
+    tol = TOL64 if dtype == torch.float64 else TOL32_WAVE
+    assert rel_err(cur, ref) <= tol, kern
+    assert rel_err(prev, ref_prev) <= tol, kern
+
+
+def test_wave_full_length_fp32_against_fp64_gpu():
+    """The benchmark's run itself, 512^3 x 1000 steps: the FP32 result
+    against the FP64 run of the same workload on the GPU (the FP64 path
+    equals the FP64 oracle to 1e-12 on the smaller cases above; the oracle
+    itself would need 1.3e11 point updates here).  A comparison of the full
+    length, declared as FP32 GPU against FP64 GPU."""
+    n, steps = 512, 1000
+    w = inputs.wave3d(n=n, steps=steps)
+    c32, p32, k32 = run_wave(w, n, steps, torch.float32)
+    c64, p64, k64 = run_wave(w, n, steps, torch.float64)
+    e = rel_err(c32, c64)
+    assert e <= TOL32_WAVE, (k32, k64, e)
+    assert rel_err(p32, p64) <= TOL32_WAVE
+    assert float(np.max(np.abs(c64))) > 0
+
+
 def test_wave_full_run_energy_and_symmetry():
     """All 1000 steps at 512^3 in FP32: once the Ricker source has decayed
     (t > t0 + 6/(pi f)) the discrete leapfrog energy is constant, and the

@@ -806,3 +806,16 @@ def test_cavity_velocity_update_of_simple_fields():
     u2, v2 = cav.velocity_update(a * x, np.zeros(x.shape), np.zeros(x.shape), CAVP)
     assert np.max(np.abs(u2[1:-1, 1:-1] - (a * x - CAVP.dt * a * a * x)[1:-1, 1:-1])) <= 1e-14
     assert np.all(v2 == 0)
+
+
+def test_sweep_const_into_equals_sweep_const():
+    """The resident-array wrapper used for timing runs the same C loop: bit
+    for bit the result of sweep_const, for even and odd step counts."""
+    rng = np.random.default_rng(41)
+    u0 = rng.random((6, 7, 9))
+    w = [0.4] + [0.1] * 6
+    for n in (1, 2, 5):
+        ref = oracle.sweep_const(u0, inputs.OFFSETS_7PT, w, True, 0.0, n)
+        u = u0.copy()
+        oracle.sweep_const_into(u, np.empty_like(u), inputs.OFFSETS_7PT, w, True, 0.0, n)
+        assert np.array_equal(u, ref)
