@@ -287,7 +287,11 @@ __device__ __forceinline__ void store_pair(bool okw, const XCtx& X, bool act, in
     }
 }
 
-template <typename T, int K, bool PERIODIC>
+// UNIT: the neighbour weight is the coefficient itself (an = 0, bn = 1, the
+// variable-diffusivity operator), so mu = kappa * lambda and the gradient's
+// neighbour sum needs no scaling; the results are the same bits as the
+// general expressions give for those weights (fma(1, k, 0) = k, 1 * s = s).
+template <typename T, int K, bool PERIODIC, bool UNIT>
 __global__ void __launch_bounds__(A_BLOCK, 1)
 k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __restrict__ kappa,
           const T* __restrict__ ua, const T* __restrict__ ub, double* __restrict__ g64,
@@ -429,7 +433,15 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
     // mu = w_n * lambda of a staged (lambda, kappa) pair; the product is
     // rounded on its own (never contracted into a later add), so every level
     // and every pass gets the same mu whatever code surrounds it
-    auto mu_of = [&](T l, T k) -> T { return mul_rn(fma(bn, k, an), l); };
+    auto mu_of = [&](T l, T k) -> T {
+        if constexpr (UNIT) return mul_rn(k, l);
+        else return mul_rn(fma(bn, k, an), l);
+    };
+    // the gradient factor bc u + bn (sum of the six neighbours of u)
+    auto gfac = [&](T u, T nb) -> T {
+        if constexpr (UNIT) return fma(bc, u, nb);
+        else return fma(bc, u, mul_rn(bn, nb));
+    };
 
     bool dead = false;
     uint32_t gq = 0, gr = 0;
@@ -456,9 +468,10 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
         const bool fastw = okw && (ngx % 32 == 0);
         // carried state (registers), per owned row: mu and u_t of the plane below the level-1 centre
         T m0p[2][VN], uap[2][VN];
-        // level 2 (K == 2): mu_1 of the planes below and at its centre, lambda_1 and w_c at its
-        // centre, u_{t-1} below its centre
-        T m1a[2][VN], m1b[2][VN], l1p[2][VN], wcp[2][VN], ubp[2][VN];
+        // level 2 (K == 2): lambda_1 and w_c at its centre, u_{t-1} below its centre (its mu_1
+        // planes are read back from the ring); hm0: the carried mu rows of a halo warp's second
+        // sub-task
+        T l1p[2][VN], wcp[2][VN], ubp[2][VN], hm0[2][VN];
         // level-1 results of this iteration, handed to level 2
         T l1n[2][VN], wcn[2][VN], m1n[2][VN], g1n[2][VN];  // g1n: this step's gradient term
 #pragma unroll
@@ -466,7 +479,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
                 m0p[i][e] = uap[i][e] = T(0);
-                m1a[i][e] = m1b[i][e] = l1p[i][e] = wcp[i][e] = ubp[i][e] = T(0);
+                l1p[i][e] = wcp[i][e] = ubp[i][e] = hm0[i][e] = T(0);
                 l1n[i][e] = wcn[i][e] = m1n[i][e] = g1n[i][e] = T(0);
             }
 
@@ -519,7 +532,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                                 nsum(X, ubp[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
 #pragma unroll
                                 for (int e = 0; e < VN; ++e) {
-                                    const T g2 = mul_rn(l1p[i][e], fma(bc, uv[i + 1][e], mul_rn(bn, nb[e])));
+                                    const T g2 = mul_rn(l1p[i][e], gfac(uv[i + 1][e], nb[e]));
                                     gp[e] = add_rn(g1n[i][e], g2);
                                     ubp[i][e] = uv[i + 1][e];
                                 }
@@ -605,7 +618,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                             nsum(X, uap[i], uv[i], uv[i + 1], uv[i + 2], uz[i], left, right, nb);
 #pragma unroll
                             for (int e = 0; e < VN; ++e) {
-                                g1n[i][e] = mul_rn(lc[i][e], fma(bc, uv[i + 1][e], mul_rn(bn, nb[e])));
+                                g1n[i][e] = mul_rn(lc[i][e], gfac(uv[i + 1][e], nb[e]));
                                 uap[i][e] = uv[i + 1][e];
                             }
                         }
@@ -632,8 +645,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
             } else if (K == 2) {
                 // ------------------------------------------------ halo rows, level 1 only
                 // Two sub-tasks per halo warp (x groups 32 apart by the halo warp
-                // count); the second keeps its carried mu rows in m1a, which only
-                // the row-pair tasks' level 2 uses otherwise.
+                // count); the second keeps its carried mu rows in hm0.
                 auto halo = [&](const XCtx& Xh, bool acth, T (&m0)[2][VN]) {
                     const int xh = Xh.x;
 #pragma unroll
@@ -696,7 +708,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                 const int s2 = warp - P.pair_warps + P.halo_warps;  // second sub-task (warp-uniform)
                 if (32 * s2 < ngx) {
                     const int gx2 = 32 * s2 + lane;
-                    halo(make_xctx<VN, PERIODIC>(gx2, lane, ngx, (int)P.nx), gx2 < ngx, m1a);
+                    halo(make_xctx<VN, PERIODIC>(gx2, lane, ngx, (int)P.nx), gx2 < ngx, hm0);
                 }
             }
 
@@ -705,9 +717,14 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&rfull[wslot]);
                 }
-                // the ring plane of the previous iteration (level 2's centre)
+                // the ring planes of the previous two iterations: level 2's centre
+                // (rn, plane c1 - 1) and the plane below it (rn - 1, plane c1 - 2);
+                // the plane above is this iteration's level-1 output, still in m1n
                 const uint32_t rn = rbase + (uint32_t)j - 3u, rslot = rn % A_RING;
-                if (pairw && j >= 4 && !dead && !ptx::mbar_wait_warp(&rfull[rslot], (rn / A_RING) & 1u)) {
+                const uint32_t ra = rn - 1u, aslot = ra % A_RING;
+                if (pairw && j >= 4 && !dead &&
+                    (!ptx::mbar_wait_warp(&rfull[rslot], (rn / A_RING) & 1u) ||
+                     !ptx::mbar_wait_warp(&rfull[aslot], (ra / A_RING) & 1u))) {
                     atimeout(P.status);
                     dead = true;
                 }
@@ -716,15 +733,20 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                     {
                         const int64_t c2 = c1 - 1;
                         const T* M = mring + (size_t)rslot * P.ring_elems + P.xl + rr0 * pitch;  // mu_1 row rr0 - 1
-                        T mup[VN], mdn[VN];
+                        const T* MA = mring + (size_t)aslot * P.ring_elems + P.xl + (rr0 + 1) * pitch;  // row rr0
+                        T mup[VN], mdn[VN], mc[2][VN], ma[2][VN];
                         vld(M + x, mup);
+                        vld(M + pitch + x, mc[0]);
+                        vld(M + 2 * pitch + x, mc[1]);
                         vld(M + 3 * pitch + x, mdn);
+                        vld(MA + x, ma[0]);
+                        vld(MA + pitch + x, ma[1]);
                         T l2[2][VN], s[2][VN];
 #pragma unroll
                         for (int i = 0; i < 2; ++i) {
                             const T* Mr = M + (i + 1) * pitch;
                             const T left = Mr[X.lcl], right = Mr[X.lcr];
-                            nsum(X, m1a[i], i == 0 ? mup : m1b[0], m1b[i], i == 0 ? m1b[1] : mdn, m1n[i], left, right,
+                            nsum(X, ma[i], i == 0 ? mup : mc[0], mc[i], i == 0 ? mc[1] : mdn, m1n[i], left, right,
                                  s[i]);
 #pragma unroll
                             for (int e = 0; e < VN; ++e) l2[i][e] = fma(wcp[i][e], l1p[i][e], s[i][e]);
@@ -738,15 +760,16 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                     for (int i = 0; i < 2; ++i)
 #pragma unroll
                         for (int e = 0; e < VN; ++e) {
-                            m1a[i][e] = m1b[i][e];
-                            m1b[i][e] = m1n[i][e];
                             l1p[i][e] = l1n[i][e];
                             wcp[i][e] = wcn[i][e];
                         }
                 }
-                if (j >= 3) {  // done with the previous ring plane (halo warps never read it)
+                // plane rn - 1 has had its last reader (level 2 of this iteration, as
+                // the plane below its centre); halo warps never read the ring but
+                // count among its readers
+                if (j >= 4) {
                     __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(&rempty[rslot]);
+                    if (lane == 0) ptx::mbar_arrive(&rempty[aslot]);
                 }
             }
 
@@ -764,8 +787,11 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
         __syncwarp();
         if (lane == 0) {
             ptx::mbar_arrive(&empty[sp]);  // the last staged plane
-            // the unit's last ring plane has no reader: release it as read
-            if (K == 2) ptx::mbar_arrive(&rempty[(rbase + (uint32_t)nq - 3u) % A_RING]);
+            // the unit's last two ring planes get no further reader: release them
+            if (K == 2) {
+                ptx::mbar_arrive(&rempty[(rbase + (uint32_t)nq - 4u) % A_RING]);
+                ptx::mbar_arrive(&rempty[(rbase + (uint32_t)nq - 3u) % A_RING]);
+            }
         }
         gq = base + nq;
         if (K == 2) gr = rbase + (uint32_t)nq - 2u;
@@ -904,12 +930,15 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
     P.status = a.status;
     const size_t smem = c.ring_bytes + (size_t)c.NS * c.stage_bytes + sizeof(uint64_t) * (2 * c.NS + 2 * A_RING) +
                         (size_t)c.CW * 32 * AV<T>::N * sizeof(double);
-    auto fn = k_adjoint<T, K, PERIODIC>;
-    static bool attr = false;
-    if (!attr) {
+    // the variable-diffusivity operator's weights (an = 0, bn = 1) take the
+    // specialised kernel
+    const bool unit = P.an == 0.0 && P.bn == 1.0;
+    auto fn = unit ? k_adjoint<T, K, PERIODIC, true> : k_adjoint<T, K, PERIODIC, false>;
+    static bool attr[2] = {false, false};
+    if (!attr[unit]) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[unit] = true;
     }
     const int grid = (int)std::min<int64_t>(P.flat ? (int64_t)P.nyt * P.nz : P.units, adj_sm_count());
     return launch_dependent(fn, dim3(grid), dim3((c.CW + 1) * 32), smem, s, (const T*)a.lam_in, (T*)a.lam_out,
