@@ -121,6 +121,10 @@ def test_gradient_full_size_two_segments():
     assert abs(loss - loss_r) <= TOL32_FWD * loss_r
     assert rel_err(lam0, lam_r) <= TOL32_FWD, kern
     assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
+    # the recomputed segment (two steps per pass) holds the same states as the
+    # forward run's single sweeps: keeping every state gives the same bits
+    kept = gpu_grad(v, steps, steps, torch.float32)
+    assert np.array_equal(lam0, kept[1]) and np.array_equal(gk, kept[2])
 
 
 @pytest.mark.parametrize("periodic,bc", [(False, 0.0), (False, 0.3), (True, 0.0)])
