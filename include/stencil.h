@@ -118,6 +118,15 @@ typedef enum { ST_DIRICHLET = 0, ST_PERIODIC = 1, ST_NEUMANN = 2 } st_bc;
                                 and stencil_step_ckpt return
                                 ST_ERR_UNSUPPORTED */
 
+#define ST_FLAG_TILE_PASSES 8u  /* FP64 2D grids whose offsets lie in the 3x3
+                                neighbourhood (one time level, constant
+                                weights, Dirichlet or periodic): start on the
+                                tile kernel, k steps per shared-memory pass and
+                                one dependent launch per pass, instead of the
+                                one-thread-per-point kernel; stencil_tune
+                                times both and keeps the faster either way.
+                                Ignored for other grids */
+
 #define ST_MAX_POINTS 64     /* most neighbour points per stencil */
 #define ST_MAX_RADIUS 8      /* widest ghost region */
 
@@ -268,9 +277,11 @@ st_status stencil_step(st_grid_t g, int nsteps, void* stream);
 /*
  * Autotune the launch configuration of this grid for nsteps-step calls (2D
  * grids on the persistent tile kernel: tile shape, threads per block, steps
- * per shared-memory pass; the FP32 constant symmetric 3D 7-point star: one
- * sweep or two sweeps per pass over HBM; other families have nothing to tune
- * and return ST_OK).  Times the candidates on the bound data and restores the
+ * per shared-memory pass; FP64 2D grids within the 3x3 neighbourhood: the
+ * tuned tile kernel, one dependent launch per pass, against the
+ * one-thread-per-point kernel, keeping the faster; the FP32 constant
+ * symmetric 3D 7-point star: one sweep or two sweeps per pass over HBM;
+ * other families have nothing to tune and return ST_OK).  Times the candidates on the bound data and restores the
  * current level afterwards (the other slot is scratch); synchronises
  * `stream`.  With temporal blocking a call may leave the newest level in
  * either slot: stencil_current() tells which.
@@ -279,7 +290,8 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream);
 
 /* The configuration in use (cfg[0] tile x, cfg[1] tile y, cfg[2] threads,
  * cfg[3] steps per pass; 3D 7-point star: zeros and the steps per pass);
- * zeros for families without one. */
+ * zeros for families without one and for FP64 2D grids on the
+ * one-thread-per-point kernel. */
 st_status stencil_tune_config(st_grid_t g, int* cfg);
 
 /*

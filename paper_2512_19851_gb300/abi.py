@@ -30,6 +30,7 @@ ST_DIRICHLET, ST_PERIODIC, ST_NEUMANN = 0, 1, 2
 ST_FLAG_GENERIC = 1
 ST_FLAG_TWO_STEP = 2
 ST_FLAG_CALLER_GHOSTS = 4
+ST_FLAG_TILE_PASSES = 8
 ST_SLOT_A, ST_SLOT_B, ST_SLOT_COEFF = 0, 1, 2
 ST_MAX_POINTS = 64
 ST_MAX_RADIUS = 8

@@ -97,6 +97,11 @@ struct st_grid_s {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     BatchPlan* plan = nullptr;  // 2D grids on the persistent tile kernel (a batch of one)
     bool plan_bound = false;
+    // FP64 2D grids: the tile kernel (one launch per pass of k steps) is an
+    // option that stencil_tune takes only where it times faster than the
+    // one-thread-per-point kernel; plan_use tells which runs
+    bool plan_optional = false;
+    bool plan_use = true;
     bool pairs = false;         // two-step passes chosen by stencil_tune (3D 7-point heat, FP32)
     bool caller_ghosts = false; // ST_FLAG_CALLER_GHOSTS: Dirichlet ghost cells hold the caller's values
     void* staging = nullptr;    // dense interior buffer of stencil_run_host
@@ -157,7 +162,7 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
     if (bc != ST_DIRICHLET && bc != ST_PERIODIC && bc != ST_NEUMANN) return fail(ST_ERR_ARG, "stencil_create: bad bc");
     if (dtype != ST_F32 && dtype != ST_F64) return fail(ST_ERR_ARG, "stencil_create: bad dtype");
     if (time_levels != 1 && time_levels != 2) return fail(ST_ERR_ARG, "stencil_create: time_levels must be 1 or 2");
-    if (flags & ~(ST_FLAG_GENERIC | ST_FLAG_TWO_STEP | ST_FLAG_CALLER_GHOSTS))
+    if (flags & ~(ST_FLAG_GENERIC | ST_FLAG_TWO_STEP | ST_FLAG_CALLER_GHOSTS | ST_FLAG_TILE_PASSES))
         return fail(ST_ERR_ARG, "stencil_create: unknown flags");
     if ((flags & ST_FLAG_CALLER_GHOSTS) && bc != ST_DIRICHLET)
         return fail(ST_ERR_ARG, "stencil_create: ST_FLAG_CALLER_GHOSTS needs a Dirichlet boundary");
@@ -239,7 +244,19 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
         d.force_generic = true;
         g->fam = select_family(d);
     }
-    if (g->fam.kind == FAM_2D_TILE) {
+    // FP64 2D grids within the 3x3 neighbourhood may run the tile kernel one
+    // launch per pass of k steps (temporal blocking on the FP64 pipe costs
+    // redundant halo work, so stencil_tune decides by timing both)
+    bool small2d = ndim == 2 && npts <= 9;
+    for (int k = 0; k < npts; ++k)
+        for (int i = 1; i < 3; ++i)
+            if (g->off[3 * k + i] < -1 || g->off[3 * k + i] > 1) small2d = false;
+    if (g->fam.kind == FAM_GENERIC && small2d && dtype == ST_F64 && time_levels == 1 && !g->has_beta &&
+        !g->caller_ghosts && bc != ST_NEUMANN && !(flags & ST_FLAG_GENERIC)) {
+        g->plan_optional = true;
+        g->plan_use = (flags & ST_FLAG_TILE_PASSES) != 0;
+    }
+    if (g->fam.kind == FAM_2D_TILE || g->plan_optional) {
         std::vector<int32_t> off2(2 * npts);
         for (int k = 0; k < npts; ++k) {
             off2[2 * k] = g->off[3 * k + 1];
@@ -355,7 +372,7 @@ st_status stencil_info(st_grid_t g, int* radius, int* npts, const char** kernel_
     if (!g) return fail(ST_ERR_ARG, "stencil_info: NULL handle");
     if (radius) *radius = g->radius;
     if (npts) *npts = g->npts;
-    if (kernel_name) *kernel_name = g->fam.name;
+    if (kernel_name) *kernel_name = (g->plan_optional && g->plan_use) ? "tile2d_passes" : g->fam.name;
     return ST_OK;
 }
 
@@ -390,6 +407,9 @@ st_status stencil_bind(st_grid_t g, int slot, void* ptr)
         bool moved = false;
         rc = reserve_batch_steps(*g->plan, 1024, &moved);
         if (rc != ST_OK) return rc;
+        // the optional FP64 plan runs one launch per pass (a grid-wide barrier
+        // per pass costs more than a dependent launch)
+        if (g->plan_optional) batch_disable_coop(*g->plan);
         g->plan_bound = true;
     }
     return ST_OK;
@@ -612,7 +632,7 @@ st_status stencil_step(st_grid_t g, int nsteps, void* stream)
     rc = refresh_ghosts(g, s);
     if (rc != ST_OK) return rc;
     if (nsteps == 0 || g->g.npoints == 0) return ST_OK;
-    if (g->plan && g->plan_bound) {
+    if (g->plan && g->plan_bound && g->plan_use && g->src < 0) {
         // 2D grid on the persistent tile kernel: one captured launch for all steps
         bool moved = false;
         rc = reserve_batch_steps(*g->plan, nsteps, &moved);
@@ -733,13 +753,52 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
     void* b = g->buf[ST_SLOT_B];
     rc = tune_batch_plan(*g->plan, std::vector<Geom>{g->g}, &a, &b, nsteps, g->cur, s);
     drop_graphs(g);
-    return rc;
+    if (rc != ST_OK || !g->plan_optional) return rc;
+    // the optional tile plan against the one-thread-per-point kernel, each as
+    // the captured step sequence stencil_step runs (second of two runs);
+    // the current level is put back after every run
+    const size_t bytes = (size_t)g->g.elems * g->g.esize;
+    void* keep = nullptr;
+    if (cudaMalloc(&keep, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ST_ERR_OOM, "stencil_tune: backup allocation failed");
+    }
+    const int cur0 = g->cur;
+    const int64_t step0 = g->step;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms[2] = {0.f, 0.f};
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(keep, g->buf[cur0], bytes, cudaMemcpyDeviceToDevice, s);
+    for (int v = 0; v < 2 && e == cudaSuccess && rc == ST_OK; ++v) {
+        g->plan_use = v == 1;
+        drop_graphs(g);
+        for (int rep = 0; rep < 2 && e == cudaSuccess && rc == ST_OK; ++rep) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) rc = stencil_step(g, nsteps, stream);
+            if (e == cudaSuccess && rc == ST_OK) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess && rc == ST_OK) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && rc == ST_OK) e = cudaEventElapsedTime(&ms[v], e0, e1);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(g->buf[cur0], keep, bytes, cudaMemcpyDeviceToDevice, s);
+            g->cur = cur0;
+            g->step = step0;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    g->plan_use = e == cudaSuccess && rc == ST_OK && ms[1] < ms[0];
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(keep);
+    drop_graphs(g);
+    if (rc != ST_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "stencil_tune");
+    return ST_OK;
 }
 
 st_status stencil_tune_config(st_grid_t g, int* cfg)
 {
     if (!g || !cfg) return fail(ST_ERR_ARG, "stencil_tune_config: NULL argument");
-    if (!g->plan) {
+    if (!g->plan || !g->plan_use) {
         cfg[0] = cfg[1] = cfg[2] = 0;
         cfg[3] = star3d_pair_supported(g->fam) ? (g->pairs ? 2 : 1) : 0;
         return ST_OK;

@@ -277,6 +277,9 @@ __device__ void run_tile(const BatchParams& P, const TileDesc& t, int kp, int sr
 template <typename T, int SHAPE, bool PERIODIC>
 __global__ void k_batch(const __grid_constant__ BatchParams P)
 {
+    // one launch per pass: the previous pass wrote this pass's input
+    ptx::griddep_wait();
+    ptx::griddep_trigger();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s0 = reinterpret_cast<T*>(smem_raw);
     T* s1 = s0 + (size_t)(P.TH + 2 * P.k) * P.row_stride;
@@ -556,8 +559,7 @@ static st_status enqueue_tiled(BatchPlan& p, int nsteps, int cur, cudaStream_t s
     for (int pass = 0; pass < npasses; ++pass) {
         P.pass0 = pass;
         P.pass1 = pass + 1;
-        kf<<<grid, threads, smem, s>>>(P);
-        ST_CUDA_TRY(cudaGetLastError());
+        ST_CUDA_TRY(launch_dependent(kf, dim3(grid), dim3(threads), smem, s, P));
     }
     return ST_OK;
 }

@@ -47,7 +47,7 @@ class Grid:
 
     def __init__(self, shape, offsets, alpha, beta=None, periodic=False, bc_value=0.0, dtype=torch.float64,
                  time_levels=1, radius=0, generic=False, device=None, two_step=False, caller_ghosts=False,
-                 neumann=False, conservative=False):
+                 neumann=False, conservative=False, tile_passes=False):
         """conservative=True: the face-averaged per-cell diffusion of
         stencil_create_conservative (offsets, alpha and beta are ignored)."""
         self.shape = tuple(int(s) for s in shape)
@@ -64,7 +64,8 @@ class Grid:
                                         bc, bc_value, _ST_DTYPE[dtype],
                                         time_levels, (ST_FLAG_GENERIC if generic else 0) |
                                         (abi.ST_FLAG_TWO_STEP if two_step else 0) |
-                                        (abi.ST_FLAG_CALLER_GHOSTS if caller_ghosts else 0))
+                                        (abi.ST_FLAG_CALLER_GHOSTS if caller_ghosts else 0) |
+                                        (abi.ST_FLAG_TILE_PASSES if tile_passes else 0))
         self.padded, self.origin, self.elems = abi.stencil_layout(self.h, self.ndim)
         self.radius, self.npts, self.kernel = abi.stencil_info(self.h)
         self.bufs = [torch.zeros(self.padded, dtype=dtype, device=self.device) for _ in range(2)]
@@ -151,6 +152,7 @@ class Grid:
         """Autotune for nsteps-step calls (2D tile kernel); returns the configuration."""
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         abi.stencil_tune(self.h, nsteps, s)
+        self.kernel = abi.stencil_info(self.h)[2]  # the tuner may change the kernel family
         return abi.stencil_tune_config(self.h)
 
     def reduce(self, a: torch.Tensor, b: torch.Tensor | None = None, stream=None) -> torch.Tensor:

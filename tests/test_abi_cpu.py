@@ -87,7 +87,7 @@ def test_radius_is_derived_from_offsets():
     (dict(bc=abi.ST_PERIODIC, dims=(8, 9, 2), offsets=[(0, 0, 2)], alpha=[1.0]), abi.ST_ERR_ARG),
     (dict(dtype=7), abi.ST_ERR_ARG),
     (dict(time_levels=3), abi.ST_ERR_ARG),
-    (dict(flags=8), abi.ST_ERR_ARG),
+    (dict(flags=16), abi.ST_ERR_ARG),
     (dict(bc=abi.ST_PERIODIC, flags=abi.ST_FLAG_CALLER_GHOSTS), abi.ST_ERR_ARG),
     (dict(alpha=[float("nan"), 0.25, 0.25]), abi.ST_ERR_ARG),
 ])
@@ -241,3 +241,26 @@ def test_cavity_arguments():
         abi.stencil_cavity_bind(h, 1 << 20, (1 << 20) + 8, 1 << 24)
     assert e.value.code == abi.ST_ERR_ALIAS
     abi.stencil_cavity_destroy(h)
+
+
+def test_tile_passes_flag_selects_the_fp64_tile_option():
+    """ST_FLAG_TILE_PASSES starts FP64 2D grids within the 3x3 neighbourhood
+    on the tile passes; other grids ignore it."""
+    offs = [(0, 0), (-1, 0), (1, 0), (0, -1), (0, 1)]
+    def name(dims, dtype, flags, bc=abi.ST_DIRICHLET, offsets=offs):
+        off = np.asarray(offsets, dtype=np.int32).reshape(-1)
+        h = abi.stencil_create(len(dims), dims, 0, off, [0.2] * (len(off) // len(dims)), None, bc, 0.0, dtype, 1,
+                               flags)
+        n = abi.stencil_info(h)[2]
+        abi.stencil_destroy(h)
+        return n
+    assert name((64, 80), abi.ST_F64, 0) == "generic_point"
+    assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES) == "tile2d_passes"
+    assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES, abi.ST_PERIODIC) == "tile2d_passes"
+    assert name((64, 80), abi.ST_F32, abi.ST_FLAG_TILE_PASSES) == "tile2d_persistent"
+    # outside the 3x3 neighbourhood, caller ghosts, zero flux, generic: the per-point kernel
+    wide = [(0, 0), (-2, 0), (2, 0), (0, -2), (0, 2)]
+    assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES, offsets=wide) == "generic_point"
+    assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES | abi.ST_FLAG_CALLER_GHOSTS) == "generic_point"
+    assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES, abi.ST_NEUMANN) == "generic_point"
+    assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES | abi.ST_FLAG_GENERIC) == "generic_point"

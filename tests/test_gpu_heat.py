@@ -318,3 +318,51 @@ def test_2d_box9_fp64_tuned_matches_oracle():
     g.sync()
     assert rel_err(g.current().cpu().numpy(), ref) <= TOL64
     g.close()
+
+
+@pytest.mark.parametrize("offsets_kind", ["star5", "box9"])
+@pytest.mark.parametrize("periodic,bc", [(False, 0.0), (False, 0.3), (True, 0.0)])
+@pytest.mark.parametrize("shape", [(256, 256), (97, 203), (37, 300)])
+def test_2d_fp64_tile_passes_match_oracle(shape, periodic, bc, offsets_kind):
+    """FP64 2D grids on the tile kernel, one dependent launch per pass of k
+    steps (ST_FLAG_TILE_PASSES): every point against the FP64 oracle, split
+    calls of odd and even length; then stencil_tune's choice (tile passes or
+    one thread per point, by timing) from the same start."""
+    from paper_2512_19851_gb300.grid import Grid
+    u0 = inputs.heat2d(shape=shape)
+    if offsets_kind == "star5":
+        offs, w = five_point(0.2)
+    else:
+        offs = inputs.OFFSETS_BOX9
+        w = list(np.random.default_rng(9).random(9))
+        w = [x / sum(w) for x in w]
+    ref = oracle.sweep_const(u0, offs, w, periodic, bc, 37)
+    g = Grid(shape, offs, w, periodic=periodic, bc_value=bc, dtype=torch.float64, tile_passes=True)
+    assert g.kernel == "tile2d_passes"
+    g.set_field(u0)
+    g.step(20)
+    g.step(17)
+    g.sync()
+    assert rel_err(g.current().cpu().numpy(), ref) <= TOL64, g.kernel
+    g.set_field(u0)
+    g.tune(37)
+    assert g.kernel in ("tile2d_passes", "generic_point")
+    g.set_field(u0)
+    g.step(37)
+    g.sync()
+    assert rel_err(g.current().cpu().numpy(), ref) <= TOL64, g.kernel
+    g.close()
+
+
+def test_heat2d_fp64_workload_on_tile_passes():
+    """The C1 workload (256^2 Dirichlet 0, 100 steps) on the tile passes."""
+    from paper_2512_19851_gb300.grid import Grid
+    u0 = inputs.heat2d()
+    offs, w = five_point(0.2)
+    ref = oracle.sweep_const(u0, offs, w, False, 0.0, 100)
+    g = Grid(u0.shape, offs, w, dtype=torch.float64, tile_passes=True)
+    g.set_field(u0)
+    g.step(100)
+    g.sync()
+    assert rel_err(g.current().cpu().numpy(), ref) <= TOL64
+    g.close()
