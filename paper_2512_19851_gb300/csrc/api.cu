@@ -1092,6 +1092,7 @@ st_status stencil_cavity_create(st_cavity_t* out, int64_t ny, int64_t nx, double
     c->P.lid = lid;
     c->P.nit = nit;
     c->P.esize = dtype == ST_F64 ? 8 : 4;
+    c->P.tb = dtype == ST_F32 ? 1 : 0;  // FP32: pressure iterations in shared-memory passes
     cavity_constants(c->P);
     *out = c;
     return ST_OK;

@@ -11,6 +11,7 @@ struct CavityParams {
     double dx, dy, dt, rho, nu, lid;
     int nit;          // pressure iterations per time step
     int esize;        // 4 or 8
+    int tb;           // FP32: pressure iterations in passes of several through shared memory
     // per-point constants computed once on the host in double precision and
     // also rounded to float there, so the kernels neither divide (a divide is
     // an iterative sequence on the FP64 pipe) nor convert (a double-to-float

@@ -87,3 +87,36 @@ def test_split_calls_equal_one_call_and_no_pressure_iterations():
     ref = cav.cavity_run(u0, v0, p0, P0, 4)
     for g, r in zip(run(P0, shape, 4, torch.float64, u0, v0, p0), ref):
         assert rel_err(g, r) <= 1e-12
+
+
+def test_large_grid_ragged_tiles_and_partial_passes():
+    """2050 x 2077 (ragged 128 x 32 tiles of the FP32 pressure passes, every
+    edge), 13 pressure iterations per step (a pass of 8 and one of 5), a
+    random start, 3 steps: FP64 and FP32 against the oracle."""
+    rng = np.random.default_rng(74)
+    shape = (2050, 2077)
+    P = cav.CavityParams(dx=2 / 2076, dy=2 / 2049, dt=2e-5, rho=1.0, nu=0.1, nit=13, lid=1.0)
+    u0, v0, p0 = (0.1 * rng.standard_normal(shape) for _ in range(3))
+    check(P, shape, 3, u0, v0, p0)
+
+
+def test_benchmark_scheme_at_2048_from_rest():
+    """The benchmark's scheme at 2048^2 (50 pressure iterations per step,
+    dt from the stability limit, from rest), 4 steps."""
+    n = 2048
+    dx = 2.0 / (n - 1)
+    P = cav.CavityParams(dx=dx, dy=dx, dt=0.25 * min(dx, dx * dx / 0.4), rho=1.0, nu=0.1, nit=50, lid=1.0)
+    check(P, (n, n), 4)
+
+
+def test_fp32_split_calls_equal_one_call():
+    """FP32 (pressure iterations in shared-memory passes): split calls give
+    the bits of one call."""
+    rng = np.random.default_rng(75)
+    shape = (70, 300)
+    P = cav.CavityParams(dx=0.05, dy=0.04, dt=0.0005, nit=11)
+    u0, v0, p0 = (0.1 * rng.standard_normal(shape) for _ in range(3))
+    one = run(P, shape, 5, torch.float32, u0, v0, p0)
+    split = run(P, shape, 5, torch.float32, u0, v0, p0, chunks=[1, 4])
+    for a, b in zip(one, split):
+        assert np.array_equal(a, b)
