@@ -27,7 +27,9 @@ Functions and the passage each follows:
   per-cell values (Example 1's boundary ring set by slice assignment, Sec.
   III-A), plain numpy; :func:`sweep_neumann` the same update with a
   zero-flux boundary (mirror-image ghosts refreshed before every step, the
-  ghost exchange of Sec. III-C on one domain).
+  ghost exchange of Sec. III-C on one domain); :func:`neumann_transpose` its
+  transpose by scatter and :func:`neumann_loss_gradient` the gradient of a
+  loss of the last state with respect to the first.
 * :func:`cons_forward`, :func:`cons_transpose`, :func:`cons_loss_gradient`
   (in :mod:`oracle.conservative`) -- the per-cell diffusion in conservative
   face-averaged form, its transpose and the coefficient gradient, plain
@@ -50,7 +52,7 @@ import sys
 import numpy as np
 
 from .conservative import cons_forward, cons_loss_gradient, cons_step, cons_transpose  # noqa: F401
-from .ghosts import sweep_ghosts, sweep_neumann  # noqa: F401
+from .ghosts import neumann_loss_gradient, neumann_transpose, sweep_ghosts, sweep_neumann  # noqa: F401
 from .taylor import taylor_second_derivative_coeffs  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

@@ -1,6 +1,6 @@
 """Constant-weight sweeps with arbitrary Dirichlet ghost values and with a
-zero-flux (Neumann) boundary (part of the oracle; TEST INFRASTRUCTURE ONLY,
-see the package header).
+zero-flux (Neumann) boundary, and the transpose of the zero-flux sweep (part
+of the oracle; TEST INFRASTRUCTURE ONLY, see the package header).
 
 Example 1 of Sec. III-A sets the boundary ring of both arrays once by slice
 assignment and never writes it again; the update reads the ring wherever a
@@ -74,3 +74,42 @@ def sweep_neumann(u0, offsets, weights, nsteps: int, dtype=np.float64):
     for _ in range(int(nsteps)):
         u = _sweep_once(np.pad(u, r, mode="symmetric"), r, offs, w, list(u.shape), dtype)
     return u
+
+
+def _mirror_index(i, n):
+    """Cell-centred reflection of index array i into [0, n): -1 - i below,
+    2n - 1 - i above (the zero-flux ghost rule, for i within n of the edge)."""
+    return np.where(i < 0, -1 - i, np.where(i >= n, 2 * n - 1 - i, i))
+
+
+def neumann_transpose(lam, offsets, weights, dtype=np.float64):
+    """Transpose of one zero-flux sweep, by scatter: the sweep reads, for
+    every interior p and offset k, the cell mirror(p + o_k) with weight w_k,
+    so its transpose sends w_k * lam[p] to that cell.  Plain numpy: for each
+    offset (in order) the mirrored target index of every p is formed and
+    the products are added there (np.add.at, which accumulates repeated
+    targets)."""
+    lam = np.asarray(lam, dtype=dtype)
+    offs = [tuple(int(c) for c in o) for o in offsets]
+    if any(len(o) != lam.ndim for o in offs):
+        raise ValueError("one offset component per axis")
+    r = max(abs(c) for o in offs for c in o)
+    if r > min(lam.shape):
+        raise ValueError("a mirror image must be interior (extent >= radius)")
+    idx = np.indices(lam.shape)
+    out = np.zeros_like(lam)
+    for o, wk in zip(offs, weights):
+        tgt = tuple(_mirror_index(idx[a] + o[a], lam.shape[a]) for a in range(lam.ndim))
+        np.add.at(out, tgt, dtype(wk) * lam)
+    return out
+
+
+def neumann_loss_gradient(u0, target, offsets, weights, nsteps: int):
+    """L = 0.5 ||u_n - target||^2 for n zero-flux sweeps from u0, and
+    dL/du0 = (S^T)^n (u_n - target), in double precision."""
+    un = sweep_neumann(u0, offsets, weights, nsteps)
+    d = un - np.asarray(target, dtype=np.float64)
+    lam = d
+    for _ in range(int(nsteps)):
+        lam = neumann_transpose(lam, offsets, weights)
+    return 0.5 * float(np.sum(d * d)), un, lam

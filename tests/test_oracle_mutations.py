@@ -128,6 +128,12 @@ GHOST_MUTANTS = {
     "Neumann mirror skips the edge cell (reflect)": ('mode="symmetric"', 'mode="reflect"'),
     "Neumann ghosts wrap around (periodic)": ('mode="symmetric"', 'mode="wrap"'),
     "Neumann ghosts held at zero (Dirichlet)": ('mode="symmetric"', 'mode="constant"'),
+    "Neumann transpose gathers instead of scattering": (
+        "np.add.at(out, tgt, dtype(wk) * lam)", "out += dtype(wk) * lam[tgt]"),
+    "Neumann transpose reflects without the edge cell": (
+        "np.where(i < 0, -1 - i,", "np.where(i < 0, -i,"),
+    "Neumann transpose loses repeated targets": (
+        "np.add.at(out, tgt, dtype(wk) * lam)", "out[tgt] += dtype(wk) * lam"),
 }
 
 GHOST_PINS = [
@@ -139,6 +145,11 @@ GHOST_PINS = [
     lambda: pins.test_neumann_cosine_mode_decay((12, 9), (3, 2), 0.2, 15),
     pins.test_neumann_conserves_the_sum_and_constants,
     pins.test_neumann_vs_assembled_operator,
+    lambda: [pins.test_neumann_transpose_is_the_assembled_transpose(*a) for a in [
+        ((5, 6), [(0, 0), (-2, 1), (1, -2), (0, 2), (2, 0), (-1, -1)], [0.3, 0.1, 0.25, -0.15, 0.2, 0.05]),
+        ((4, 3, 5), [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)],
+         [0.4, 0.05, 0.15, 0.1, 0.1, 0.12, 0.08])]],
+    pins.test_neumann_loss_gradient_finite_differences,
 ]
 
 
@@ -151,6 +162,8 @@ def test_ghost_pins_catch_planted_mistake(name, monkeypatch):
     exec(compile(src.replace(old, new), "ghosts_mutant", "exec"), ns)
     monkeypatch.setattr(oracle, "sweep_ghosts", ns["sweep_ghosts"])
     monkeypatch.setattr(oracle, "sweep_neumann", ns["sweep_neumann"])
+    monkeypatch.setattr(oracle, "neumann_transpose", ns["neumann_transpose"])
+    monkeypatch.setattr(oracle, "neumann_loss_gradient", ns["neumann_loss_gradient"])
     caught = []
     for fn in GHOST_PINS:
         try:

@@ -593,6 +593,59 @@ def test_neumann_vs_assembled_operator():
     assert np.max(np.abs(got.reshape(-1) - x)) <= 1e-14
 
 
+def _neumann_matrix(shape, offsets, weights):
+    n = int(np.prod(shape))
+    A = np.zeros((n, n))
+    for p in np.ndindex(*shape):
+        ip = np.ravel_multi_index(p, shape)
+        for o, w in zip(offsets, weights):
+            q = tuple(_mirror(p[a] + o[a], shape[a]) for a in range(len(shape)))
+            A[ip, np.ravel_multi_index(q, shape)] += w
+    return A
+
+
+@pytest.mark.parametrize("shape,offsets,weights", [
+    ((5, 6), [(0, 0), (-2, 1), (1, -2), (0, 2), (2, 0), (-1, -1)], [0.3, 0.1, 0.25, -0.15, 0.2, 0.05]),
+    ((4, 3, 5), [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)],
+     [0.4, 0.05, 0.15, 0.1, 0.1, 0.12, 0.08]),
+])
+def test_neumann_transpose_is_the_assembled_transpose(shape, offsets, weights):
+    """The zero-flux transpose equals A^T of the matrix assembled with
+    mirrored indices (asymmetric offsets and weights, so A^T != A), and the
+    dot-product identity <S x, y> = <x, S^T y> holds."""
+    A = _neumann_matrix(shape, offsets, weights)
+    rng = np.random.default_rng(25)
+    y = rng.random(shape)
+    got = oracle.neumann_transpose(y, offsets, weights)
+    assert np.max(np.abs(got.reshape(-1) - A.T @ y.reshape(-1))) <= 1e-14
+    x = rng.random(shape)
+    sx = oracle.sweep_neumann(x, offsets, weights, 1)
+    assert abs(np.sum(sx * y) - np.sum(x * got)) <= 1e-13 * abs(np.sum(sx * y))
+
+
+def test_neumann_loss_gradient_finite_differences():
+    """dL/du0 of L = 0.5 ||S^n u0 - t||^2 by central differences along random
+    directions and single coordinates (the loss is quadratic, so central
+    differences are exact up to rounding)."""
+    rng = np.random.default_rng(26)
+    shape = (6, 7, 5)
+    offsets, weights = inputs.OFFSETS_7PT, [0.3, 0.1, 0.15, 0.12, 0.08, 0.13, 0.12]
+    u0, t = rng.random(shape), rng.random(shape)
+    _, _, g = oracle.neumann_loss_gradient(u0, t, offsets, weights, 9)
+    L = lambda u: oracle.neumann_loss_gradient(u, t, offsets, weights, 9)[0]  # noqa: E731
+    eps = 1e-4
+    for _ in range(4):
+        d = rng.standard_normal(shape)
+        d /= np.linalg.norm(d)
+        fd = (L(u0 + eps * d) - L(u0 - eps * d)) / (2 * eps)
+        assert abs(fd - np.sum(g * d)) <= 1e-8 * abs(fd) + 1e-12
+    for p in ((0, 0, 0), (5, 6, 4), (2, 3, 1)):
+        e = np.zeros(shape)
+        e[p] = 1.0
+        fd = (L(u0 + eps * e) - L(u0 - eps * e)) / (2 * eps)
+        assert abs(fd - g[p]) <= 1e-8 * abs(fd) + 1e-12
+
+
 # ---------------------------------------------------------------- conservative face-averaged operator
 def _cons_matrix(shape, kappa, periodic):
     """S assembled column by column from the oracle's step (boundary value 0,
