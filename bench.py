@@ -557,6 +557,17 @@ def cavity_flow(dev, hbm_peak, n=16384, steps=3, nit=50):
                      "time_steps_per_s": steps / t, "grid": [n, n], "pressure_iterations": nit,
                      "hbm_frac": bytes_step * steps / t / 1e9 / hbm_peak,
                      "count": "interior points x (pressure iterations + 2) per time step"}
+        if dtype == torch.float64:
+            # FP64 instructions per cell counted by ncu
+            # (smsp__sass_thread_inst_executed_op_fp64_pred_on.sum over the
+            # cells of an 8192^2 step): source term 15, each pressure
+            # iteration 6, fused velocity update 30.  Every cell of the
+            # array runs them (boundary cells recompute clamped updates).
+            dp_step = n * n * (15 + 6 * nit + 30)
+            bound_s = dp_step / FP64_INSTR_PER_S
+            out[name].update({"bound": "alu", "dp_instr_per_cell_step": 15 + 6 * nit + 30,
+                              "alu_bound_ms_per_time_step": bound_s * 1e3,
+                              "alu_frac": bound_s * steps / t})
         c.close()
         del c
         torch.cuda.empty_cache()

@@ -92,10 +92,11 @@ typedef enum { ST_F32 = 0, ST_F64 = 1 } st_dtype;
  *                 i < 0 reads -1 - i, i >= n reads 2n - 1 - i, per axis);
  *                 needs every extent >= radius; constant weights, one time
  *                 level and single grids only (otherwise stencil_create
- *                 returns ST_ERR_UNSUPPORTED; the batched form ST_ERR_ARG;
- *                 stencil_step_ckpt and the adjoint ST_ERR_UNSUPPORTED);
+ *                 returns ST_ERR_UNSUPPORTED; the batched form ST_ERR_ARG);
  *                 2D grids take the one-thread-per-point kernel, 3D grids
- *                 single sweeps. */
+ *                 single sweeps; stencil_step_ckpt and stencil_adjoint
+ *                 give the gradient with respect to u_0 through the
+ *                 transpose of the mirror-then-sweep step. */
 typedef enum { ST_DIRICHLET = 0, ST_PERIODIC = 1, ST_NEUMANN = 2 } st_bc;
 
 /* stencil_create flags */
@@ -395,15 +396,20 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int ckpt_every, void* works
 /*
  * Defined by: the adjoint workload (see stencil_adjoint_workspace).
  * Reverse pass of a run recorded by stencil_step_ckpt with the same nsteps
- * and ckpt_every (it reads the workspace and never writes the checkpoints or
- * the kept levels, so it may run again on the same record).  lambda (in: dL/du_T, out: dL/du_0) and lambda_tmp are
+ * and ckpt_every (it never writes the interiors of the checkpoints or the
+ * kept levels, so it may run again on the same record; with ST_NEUMANN it
+ * refreshes their mirror ghosts from their interiors).  lambda (in: dL/du_T, out: dL/du_0) and lambda_tmp are
  * field-layout buffers of the grid's dtype; grad_coeff (may be NULL) is a
  * field-layout buffer of DOUBLES into which
  *     sum_t lambda_{t+1}[p] * sum_k beta_k u_t[p + o_k]     (= dL/dkappa_p)
  * is ACCUMULATED (+=).  The transpose step is
  *     lambda_t[q] = sum_k w_k(q - o_k) lambda_{t+1}[q - o_k],
  * over the points q - o_k that are interior (wrapped when periodic); ghost
- * cells are boundary data, not variables.  The current level is unchanged.
+ * cells are boundary data, not variables.  With ST_NEUMANN a step reads
+ * u[mirror(p + o_k)], so its transpose sends w_k lambda_{t+1}[p] to the
+ * mirror image: lambda_t[q] = sum_k w_k sum over the cells g with
+ * mirror(g) = q of lambda_{t+1}[g - o_k] (g - o_k interior; constant weights,
+ * so grad_coeff must be NULL).  The current level is unchanged.
  * workspace, lambda, lambda_tmp and grad_coeff are 16-byte aligned
  * (ST_ERR_ARG otherwise).
  */

@@ -944,7 +944,6 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stre
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_step_ckpt: nsteps >= 0, ckpt_every >= 1");
     if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_step_ckpt: one time level only");
     if (g->caller_ghosts) return fail(ST_ERR_UNSUPPORTED, "stencil_step_ckpt: not with ST_FLAG_CALLER_GHOSTS");
-    if (g->bc == ST_NEUMANN) return fail(ST_ERR_UNSUPPORTED, "stencil_step_ckpt: not with ST_NEUMANN");
     if (((uintptr_t)ws & 15u) != 0) return fail(ST_ERR_ARG, "stencil_step_ckpt: workspace not 16-byte aligned");
     st_status rc = check_ready(g, "stencil_step_ckpt");
     if (rc != ST_OK) return rc;
@@ -973,6 +972,8 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stre
                 void* out = j < seg ? (void*)(last + (size_t)(j - 1) * sb) : g->buf[fin];
                 if (j < seg && g->bc == ST_DIRICHLET)
                     ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, out, g->g, g->bc_value, s));
+                // zero flux: the input's ghosts mirror its interior before every sweep
+                if (g->bc == ST_NEUMANN) ST_CUDA_TRY(launch_mirror_ghosts(g->g.esize, const_cast<void*>(in), g->g, s));
                 SweepArgs a = sweep_args(g, in, out, g->step + j - 1);
                 ST_CUDA_TRY(launch_family(g->fam, a, s));
                 in = out;
@@ -991,7 +992,6 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     if (nsteps < 0 || m < 1) return fail(ST_ERR_ARG, "stencil_adjoint: nsteps >= 0, ckpt_every >= 1");
     if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: one time level only");
     if (g->caller_ghosts) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: not with ST_FLAG_CALLER_GHOSTS");
-    if (g->bc == ST_NEUMANN) return fail(ST_ERR_UNSUPPORTED, "stencil_adjoint: not with ST_NEUMANN");
     if (lambda == lambda_tmp) return fail(ST_ERR_ALIAS, "stencil_adjoint: lambda and lambda_tmp alias");
     if ((((uintptr_t)ws) | ((uintptr_t)lambda) | ((uintptr_t)lambda_tmp) | ((uintptr_t)grad)) & 15u)
         return fail(ST_ERR_ARG, "stencil_adjoint: buffers must be 16-byte aligned");
@@ -1030,6 +1030,7 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
             return (kept && j > 0) ? (void*)(last + (size_t)(j - 1) * sb) : state(c, j);
         };
         for (int j = 1; j < L && !kept; ++j) {
+            if (g->bc == ST_NEUMANN) ST_CUDA_TRY(launch_mirror_ghosts(g->g.esize, state(c, j - 1), g->g, s));
             SweepArgs a = sweep_args(g, state(c, j - 1), state(c, j), t0 + j - 1);
             ST_CUDA_TRY(launch_family(g->fam, a, s));
         }
@@ -1045,7 +1046,10 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
             a.gk = grad;
             a.steps = k;
             a.status = g->d_status;
-            ST_CUDA_TRY(launch_family_adjoint(g->fam, a, s));
+            if (g->bc == ST_NEUMANN)  // the transpose of the mirror-then-sweep step
+                ST_CUDA_TRY(launch_neumann_adjoint(g->g.esize, lin, lout, g->fam.gp, g->g.r, g->g.rz, s));
+            else
+                ST_CUDA_TRY(launch_family_adjoint(g->fam, a, s));
             std::swap(lin, lout);
             j -= k;
         }

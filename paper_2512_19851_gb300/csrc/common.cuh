@@ -96,6 +96,10 @@ cudaError_t launch_generic_sweep(int esize, const void* in, void* out, const voi
 cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_in, void* lam_out,
                                    const void* kappa, double* gk, const GenParams& P,
                                    cudaStream_t s);
+// Transposed step of the zero-flux (Neumann) sweep, constant weights: the
+// gather over the mirror pre-images of every interior cell.
+cudaError_t launch_neumann_adjoint(int esize, const void* lam_in, void* lam_out, const GenParams& P, int r, int rz,
+                                   cudaStream_t s);
 cudaError_t launch_fill_ghosts(int esize, void* buf, const Geom& g, double value, cudaStream_t s);
 cudaError_t launch_mirror_ghosts(int esize, void* buf, const Geom& g, cudaStream_t s);
 cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int dir, cudaStream_t s);

@@ -107,6 +107,56 @@ k_adjoint_generic(const T* __restrict__ u, const T* __restrict__ lam, T* __restr
     if (gk) gk[q] += (double)lam[q] * (double)s;
 }
 
+// Transposed step of the zero-flux sweep (constant weights).  The sweep
+// reads, for interior p and offset k, the cell mirror(p + o_k) (mirror per
+// axis: -1 - i below the interior, 2n - 1 - i above), so its transpose
+// gathers at q
+//   lambda_t[q] = sum_k w_k sum over the cells g with mirror(g) = q of
+//                 lambda_{t+1}[g - o_k]   (g - o_k interior),
+// where per axis g takes q itself and, within r of a face, q's reflection
+// across it (axes without ghosts, z in 2D, have only q).  Offsets in order,
+// pre-images in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adjoint_neumann(const T* __restrict__ lam, T* __restrict__ lout, const __grid_constant__ GenParams P, int r, int rz)
+{
+    ptx::griddep_wait();
+    ptx::griddep_trigger();
+    const int64_t x = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t y = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    const int64_t z = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    // pre-images of q per axis (at most three)
+    int64_t cz[3], cy[3], cx[3];
+    int nzc = 0, nyc = 0, nxc = 0;
+    auto pre = [](int64_t q, int64_t n, int rr, int64_t (&c)[3], int& m) {
+        c[m++] = q;
+        if (q <= rr - 1) c[m++] = -1 - q;
+        if (q >= n - rr) c[m++] = 2 * n - 1 - q;
+    };
+    pre(z, P.nz, rz, cz, nzc);
+    pre(y, P.ny, r, cy, nyc);
+    pre(x, P.nx, r, cx, nxc);
+    T acc = T(0);
+    for (int k = 0; k < P.npts; ++k) {
+        const T w = alpha_of<T>(P, k);
+        for (int a = 0; a < nzc; ++a) {
+            const int64_t pz = cz[a] - P.dz[k];
+            if (pz < 0 || pz >= P.nz) continue;
+            for (int b = 0; b < nyc; ++b) {
+                const int64_t py = cy[b] - P.dy[k];
+                if (py < 0 || py >= P.ny) continue;
+                for (int c = 0; c < nxc; ++c) {
+                    const int64_t px = cx[c] - P.dx[k];
+                    if (px < 0 || px >= P.nx) continue;
+                    acc = fma(w, lam[P.origin + pz * P.plane + py * P.pitch + px], acc);
+                }
+            }
+        }
+    }
+    lout[P.origin + z * P.plane + y * P.pitch + x] = acc;
+}
+
 // Write `value` into every cell of a padded buffer that is not interior: the
 // whole rows of the z ghost planes and of the y ghost rows, then the lead and
 // tail columns of the interior rows.  Flat grid-stride loops over those cells
@@ -499,6 +549,18 @@ cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_i
                                 (const double*)lam_in, (double*)lam_out, (const double*)kappa, gk, P);
     return launch_dependent(k_adjoint_generic<float>, grid, block, 0, s, (const float*)u_t, (const float*)lam_in,
                             (float*)lam_out, (const float*)kappa, gk, P);
+}
+
+cudaError_t launch_neumann_adjoint(int esize, const void* lam_in, void* lam_out, const GenParams& P, int r, int rz,
+                                   cudaStream_t s)
+{
+    if (P.nz * P.ny * P.nx == 0) return cudaSuccess;
+    const dim3 grid = point_grid(P), block(32, 8);
+    if (esize == 8)
+        return launch_dependent(k_adjoint_neumann<double>, grid, block, 0, s, (const double*)lam_in, (double*)lam_out,
+                                P, r, rz);
+    return launch_dependent(k_adjoint_neumann<float>, grid, block, 0, s, (const float*)lam_in, (float*)lam_out, P, r,
+                            rz);
 }
 
 cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int dir, cudaStream_t s)

@@ -150,3 +150,38 @@ def test_neumann_conserves_heat_at_size():
     got, kern = run_neumann(u0, inputs.OFFSETS_7PT, [1 - 6 * a] + [a] * 6, torch.float64, [100])
     assert abs(got.sum() - u0.sum()) <= 1e-12 * u0.sum(), kern
     assert np.max(np.abs(got - (1.0 + lam ** 100 * (u0 - 1.0)))) <= 1e-12, kern
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape,stencil,steps,m", [
+    ((37, 53), (inputs.OFFSETS_5PT, [0.2] * 5), 12, 5),
+    ((23, 29), ASYM2, 9, 4),
+    ((14, 17, 19), (inputs.OFFSETS_7PT, [0.4] + [0.1] * 6), 10, 3),
+    ((9, 12, 70), (inputs.OFFSETS_7PT, [0.3, 0.1, 0.15, 0.12, 0.08, 0.13, 0.12]), 8, 8),
+])
+def test_neumann_adjoint_matches_oracle(dtype, shape, stencil, steps, m):
+    """Checkpointed zero-flux run and its reverse pass (the transpose of the
+    mirror-then-sweep step): the loss and dL/du0 against the oracle's
+    scatter transpose; lambda_0 bitwise independent of the checkpoint
+    interval (every transposed step is one launch of the same kernel and
+    recomputed states equal the forward run's)."""
+    from paper_2512_19851_gb300.grid import VarCoefProblem
+    rng = np.random.default_rng(34)
+    u0, t = rng.random(shape), rng.random(shape)
+    offs, w = stencil
+    loss_r, uT_r, lam_r = oracle.neumann_loss_gradient(u0, t, offs, w, steps)
+    out = []
+    for mm in (m, 1, steps):
+        g = Grid(shape, offs, w, dtype=dtype, neumann=True)
+        p = VarCoefProblem(g, steps, mm)
+        uT = p.forward(u0).double().cpu().numpy()
+        lam0, _, loss = p.backward_from(target=t)
+        g.sync()
+        out.append((uT, lam0.double().cpu().numpy(), float(loss.cpu()[0])))
+        g.close()
+    uT, lam0, loss = out[0]
+    tol = TOL[dtype]
+    assert rel_err(uT, uT_r) <= tol
+    assert abs(loss - loss_r) <= tol * loss_r
+    assert rel_err(lam0, lam_r) <= tol
+    assert np.array_equal(lam0, out[1][1]) and np.array_equal(lam0, out[2][1])
