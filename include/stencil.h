@@ -128,6 +128,7 @@ typedef enum { ST_DIRICHLET = 0, ST_PERIODIC = 1, ST_NEUMANN = 2 } st_bc;
                                 times both and keeps the faster either way.
                                 Ignored for other grids */
 
+
 #define ST_MAX_POINTS 64     /* most neighbour points per stencil */
 #define ST_MAX_RADIUS 8      /* widest ghost region */
 
@@ -158,8 +159,8 @@ const char* stencil_last_error(void);
  *   bc          ST_DIRICHLET (ghosts = bc_value), ST_PERIODIC or ST_NEUMANN.
  *   dtype       storage and arithmetic type of the fields.
  *   time_levels 1: form (1); 2: leapfrog form (3).
- *   flags       0 or a combination of ST_FLAG_GENERIC, ST_FLAG_TWO_STEP and
- *               ST_FLAG_CALLER_GHOSTS.
+ *   flags       0 or a combination of ST_FLAG_GENERIC, ST_FLAG_TWO_STEP,
+ *               ST_FLAG_CALLER_GHOSTS and ST_FLAG_TILE_PASSES.
  * Copies all arrays; allocates only library scratch.  *out is NULL on error.
  */
 st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radius, int npts,
@@ -327,8 +328,11 @@ st_status stencil_sync(st_grid_t g);
  * Interior reductions in double precision over a (and b, if not NULL), two
  * buffers in this grid's layout and dtype:
  *   dev_out[0] = sum (a - b), dev_out[1] = sum (a - b)^2, dev_out[2] = max |a - b|.
- * dev_out: 3 doubles in device memory.  Deterministic: fixed block partials
- * summed in a fixed order by a second pass.
+ * dev_out: 3 doubles in device memory.  a and b must be 16-byte aligned
+ * (ST_ERR_ARG otherwise; buffers from the library's own allocations and
+ * torch's are).  Deterministic: fixed block partials summed in a fixed order
+ * by a second pass.  A timed-out wait inside the FP32 kernel is reported by
+ * the next stencil_sync (ST_ERR_DEVICE_TIMEOUT).
  */
 st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_out,
                          void* stream);
@@ -344,8 +348,9 @@ st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_
  * handle scratch that its first call allocates; this entry point takes them
  * from a static device array instead and calls no cudaMalloc, cudaFree or
  * other allocating routine.
- *   Same arguments and results as stencil_reduce (a, b: field-layout buffers
- *   of the grid's dtype, b may be NULL; dev_out: 3 doubles in device memory).
+ *   Same arguments and results as stencil_reduce (a, b: 16-byte aligned
+ *   field-layout buffers of the grid's dtype, b may be NULL; dev_out: 3
+ *   doubles in device memory).
  *   Scratch: a static array of 4096 block partials (96 KB, held by every
  *   GPU that loads the library until the process exits).  The blocks walk
  *   the interior rows in a grid-stride loop, so grids of every size fit it
@@ -366,6 +371,7 @@ st_status stencil_reduce_noalloc(st_grid_t g, const void* a, const void* b, doub
  * counterpart in the paper.
  * Loss residual: lambda = u - target on the interior (lambda's ghosts set to
  * 0) and dev_loss[0] = 0.5 * sum (u - target)^2 in double precision.
+ * u, target and lambda must be 16-byte aligned (ST_ERR_ARG otherwise).
  */
 st_status stencil_residual(st_grid_t g, const void* u, const void* target, void* lambda,
                            double* dev_loss, void* stream);
@@ -389,7 +395,11 @@ st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int ckpt_every, siz
  * stencil_adjoint_workspace); each step is the sweep of stencil_step.
  * Forward nsteps from the current level, storing u at t = 0, m, 2m, ... and
  * the inner levels of the last segment in `workspace` (device,
- * >= stencil_adjoint_workspace bytes, 16-byte aligned). */
+ * >= stencil_adjoint_workspace bytes, 16-byte aligned).  With two segments
+ * or more it also stores the inner levels of the second-to-last segment, in
+ * the recomputation levels (idle until the reverse pass reaches that
+ * segment), so that the first stencil_adjoint on this record recomputes one
+ * segment fewer; the handle remembers which workspace holds them. */
 st_status stencil_step_ckpt(st_grid_t g, int nsteps, int ckpt_every, void* workspace,
                             void* stream);
 
@@ -397,8 +407,11 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int ckpt_every, void* works
  * Defined by: the adjoint workload (see stencil_adjoint_workspace).
  * Reverse pass of a run recorded by stencil_step_ckpt with the same nsteps
  * and ckpt_every (it never writes the interiors of the checkpoints or the
- * kept levels, so it may run again on the same record; with ST_NEUMANN it
- * refreshes their mirror ghosts from their interiors).  lambda (in: dL/du_T, out: dL/du_0) and lambda_tmp are
+ * last segment's levels, so it may run again on the same record; the
+ * second-to-last segment is read from the recomputation levels on the first
+ * reverse pass after the record and recomputed on later ones, whose
+ * recomputations have overwritten them; with ST_NEUMANN it refreshes the
+ * mirror ghosts of the levels it reads from their interiors).  lambda (in: dL/du_T, out: dL/du_0) and lambda_tmp are
  * field-layout buffers of the grid's dtype; grad_coeff (may be NULL) is a
  * field-layout buffer of DOUBLES into which
  *     sum_t lambda_{t+1}[p] * sum_k beta_k u_t[p + o_k]     (= dL/dkappa_p)

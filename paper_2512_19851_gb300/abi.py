@@ -262,7 +262,7 @@ def stencil_reduce(h, a_ptr, b_ptr, out_ptr, stream=None) -> None:
 
 
 def stencil_reduce_noalloc(h, a_ptr, b_ptr, out_ptr, stream=None) -> None:
-    """stencil_reduce without device allocation (static scratch, <= 2^28 points)."""
+    """stencil_reduce without device allocation (partials in a static device array)."""
     _check(lib().stencil_reduce_noalloc(h, ctypes.c_void_p(int(a_ptr)),
                                         ctypes.c_void_p(int(b_ptr) if b_ptr else None),
                                         ctypes.c_void_p(int(out_ptr)), ctypes.c_void_p(_stream(stream))),

@@ -102,6 +102,12 @@ struct st_grid_s {
     // one-thread-per-point kernel; plan_use tells which runs
     bool plan_optional = false;
     bool plan_use = true;
+    // the workspace whose recomputation levels hold the inner states of the
+    // second-to-last segment, written by the last stencil_step_ckpt (run of
+    // kept2_n steps, checkpoints every kept2_m); cleared once a reverse pass
+    // overwrites them
+    const void* kept2_ws = nullptr;
+    int kept2_n = 0, kept2_m = 0;
     bool pairs = false;         // two-step passes chosen by stencil_tune (3D 7-point heat, FP32)
     bool caller_ghosts = false; // ST_FLAG_CALLER_GHOSTS: Dirichlet ghost cells hold the caller's values
     void* staging = nullptr;    // dense interior buffer of stencil_run_host
@@ -896,11 +902,12 @@ st_status stencil_sync(st_grid_t g)
 st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_out, void* stream)
 {
     if (!g || !a || !dev_out) return fail(ST_ERR_ARG, "stencil_reduce: NULL argument");
+    if ((((uintptr_t)a) | ((uintptr_t)b)) & 15u) return fail(ST_ERR_ARG, "stencil_reduce: a, b must be 16-byte aligned");
     st_status rc = ensure_scratch(g);
     if (rc != ST_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     g->last = s;
-    ST_CUDA_TRY(launch_reduce(g->g.esize, a, b, g->g, g->d_partials, g->red_blocks, dev_out, 0, nullptr, s));
+    ST_CUDA_TRY(launch_reduce(g->g.esize, a, b, g->g, g->d_partials, g->red_blocks, dev_out, 0, nullptr, g->d_status, s));
     return ST_OK;
 }
 
@@ -909,12 +916,14 @@ st_status stencil_residual(st_grid_t g, const void* u, const void* target, void*
 {
     if (!g || !u || !target || !lambda || !dev_loss) return fail(ST_ERR_ARG, "stencil_residual: NULL argument");
     if (lambda == u || lambda == target) return fail(ST_ERR_ALIAS, "stencil_residual: lambda aliases an input");
+    if ((((uintptr_t)u) | ((uintptr_t)target) | ((uintptr_t)lambda)) & 15u)
+        return fail(ST_ERR_ARG, "stencil_residual: u, target, lambda must be 16-byte aligned");
     st_status rc = ensure_scratch(g);
     if (rc != ST_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     g->last = s;
     ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, lambda, g->g, 0.0, s));
-    ST_CUDA_TRY(launch_reduce(g->g.esize, u, target, g->g, g->d_partials, g->red_blocks, dev_loss, 1, lambda, s));
+    ST_CUDA_TRY(launch_reduce(g->g.esize, u, target, g->g, g->d_partials, g->red_blocks, dev_loss, 1, lambda, g->d_status, s));
     return ST_OK;
 }
 
@@ -955,21 +964,28 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stre
     const size_t bytes = (size_t)g->g.elems * g->g.esize;
     const int64_t nck = (nsteps + m - 1) / m;
     char* last = (char*)ws + ws_last_offset(nck, m, sb);  // states t0 + 1 .. t0 + L - 1 of the last segment
+    char* rec = (char*)ws + (size_t)nck * sb;               // the recomputation levels
+    g->kept2_ws = nullptr;
     for (int t = 0; t < nsteps; t += m) {
         ST_CUDA_TRY(cudaMemcpyAsync((char*)ws + (size_t)(t / m) * sb, g->buf[g->cur], bytes,
                                     cudaMemcpyDeviceToDevice, s));
         const int seg = std::min(m, nsteps - t);
-        if (t + m < nsteps) {
+        const int64_t c = t / m;
+        if (c < nck - 2) {
             rc = enqueue_steps(g, g->cur, g->step, seg, s);
             if (rc != ST_OK) return rc;
         } else {
-            // the last segment: its inner states go to the workspace, where the
-            // reverse pass reads them instead of recomputing them; the final
-            // state lands in the slot a plain run would leave it in
+            // the last two segments: their inner states go to the workspace
+            // (the last segment's to its own levels, the one before to the
+            // recomputation levels, which the reverse pass does not need
+            // until it reaches that segment), where the reverse pass reads
+            // them instead of recomputing them; the final state lands in the
+            // slot a plain run would leave it in
+            char* keep = c == nck - 1 ? last : rec;
             const int fin = final_slot(g, g->cur, seg);
             const void* in = g->buf[g->cur];
             for (int j = 1; j <= seg; ++j) {
-                void* out = j < seg ? (void*)(last + (size_t)(j - 1) * sb) : g->buf[fin];
+                void* out = j < seg ? (void*)(keep + (size_t)(j - 1) * sb) : g->buf[fin];
                 if (j < seg && g->bc == ST_DIRICHLET)
                     ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, out, g->g, g->bc_value, s));
                 // zero flux: the input's ghosts mirror its interior before every sweep
@@ -981,6 +997,11 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int m, void* ws, void* stre
         }
         g->cur = final_slot(g, g->cur, seg);
         g->step += seg;
+    }
+    if (nck >= 2) {
+        g->kept2_ws = ws;
+        g->kept2_n = nsteps;
+        g->kept2_m = m;
     }
     return ST_OK;
 }
@@ -1022,14 +1043,20 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     void* lin = lambda;
     void* lout = lambda_tmp;
     char* last = base + ws_last_offset(nck, m, sb);  // the last segment's states, kept by the forward run
+    // the second-to-last segment's states are in the recomputation levels if
+    // the forward run that filled this workspace left them there and no
+    // reverse pass has recomputed another segment into them since
+    const bool kept2 = nck >= 2 && g->kept2_ws == ws && g->kept2_n == nsteps && g->kept2_m == m;
+    if (nck >= 3) g->kept2_ws = nullptr;
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t t0 = c * m;
         const int L = (int)std::min<int64_t>(m, nsteps - t0);
         const bool kept = c == nck - 1;
+        const bool recompute = !kept && !(kept2 && c == nck - 2);
         auto st = [&](int j) -> void* {
             return (kept && j > 0) ? (void*)(last + (size_t)(j - 1) * sb) : state(c, j);
         };
-        for (int j = 1; j < L && !kept; ++j) {
+        for (int j = 1; j < L && recompute; ++j) {
             if (g->bc == ST_NEUMANN) ST_CUDA_TRY(launch_mirror_ghosts(g->g.esize, state(c, j - 1), g->g, s));
             SweepArgs a = sweep_args(g, state(c, j - 1), state(c, j), t0 + j - 1);
             ST_CUDA_TRY(launch_family(g->fam, a, s));
@@ -1409,5 +1436,6 @@ st_status stencil_batch_sync(st_batch_t b)
 namespace st {
 // Accessors for translation units that do not see st_grid_s.
 const Geom* grid_geom(st_grid_t g) { return &g->g; }
+int* grid_status(st_grid_t g) { return g->d_status; }
 void grid_note_stream(st_grid_t g, cudaStream_t s) { g->last = s; }
 }  // namespace st

@@ -106,7 +106,9 @@ cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int
 // Grid size of the reduction kernels for grid g: the blocks resident at once
 // on this GPU, at most max_blocks and at most one per eight interior rows.
 int reduce_blocks(const Geom& g, int max_blocks);
+// status: the grid's device status word (a timed-out wait of the FP32 ring
+// kernel records ST_ERR_DEVICE_TIMEOUT there); may be NULL.
 cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g, double* partials,
-                          int nblocks, double* out, int mode, void* lam_out, cudaStream_t s);
+                          int nblocks, double* out, int mode, void* lam_out, int* status, cudaStream_t s);
 
 }  // namespace st

@@ -281,74 +281,18 @@ __device__ Red3 block_red(Red3 v)
     return w;  // valid in thread 0
 }
 
-// Compensated single-precision accumulator (hi + lo carries ~48 bits): the
-// per-element work of an FP32 reduction stays on the FP32 pipe, because the
-// FP64 rate of this GPU is 1/64 of FP32.  Error-free transformations:
-// TwoSum (Knuth) for additions, fma for the exact product error.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-// The sum and the sum of squares are two independent compensated pairs that
-// take the same operations, so they run side by side in packed FP32x2
-// instructions (one instruction per pair; each lane rounds exactly as the
-// scalar operation would).  a - b is formed as fma(b, -1, a), which rounds
+// FP32 reductions accumulate in compensated single precision (hi + lo
+// carries about 48 bits): the per-element work stays on the FP32 pipe,
+// because the FP64 rate of this GPU is 1/64 of FP32.  Error-free
+// transformations: TwoSum (Knuth) for additions, fma for the exact product
+// error.  They run in packed FP32x2 instructions (each lane rounds exactly as
+// the scalar operation would); a - b is formed as fma(b, -1, a), which rounds
 // a - b once, as a subtraction does.
 __device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
-// (hi, lo) += x + xlo for both pairs at once: lane 0 is the sum, lane 1 the
-// sum of squares.  TwoSum of hi and x, then lo += err + xlo.
-__device__ __forceinline__ void f2_add2(float2& hi, float2& lo, float2 x, float2 xlo)
-{
-    const float2 s = p_add(hi, x);
-    const float2 bb = p_sub(s, hi);
-    const float2 e = p_add(p_sub(hi, p_sub(s, bb)), p_sub(x, bb));
-    hi = s;
-    lo = p_add(lo, p_add(e, xlo));
-}
-
-// Per-element accumulation: FP32 inputs use the compensated float pair,
-// FP64 inputs plain double.
-struct AccF {
-    float2 H{0.f, 0.f}, L{0.f, 0.f};  // (sum, sum of squares): high and low parts
-    // max |d| kept exactly in single precision: |d| = |dh| + sign(dh) dl with
-    // |dl| at most half the float spacing around dh, so ordering by |dh| first
-    // and sign(dh) dl second orders the exact |d| (a rounding interval never
-    // reaches past the gap to the next float)
-    float mA = 0.f, mS = 0.f;
-    __device__ __forceinline__ float add(float av, float bv)
-    {
-        float dh, dl;
-        two_sum(av, -bv, dh, dl);  // d = dh + dl exactly
-        const float p = dh * dh;
-        const float pe = fmaf(dh, dh, -p);  // dh^2 = p + pe exactly
-        f2_add2(H, L, make_float2(dh, p), make_float2(dl, pe + 2.f * dh * dl));
-        const float A = fabsf(dh);
-        const float sg = dh < 0.f ? -dl : dl;
-        const bool gt = A > mA || (A == mA && sg > mS);
-        mA = gt ? A : mA;
-        mS = gt ? sg : mS;
-        return dh;
-    }
-    // the same with b = 0 (then d = a exactly, dl = 0): fewer operations, the
-    // same results
-    __device__ __forceinline__ float add1(float av)
-    {
-        const float p = av * av;
-        f2_add2(H, L, make_float2(av, p), make_float2(0.f, fmaf(av, av, -p)));
-        mA = fmaxf(mA, fabsf(av));
-        return av;
-    }
-    __device__ __forceinline__ Red3 result() const
-    {
-        return Red3{(double)H.x + (double)L.x, (double)H.y + (double)L.y, (double)mA + (double)mS};
-    }
-};
-
+// FP64 reductions: plain double accumulation (three FP64 operations per
+// element; the FP64 pipe, not the loads, sets their pace).
 struct AccD {
     Red3 r{0.0, 0.0, 0.0};
     __device__ __forceinline__ double add(double av, double bv)
@@ -366,18 +310,13 @@ struct AccD {
 template <typename T>
 struct VecOf;
 template <>
-struct VecOf<float> {
-    typedef float4 V;
-    typedef AccF Acc;
-    static constexpr int N = 4;
-};
-template <>
 struct VecOf<double> {
     typedef double2 V;
     typedef AccD Acc;
     static constexpr int N = 2;
 };
 
+// FP64 fields (k_reduce_ring takes FP32).
 // mode 0: d = a - b (b may be null); mode 1: also lam_out = d on the interior.
 // Each warp walks whole interior rows; each lane loads 16-byte vectors, four
 // per trip, so several loads are in flight (interior rows start 16-byte
@@ -447,9 +386,439 @@ k_reduce_partial(const T* __restrict__ a, const T* __restrict__ b, Geom g, doubl
     }
 }
 
+// FP32 reductions through a shared-memory ring filled by bulk copies.  Two
+// persistent blocks per SM: lane 0 of the last warp of a block copies work
+// items into an NS-stage ring, RR_CW consumer warps accumulate the interior
+// elements of each stage.  The bytes in flight per SM are set by the rings
+// (several stages), not by the consumers' registers, which is what a plain
+// load loop runs short of.
+//
+// A work item is either a run of whole padded rows of one plane (rpi rows,
+// ghost columns included: they share the DRAM sectors of the interior's first
+// and last elements, so copying them adds no traffic) or, when a padded row
+// is longer than a stage, one segment of an interior row.  Consumer warp w
+// takes rows w, w + RR_CW, ... of a row item, or the w-th slice of a segment;
+// its lanes walk 16-byte vectors of the row.
+struct RedRing {
+    int64_t nz, ny, nx, pitch, plane, origin, xl, r, rz;
+    int se;        // elements per array per stage (a multiple of 4)
+    int ns;        // stages
+    int rpi;       // rows per item; 0: row segments of se elements
+    int nseg;      // segments per interior row (segment items)
+    int64_t ipp;   // items per plane (row items)
+    int64_t items;
+    int mode;      // 1: also lam_out = a - b on the interior
+    int* status;   // set to ST_ERR_DEVICE_TIMEOUT when a wait runs out
+};
+constexpr int RR_CW = 16;  // consumer warps per block
+
+// Position of a work item as (plane z, b, c): row items b = item in the plane,
+// c = 0; segment items b = row in the plane, c = segment.  A block visits
+// items blockIdx.x, blockIdx.x + gridDim.x, ...; the walk advances (z, b, c)
+// by the grid size in mixed radix (nb, nc) without dividing per item (all
+// three fit in 32 bits: nz <= 65535, ny <= 2^24).
+struct ItemWalk {
+    int z, b, c;
+    int nb, nc;
+    int dz, db, dc;
+    __device__ __forceinline__ void init(const RedRing& P)
+    {
+        nb = (int)(P.rpi > 0 ? P.ipp : P.ny);
+        nc = P.rpi > 0 ? 1 : P.nseg;
+        const int64_t it = blockIdx.x, G = gridDim.x;
+        c = (int)(it % nc);
+        b = (int)((it / nc) % nb);
+        z = (int)(it / nc / nb);
+        dc = (int)(G % nc);
+        db = (int)((G / nc) % nb);
+        dz = (int)(G / nc / nb);
+    }
+    __device__ __forceinline__ void next()
+    {
+        c += dc;
+        const int carry = c >= nc;
+        c -= carry ? nc : 0;
+        b += db + carry;
+        z += dz;
+        if (b >= nb) {
+            b -= nb;
+            ++z;
+        }
+    }
+};
+
+struct RedItem {
+    int64_t gsrc;    // element index of the first copied element
+    int64_t gbase;   // element index of interior x = x0 of the item's first row
+    uint32_t bytes;  // bytes per array
+    int nrows, sstride, sx0, nxe;
+};
+
+// The layout fields an item needs, copied out of the kernel parameters once
+// so that they live in registers (a parameter struct read through a
+// reference each item costs a memory access per field).
+struct RedGeo {
+    int64_t plane, pitch, origin;
+    int ny, nx, rpi, se, xl, r, rz;
+};
+
+__device__ __forceinline__ RedItem red_item(const RedGeo& G, const ItemWalk& w)
+{
+    RedItem I;
+    if (G.rpi > 0) {
+        const int64_t y0 = (int64_t)w.b * G.rpi;
+        I.nrows = (int)(G.ny - y0 < G.rpi ? G.ny - y0 : G.rpi);
+        I.gsrc = ((int64_t)w.z + G.rz) * G.plane + (y0 + G.r) * G.pitch;
+        I.gbase = I.gsrc + G.xl;
+        I.bytes = (uint32_t)(I.nrows * G.pitch * 4);
+        I.sstride = (int)G.pitch;
+        I.sx0 = G.xl;
+        I.nxe = G.nx;
+    } else {
+        const int64_t x0 = (int64_t)w.c * G.se;
+        I.nxe = (int)(G.nx - x0 < G.se ? G.nx - x0 : G.se);
+        I.gsrc = G.origin + (int64_t)w.z * G.plane + (int64_t)w.b * G.pitch + x0;
+        I.gbase = I.gsrc;
+        I.bytes = (uint32_t)(((I.nxe + 3) & ~3) * 4);
+        I.nrows = 1;
+        I.sstride = 0;
+        I.sx0 = 0;
+    }
+    return I;
+}
+
+// How the consumer warps share an item of nrows rows of nxe elements: wpr
+// warps per row (rows fewer than warps, or one long segment), warp w takes
+// slice w % wpr of rows w / wpr, w / wpr + jstep, ...; its lanes walk the
+// 16-byte vectors [vb, ve) of the slice.
+struct WarpShare {
+    int j0, jstep, vb, ve, nfull, rem, slice, active;
+    __device__ __forceinline__ void set(int nrows, int nxe, int warp)
+    {
+        nfull = nxe >> 2;
+        rem = nxe - 4 * nfull;
+        const int wpr = RR_CW / min(nrows, RR_CW);
+        jstep = RR_CW / wpr;
+        slice = warp % wpr;
+        j0 = warp / wpr;
+        active = warp < wpr * jstep;
+        const int q = (nfull + wpr - 1) / wpr;
+        vb = slice * q;
+        ve = min(nfull, vb + q);
+    }
+};
+
+// Compensated accumulation of two interleaved element streams: the even and
+// the odd elements of a row each have their own (hi, lo) pairs for the sum
+// and the sum of squares, so one packed FP32x2 instruction advances both
+// (a quarter fewer instructions per element than one stream carrying the sum
+// and the sum of squares side by side).  TwoSum for the additions, fma for
+// the exact square error.
+struct AccP {
+    float2 Hs{0.f, 0.f}, Ls{0.f, 0.f}, Hq{0.f, 0.f}, Lq{0.f, 0.f};
+    // max |d| kept exactly in single precision: |d| = |dh| + sign(dh) dl with
+    // |dl| at most half the float spacing around dh, so ordering by |dh| first
+    // and sign(dh) dl second orders the exact |d| (a rounding interval never
+    // reaches past the gap to the next float)
+    float mA = 0.f, mS = 0.f;
+    // hi + lo += x + xlo
+    __device__ __forceinline__ static void add(float2& hi, float2& lo, float2 x, float2 xlo)
+    {
+        const float2 s = p_add(hi, x);
+        const float2 bb = p_sub(s, hi);
+        const float2 e = p_add(p_sub(hi, p_sub(s, bb)), p_sub(x, bb));
+        hi = s;
+        lo = p_add(lo, p_add(e, xlo));
+    }
+    // hi + lo += x (no low part)
+    __device__ __forceinline__ static void add0(float2& hi, float2& lo, float2 x)
+    {
+        const float2 s = p_add(hi, x);
+        const float2 bb = p_sub(s, hi);
+        const float2 e = p_add(p_sub(hi, p_sub(s, bb)), p_sub(x, bb));
+        hi = s;
+        lo = p_add(lo, e);
+    }
+    // two elements of a (b = 0)
+    __device__ __forceinline__ void put1(float2 x)
+    {
+        const float2 p = __fmul2_rn(x, x);
+        const float2 pe = __ffma2_rn(x, x, make_float2(-p.x, -p.y));  // x^2 = p + pe exactly
+        add0(Hs, Ls, x);
+        add(Hq, Lq, p, pe);
+        mA = fmaxf(mA, fmaxf(fabsf(x.x), fabsf(x.y)));
+    }
+    // two elements of a - b; returns the rounded differences
+    __device__ __forceinline__ float2 put2(float2 a, float2 b)
+    {
+        // d = dh + dl exactly (TwoSum of a and -b)
+        const float2 dh = p_sub(a, b);
+        const float2 bb = p_sub(dh, a);
+        const float2 dl = p_sub(p_sub(a, p_sub(dh, bb)), p_add(b, bb));
+        const float2 p = __fmul2_rn(dh, dh);
+        float2 pe = __ffma2_rn(dh, dh, make_float2(-p.x, -p.y));
+        pe = __ffma2_rn(p_add(dh, dh), dl, pe);  // d^2 = p + pe + dl^2 (dl^2 below the pair's precision)
+        add(Hs, Ls, dh, dl);
+        add(Hq, Lq, p, pe);
+        max1(dh.x, dl.x);
+        max1(dh.y, dl.y);
+        return dh;
+    }
+    __device__ __forceinline__ void max1(float dh, float dl)
+    {
+        const float A = fabsf(dh);
+        const float sg = dh < 0.f ? -dl : dl;
+        const bool gt = A > mA || (A == mA && sg > mS);
+        mA = gt ? A : mA;
+        mS = gt ? sg : mS;
+    }
+    // one element (a row's ragged end)
+    __device__ __forceinline__ float put_one(float a, float b, bool has_b)
+    {
+        if (has_b) return put2(make_float2(a, 0.f), make_float2(b, 0.f)).x;
+        put1(make_float2(a, 0.f));
+        return a;
+    }
+};
+
+// A compensated single-precision value hi + lo and its sum (TwoSum of the
+// high parts, the low parts added): the block's partial sums are combined in
+// single precision, and converted to double once per block, because every
+// FP64 instruction runs on this GPU's narrow FP64 pipe.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return FF{s, (a.lo + b.lo) + e};
+}
+
+// The block's (sum, sum of squares, max |d|) from every thread's AccP;
+// valid in thread 0.
+__device__ Red3 block_red_ff(const AccP& acc)
+{
+    __shared__ float sh[6][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    FF S = ff_add(FF{acc.Hs.x, acc.Ls.x}, FF{acc.Hs.y, acc.Ls.y});
+    FF Q = ff_add(FF{acc.Hq.x, acc.Lq.x}, FF{acc.Hq.y, acc.Lq.y});
+    float mA = acc.mA, mS = acc.mS;
+    auto fold = [&](int o) {
+        const FF S2{__shfl_down_sync(0xffffffffu, S.hi, o), __shfl_down_sync(0xffffffffu, S.lo, o)};
+        const FF Q2{__shfl_down_sync(0xffffffffu, Q.hi, o), __shfl_down_sync(0xffffffffu, Q.lo, o)};
+        const float A2 = __shfl_down_sync(0xffffffffu, mA, o), B2 = __shfl_down_sync(0xffffffffu, mS, o);
+        S = ff_add(S, S2);
+        Q = ff_add(Q, Q2);
+        const bool gt = A2 > mA || (A2 == mA && B2 > mS);
+        mA = gt ? A2 : mA;
+        mS = gt ? B2 : mS;
+    };
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fold(o);
+    if (lane == 0) {
+        sh[0][wid] = S.hi;
+        sh[1][wid] = S.lo;
+        sh[2][wid] = Q.hi;
+        sh[3][wid] = Q.lo;
+        sh[4][wid] = mA;
+        sh[5][wid] = mS;
+    }
+    __syncthreads();
+    Red3 r{0.0, 0.0, 0.0};
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        const bool in = lane < nw;
+        S = FF{in ? sh[0][lane] : 0.f, in ? sh[1][lane] : 0.f};
+        Q = FF{in ? sh[2][lane] : 0.f, in ? sh[3][lane] : 0.f};
+        mA = in ? sh[4][lane] : 0.f;
+        mS = in ? sh[5][lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fold(o);
+        r = Red3{(double)S.hi + (double)S.lo, (double)Q.hi + (double)Q.lo, (double)mA + (double)mS};
+    }
+    return r;
+}
+
+// One 16-byte vector v of a staged row (a at ra, b at ra + bofs): accumulate
+// a - b (or a) and, in mode 1, store the differences at lo.
+template <bool HAS_B>
+__device__ __forceinline__ void red_vec(AccP& acc, const float* ra, int bofs, int v, bool mode1, float* lo)
+{
+    const float4 x = *reinterpret_cast<const float4*>(ra + 4 * v);
+    if (HAS_B) {
+        const float4 y = *reinterpret_cast<const float4*>(ra + bofs + 4 * v);
+        const float2 d0 = acc.put2(make_float2(x.x, x.y), make_float2(y.x, y.y));
+        const float2 d1 = acc.put2(make_float2(x.z, x.w), make_float2(y.z, y.w));
+        if (mode1) *reinterpret_cast<float4*>(lo + 4 * v) = make_float4(d0.x, d0.y, d1.x, d1.y);
+    } else {
+        acc.put1(make_float2(x.x, x.y));
+        acc.put1(make_float2(x.z, x.w));
+    }
+}
+
+// Vectors v, v + 32, v + 64 and v + 96 of a staged row, all loads first
+// (one field).
+template <bool HAS_B>
+__device__ __forceinline__ void red_vec4(AccP& acc, const float* ra, int, int v, bool, float*)
+{
+    static_assert(!HAS_B, "one field only");
+    float4 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const float4*>(ra + 4 * (v + 32 * u));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        acc.put1(make_float2(x[u].x, x[u].y));
+        acc.put1(make_float2(x[u].z, x[u].w));
+    }
+}
+
+// One element x of a row's ragged end.
+template <bool HAS_B>
+__device__ __forceinline__ void red_tail(AccP& acc, const float* ra, int bofs, int x, bool mode1, float* lo)
+{
+    const float d = acc.put_one(ra[x], HAS_B ? ra[bofs + x] : 0.f, HAS_B);
+    if (mode1) lo[x] = d;
+}
+
+// A partial item (a plane's last rows, a row's last segment), out of line so
+// that its bookkeeping does not take registers from the whole-item loop.
+template <bool HAS_B>
+__device__ __noinline__ AccP red_partial(AccP acc, const RedGeo G, const ItemWalk w, const float* stg, int warp,
+                                         int lane, bool mode1, float* lam_out)
+{
+    const RedItem I = red_item(G, w);
+    stg += I.sx0;
+    WarpShare sh;
+    sh.set(I.nrows, I.nxe, warp);
+    for (int j = sh.j0; sh.active && j < I.nrows; j += sh.jstep) {
+        const float* ra = stg + j * I.sstride;
+        float* lo = lam_out + I.gbase + (int64_t)j * G.pitch;
+        for (int v = sh.vb + lane; v < sh.ve; v += 32) red_vec<HAS_B>(acc, ra, G.se, v, mode1, lo);
+        // the row's ragged end (fewer than 4 elements), by the row's first slice
+        if (sh.rem > 0 && sh.slice == 0 && lane < sh.rem) red_tail<HAS_B>(acc, ra, G.se, 4 * sh.nfull + lane, mode1, lo);
+    }
+    return acc;
+}
+
+template <bool HAS_B>
+__global__ void __launch_bounds__((RR_CW + 1) * 32, 2)
+k_reduce_ring(const float* __restrict__ a, const float* __restrict__ b, const __grid_constant__ RedRing P,
+              double* __restrict__ partials, float* __restrict__ lam_out)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* ring = reinterpret_cast<float*>(smem_raw);
+    const int stage_f = (HAS_B ? 2 : 1) * P.se;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + (size_t)P.ns * stage_f * sizeof(float));
+    uint64_t* empty = full + P.ns;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.ns; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], RR_CW);
+        }
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    ptx::griddep_wait();  // earlier kernels of the stream wrote the inputs
+    ptx::griddep_trigger();
+
+    const RedGeo G{P.plane, P.pitch, P.origin, (int)P.ny, (int)P.nx, P.rpi, P.se, (int)P.xl, (int)P.r, (int)P.rz};
+    // items of this block: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int my_items = P.items > blockIdx.x ? (int)((P.items - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0;
+    const int ns = P.ns;
+    const bool mode1 = HAS_B && P.mode == 1;  // the residual's lambda (needs b)
+    AccP acc;
+    if (warp == RR_CW) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t gq = 0;
+            ItemWalk w;
+            w.init(P);
+            uint32_t s = 0, k = 0;  // ring slot and its use count
+            for (int it = 0; it < my_items; ++it, ++gq, w.next()) {
+                if (k > 0 && !ptx::mbar_wait(&empty[s], (k - 1) & 1)) {
+                    if (P.status) atomicCAS(P.status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
+                    break;
+                }
+                const RedItem I = red_item(G, w);
+                float* dst = ring + (size_t)s * stage_f;
+                ptx::mbar_arrive_expect_tx(&full[s], (HAS_B ? 2u : 1u) * I.bytes);
+                ptx::bulk_g2s(dst, a + I.gsrc, I.bytes, &full[s]);
+                if (HAS_B) ptx::bulk_g2s(dst + G.se, b + I.gsrc, I.bytes, &full[s]);
+                if (++s == (uint32_t)ns) {
+                    s = 0;
+                    ++k;
+                }
+            }
+            // every issued copy lands before the block leaves
+            for (uint32_t d = 0; d < (uint32_t)ns && d < gq; ++d) {
+                const uint32_t g = gq - 1 - d;
+                if (!ptx::mbar_wait(&full[g % ns], (g / ns) & 1) && P.status)
+                    atomicCAS(P.status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------- consumers
+        ItemWalk w;
+        w.init(P);
+        // a whole item (all but a plane's last row item when rpi does not
+        // divide ny, all but a row's last segment when se does not divide
+        // nx): b < lim_b and c < lim_c.  Each warp holds at most one of its
+        // rows (see WarpShare); this thread's part of it is fixed.
+        WarpShare fs;
+        const int full_rows = G.rpi > 0 ? G.rpi : 1;
+        fs.set(full_rows, G.rpi > 0 ? G.nx : G.se, warp);
+        const int lim_b = G.rpi > 0 ? G.ny / G.rpi : G.ny;
+        const int lim_c = G.rpi > 0 ? 1 : G.nx / G.se;
+        const bool f_act = fs.active && fs.j0 < full_rows;
+        const int f_off = (G.rpi > 0 ? G.xl + fs.j0 * (int)G.pitch : 0);
+        const int f_ve = fs.ve;
+        const bool f_tail = f_act && fs.rem > 0 && fs.slice == 0 && lane < fs.rem;
+        const int f_tx = 4 * fs.nfull + lane;
+        uint32_t s = 0, par = 0;  // ring slot and the parity of its phase
+        for (int it = 0; it < my_items; ++it, w.next()) {
+            if (!ptx::mbar_wait_warp(&full[s], par)) {
+                if (lane == 0 && P.status) atomicCAS(P.status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
+                break;
+            }
+            const float* stg = ring + (size_t)s * stage_f;
+            if (w.b < lim_b && w.c < lim_c) {
+                if (f_act) {
+                    const float* ra = stg + f_off;
+                    // the item's position is needed only for mode 1's stores
+                    float* lo = mode1 ? lam_out + red_item(G, w).gbase + (int64_t)fs.j0 * G.pitch : nullptr;
+                    int v = fs.vb + lane;
+                    if constexpr (!HAS_B)  // (two fields: one vector pair at a time)
+                        for (; v + 96 < f_ve; v += 128) red_vec4<HAS_B>(acc, ra, G.se, v, mode1, lo);
+                    for (; v < f_ve; v += 32) red_vec<HAS_B>(acc, ra, G.se, v, mode1, lo);
+                    if (f_tail) red_tail<HAS_B>(acc, ra, G.se, f_tx, mode1, lo);
+                }
+            } else {
+                acc = red_partial<HAS_B>(acc, G, w, stg, warp, lane, mode1, lam_out);
+            }
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&empty[s]);
+            if (++s == (uint32_t)ns) {
+                s = 0;
+                par ^= 1u;
+            }
+        }
+    }
+    const Red3 r = block_red_ff(acc);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x + 0] = r.s;
+        partials[3 * blockIdx.x + 1] = r.q;
+        partials[3 * blockIdx.x + 2] = r.m;
+    }
+}
+
 __global__ void __launch_bounds__(256)
 k_reduce_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out, int mode)
 {
+    ptx::griddep_wait();  // the partial kernel's results
     Red3 acc{0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
         acc.s += partials[3 * i + 0];
@@ -605,8 +974,7 @@ cudaError_t launch_mirror_ghosts(int esize, void* buf, const Geom& g, cudaStream
 }
 
 namespace {
-// Blocks of one reduction kernel instance resident at once on this GPU.
-int resident_blocks(const void* fn)
+int sm_count()
 {
     static int nsm = 0;
     if (nsm == 0) {
@@ -614,12 +982,18 @@ int resident_blocks(const void* fn)
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
     }
+    return nsm;
+}
+
+// Blocks of one reduction kernel instance resident at once on this GPU.
+int resident_blocks(const void* fn)
+{
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, 0) != cudaSuccess || occ <= 0) {
         (void)cudaGetLastError();
         occ = 1;
     }
-    return nsm * occ;
+    return sm_count() * occ;
 }
 
 int64_t blocks_by_rows(const Geom& g) { return std::max<int64_t>(1, (g.nz * g.ny + 7) / 8); }
@@ -629,44 +1003,96 @@ int reduce_blocks(const Geom& g, int max_blocks)
 {
     static int resident = 0;  // the most blocks any reduction kernel instance keeps resident
     if (resident == 0)
-        for (const void* f : {(const void*)k_reduce_partial<float, true>, (const void*)k_reduce_partial<float, false>,
-                              (const void*)k_reduce_partial<double, true>, (const void*)k_reduce_partial<double, false>})
+        for (const void* f : {(const void*)k_reduce_partial<double, true>, (const void*)k_reduce_partial<double, false>})
             resident = std::max(resident, resident_blocks(f));
     return (int)std::min<int64_t>(std::min<int64_t>(resident, max_blocks), blocks_by_rows(g));
 }
 
-cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g, double* partials,
-                          int nblocks, double* out, int mode, void* lam_out, cudaStream_t s)
+namespace {
+// Stage and ring sizes of k_reduce_ring: 36 KB per stage (one array of 9216
+// floats, or two of 4608), three stages per block, two blocks per SM.
+constexpr int RR_STAGE = 9216;
+constexpr int RR_NS = 3;
+
+cudaError_t launch_reduce_ring(const float* a, const float* b, const Geom& g, double* partials, int nblocks,
+                               int mode, float* lam_out, int* status, cudaStream_t s, int* used_blocks)
 {
-    // the grid: the blocks of this kernel instance that are resident at once
-    // (no partial second wave), within the caller's partials
-    static int res[2][2] = {{0, 0}, {0, 0}};
-    const int di = esize == 8, bi = b != nullptr;
-    if (res[di][bi] == 0) {
-        const void* fns[2][2] = {{(const void*)k_reduce_partial<float, false>, (const void*)k_reduce_partial<float, true>},
-                                 {(const void*)k_reduce_partial<double, false>, (const void*)k_reduce_partial<double, true>}};
-        res[di][bi] = resident_blocks(fns[di][bi]);
-    }
-    nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(nblocks, res[di][bi]), blocks_by_rows(g)));
-    if (esize == 8) {
-        if (b)
-            k_reduce_partial<double, true><<<nblocks, 256, 0, s>>>((const double*)a, (const double*)b, g, partials,
-                                                                   mode, (double*)lam_out);
-        else
-            k_reduce_partial<double, false><<<nblocks, 256, 0, s>>>((const double*)a, nullptr, g, partials, mode,
-                                                                    (double*)lam_out);
+    RedRing P{};
+    P.nz = g.nz;
+    P.ny = g.ny;
+    P.nx = g.nx;
+    P.pitch = g.pitch;
+    P.plane = g.plane;
+    P.origin = g.origin;
+    P.xl = g.xl;
+    P.r = g.r;
+    P.rz = g.rz;
+    P.se = b ? RR_STAGE / 2 : RR_STAGE;
+    P.ns = RR_NS;
+    if (g.pitch <= P.se) {
+        P.rpi = (int)std::min<int64_t>(RR_CW, P.se / g.pitch);
+        P.nseg = 1;
+        P.ipp = (g.ny + P.rpi - 1) / P.rpi;
+        P.items = g.nz * P.ipp;
     } else {
-        if (b)
-            k_reduce_partial<float, true><<<nblocks, 256, 0, s>>>((const float*)a, (const float*)b, g, partials,
-                                                                  mode, (float*)lam_out);
-        else
-            k_reduce_partial<float, false><<<nblocks, 256, 0, s>>>((const float*)a, nullptr, g, partials, mode,
-                                                                   (float*)lam_out);
+        P.rpi = 0;
+        P.nseg = (int)((g.nx + P.se - 1) / P.se);
+        P.ipp = 0;
+        P.items = g.nz * g.ny * P.nseg;
     }
+    P.mode = mode;
+    P.status = status;
+    const size_t smem = (size_t)RR_NS * RR_STAGE * sizeof(float) + 2 * (size_t)RR_NS * sizeof(uint64_t);
+    static int per_sm[2] = {0, 0};
+    const int bi = b != nullptr;
+    if (per_sm[bi] == 0) {
+        const void* fn = bi ? (const void*)k_reduce_ring<true> : (const void*)k_reduce_ring<false>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, (RR_CW + 1) * 32, smem);
+        if (e != cudaSuccess) return e;
+        per_sm[bi] = std::max(1, occ);
+    }
+    const int nb = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min(nblocks, per_sm[bi] * sm_count()), P.items));
+    *used_blocks = nb;
+    const dim3 block((RR_CW + 1) * 32);
+    if (b) return launch_dependent(k_reduce_ring<true>, dim3(nb), block, smem, s, a, b, P, partials, lam_out);
+    return launch_dependent(k_reduce_ring<false>, dim3(nb), block, smem, s, a, (const float*)nullptr, P, partials,
+                            lam_out);
+}
+}  // namespace
+
+cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g, double* partials,
+                          int nblocks, double* out, int mode, void* lam_out, int* status, cudaStream_t s)
+{
+    if (esize == 4) {
+        // FP32: the ring-staged kernel, one block per SM (at most nblocks)
+        int nb = 1;
+        cudaError_t e = launch_reduce_ring((const float*)a, (const float*)b, g, partials, nblocks, mode,
+                                           (float*)lam_out, status, s, &nb);
+        if (e != cudaSuccess) return e;
+        return launch_dependent(k_reduce_final, dim3(1), dim3(256), 0, s, (const double*)partials, nb, out, mode);
+    }
+    // FP64 (bound by the FP64 pipe, not by loads): the blocks of this kernel
+    // instance that are resident at once (no partial second wave), within the
+    // caller's partials
+    static int res[2] = {0, 0};
+    const int bi = b != nullptr;
+    if (res[bi] == 0)
+        res[bi] = resident_blocks(bi ? (const void*)k_reduce_partial<double, true>
+                                     : (const void*)k_reduce_partial<double, false>);
+    nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(nblocks, res[bi]), blocks_by_rows(g)));
+    if (b)
+        k_reduce_partial<double, true><<<nblocks, 256, 0, s>>>((const double*)a, (const double*)b, g, partials, mode,
+                                                               (double*)lam_out);
+    else
+        k_reduce_partial<double, false><<<nblocks, 256, 0, s>>>((const double*)a, nullptr, g, partials, mode,
+                                                                (double*)lam_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce_final<<<1, 256, 0, s>>>(partials, nblocks, out, mode);
-    return cudaGetLastError();
+    return launch_dependent(k_reduce_final, dim3(1), dim3(256), 0, s, (const double*)partials, nblocks, out, mode);
 }
 
 }  // namespace st

@@ -8,6 +8,7 @@
 namespace st {
 const Geom* grid_geom(st_grid_t g);                    // api.cu
 void grid_note_stream(st_grid_t g, cudaStream_t s);   // api.cu
+int* grid_status(st_grid_t g);                         // api.cu
 }  // namespace st
 
 using namespace st;
@@ -52,6 +53,8 @@ extern "C" st_status stencil_reduce_noalloc(st_grid_t g, const void* a, const vo
                                             void* stream)
 {
     if (!g || !a || !dev_out) return fail(ST_ERR_ARG, "stencil_reduce_noalloc: NULL argument");
+    if ((((uintptr_t)a) | ((uintptr_t)b)) & 15u)
+        return fail(ST_ERR_ARG, "stencil_reduce_noalloc: a, b must be 16-byte aligned");
     const Geom& G = *grid_geom(g);
     double* partials = nullptr;
     st_status rc = noalloc_scratch(&partials);
@@ -61,7 +64,7 @@ extern "C" st_status stencil_reduce_noalloc(st_grid_t g, const void* a, const vo
     const int nb = reduce_blocks(G, NOALLOC_MAX_BLOCKS);
     cudaStream_t s = (cudaStream_t)stream;
     // every block overwrites its own partial, so nothing needs clearing first
-    ST_CUDA_TRY(launch_reduce(G.esize, a, b, G, partials, nb, dev_out, 0, nullptr, s));
+    ST_CUDA_TRY(launch_reduce(G.esize, a, b, G, partials, nb, dev_out, 0, nullptr, grid_status(g), s));
     grid_note_stream(g, s);
     return ST_OK;
 }

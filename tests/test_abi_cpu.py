@@ -264,3 +264,4 @@ def test_tile_passes_flag_selects_the_fp64_tile_option():
     assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES | abi.ST_FLAG_CALLER_GHOSTS) == "generic_point"
     assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES, abi.ST_NEUMANN) == "generic_point"
     assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES | abi.ST_FLAG_GENERIC) == "generic_point"
+

@@ -337,3 +337,29 @@ def test_autograd_second_application_invalidates_first():
     with pytest.raises(RuntimeError):
         lc.backward()
     g.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_kept_second_to_last_segment_and_repeated_reverse(dtype):
+    """The forward run keeps the second-to-last segment's states in the
+    recomputation levels, and the first reverse pass reads them; a second
+    reverse pass on the same record recomputes that segment (the first one
+    overwrote the levels).  Both give the bits of a run that keeps every
+    state (one segment; the same pairing of steps, since every segment has an
+    even length), and of a reverse pass whose workspace the handle does not
+    know as holding them."""
+    v = inputs.varcoef3d(shape=(18, 22, 40))
+    steps, m = 24, 6
+    g = make(v.u0.shape, dtype)
+    prob = VarCoefProblem(g, steps, m)
+    prob.forward(v.u0, v.kappa)
+    first = [t.double().cpu().numpy() for t in prob.backward_from(target=v.target)[:2]]
+    second = [t.double().cpu().numpy() for t in prob.backward_from(target=v.target)[:2]]
+    other = VarCoefProblem(g, steps, m)   # a second record: the handle now remembers its workspace
+    other.forward(v.u0, v.kappa)
+    third = [t.double().cpu().numpy() for t in prob.backward_from(target=v.target)[:2]]
+    g.close()
+    _, lam_all, gk_all, _, _ = gpu_grad(v, steps, steps, dtype)
+    for got in (first, second, third):
+        assert np.array_equal(got[0], lam_all)
+        assert np.array_equal(got[1], gk_all)
