@@ -408,6 +408,7 @@ struct RedRing {
     int64_t ipp;   // items per plane (row items)
     int64_t items;
     int mode;      // 1: also lam_out = a - b on the interior
+    int all_whole; // every item is whole (rpi divides ny, or se divides nx)
     int* status;   // set to ST_ERR_DEVICE_TIMEOUT when a wait runs out
 };
 constexpr int RR_CW = 16;  // consumer warps per block
@@ -419,12 +420,13 @@ constexpr int RR_CW = 16;  // consumer warps per block
 // three fit in 32 bits: nz <= 65535, ny <= 2^24).
 struct ItemWalk {
     int z, b, c;
-    int nb, nc;
+    int nz, nb, nc;
     int dz, db, dc;
     __device__ __forceinline__ void init(const RedRing& P)
     {
         nb = (int)(P.rpi > 0 ? P.ipp : P.ny);
         nc = P.rpi > 0 ? 1 : P.nseg;
+        nz = (int)P.nz;
         const int64_t it = blockIdx.x, G = gridDim.x;
         c = (int)(it % nc);
         b = (int)((it / nc) % nb);
@@ -432,6 +434,18 @@ struct ItemWalk {
         dc = (int)(G % nc);
         db = (int)((G / nc) % nb);
         dz = (int)(G / nc / nb);
+    }
+    // The item the walk's position stands for: positions run backwards
+    // through memory (the last item first), so that a reduction launched
+    // right after a sweep starts on the part of the field the sweep wrote
+    // last, which is still in L2.
+    __device__ __forceinline__ ItemWalk item() const
+    {
+        ItemWalk r = *this;
+        r.z = nz - 1 - z;
+        r.b = nb - 1 - b;
+        r.c = nc - 1 - c;
+        return r;
     }
     __device__ __forceinline__ void next()
     {
@@ -658,22 +672,6 @@ __device__ __forceinline__ void red_vec(AccP& acc, const float* ra, int bofs, in
     }
 }
 
-// Vectors v, v + 32, v + 64 and v + 96 of a staged row, all loads first
-// (one field).
-template <bool HAS_B>
-__device__ __forceinline__ void red_vec4(AccP& acc, const float* ra, int, int v, bool, float*)
-{
-    static_assert(!HAS_B, "one field only");
-    float4 x[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = *reinterpret_cast<const float4*>(ra + 4 * (v + 32 * u));
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        acc.put1(make_float2(x[u].x, x[u].y));
-        acc.put1(make_float2(x[u].z, x[u].w));
-    }
-}
-
 // One element x of a row's ragged end.
 template <bool HAS_B>
 __device__ __forceinline__ void red_tail(AccP& acc, const float* ra, int bofs, int x, bool mode1, float* lo)
@@ -742,7 +740,7 @@ k_reduce_ring(const float* __restrict__ a, const float* __restrict__ b, const __
                     if (P.status) atomicCAS(P.status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
                     break;
                 }
-                const RedItem I = red_item(G, w);
+                const RedItem I = red_item(G, w.item());
                 float* dst = ring + (size_t)s * stage_f;
                 ptx::mbar_arrive_expect_tx(&full[s], (HAS_B ? 2u : 1u) * I.bytes);
                 ptx::bulk_g2s(dst, a + I.gsrc, I.bytes, &full[s]);
@@ -762,8 +760,6 @@ k_reduce_ring(const float* __restrict__ a, const float* __restrict__ b, const __
         __syncwarp();
     } else {
         // ---------------------------------------------------------- consumers
-        ItemWalk w;
-        w.init(P);
         // a whole item (all but a plane's last row item when rpi does not
         // divide ny, all but a row's last segment when se does not divide
         // nx): b < lim_b and c < lim_c.  Each warp holds at most one of its
@@ -778,32 +774,50 @@ k_reduce_ring(const float* __restrict__ a, const float* __restrict__ b, const __
         const int f_ve = fs.ve;
         const bool f_tail = f_act && fs.rem > 0 && fs.slice == 0 && lane < fs.rem;
         const int f_tx = 4 * fs.nfull + lane;
+        auto whole = [&](const float* stg, float* lo) {
+            const float* ra = stg + f_off;
+            for (int v = fs.vb + lane; v < f_ve; v += 32) red_vec<HAS_B>(acc, ra, G.se, v, mode1, lo);
+            if (f_tail) red_tail<HAS_B>(acc, ra, G.se, f_tx, mode1, lo);
+        };
         uint32_t s = 0, par = 0;  // ring slot and the parity of its phase
-        for (int it = 0; it < my_items; ++it, w.next()) {
-            if (!ptx::mbar_wait_warp(&full[s], par)) {
-                if (lane == 0 && P.status) atomicCAS(P.status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
-                break;
-            }
-            const float* stg = ring + (size_t)s * stage_f;
-            if (w.b < lim_b && w.c < lim_c) {
-                if (f_act) {
-                    const float* ra = stg + f_off;
-                    // the item's position is needed only for mode 1's stores
-                    float* lo = mode1 ? lam_out + red_item(G, w).gbase + (int64_t)fs.j0 * G.pitch : nullptr;
-                    int v = fs.vb + lane;
-                    if constexpr (!HAS_B)  // (two fields: one vector pair at a time)
-                        for (; v + 96 < f_ve; v += 128) red_vec4<HAS_B>(acc, ra, G.se, v, mode1, lo);
-                    for (; v < f_ve; v += 32) red_vec<HAS_B>(acc, ra, G.se, v, mode1, lo);
-                    if (f_tail) red_tail<HAS_B>(acc, ra, G.se, f_tx, mode1, lo);
+        if (P.all_whole && !mode1) {
+            // every item whole and nothing to store: no item positions needed
+            for (int it = 0; it < my_items; ++it) {
+                if (!ptx::mbar_wait_warp(&full[s], par)) {
+                    if (lane == 0 && P.status) atomicCAS(P.status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
+                    break;
                 }
-            } else {
-                acc = red_partial<HAS_B>(acc, G, w, stg, warp, lane, mode1, lam_out);
+                if (f_act) whole(ring + (size_t)s * stage_f, nullptr);
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&empty[s]);
+                if (++s == (uint32_t)ns) {
+                    s = 0;
+                    par ^= 1u;
+                }
             }
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&empty[s]);
-            if (++s == (uint32_t)ns) {
-                s = 0;
-                par ^= 1u;
+        } else {
+            ItemWalk w;
+            w.init(P);
+            for (int it = 0; it < my_items; ++it, w.next()) {
+                if (!ptx::mbar_wait_warp(&full[s], par)) {
+                    if (lane == 0 && P.status) atomicCAS(P.status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
+                    break;
+                }
+                const float* stg = ring + (size_t)s * stage_f;
+                const ItemWalk at = w.item();
+                if (at.b < lim_b && at.c < lim_c) {
+                    // the item's position is needed only for mode 1's stores
+                    if (f_act)
+                        whole(stg, mode1 ? lam_out + red_item(G, at).gbase + (int64_t)fs.j0 * G.pitch : nullptr);
+                } else {
+                    acc = red_partial<HAS_B>(acc, G, at, stg, warp, lane, mode1, lam_out);
+                }
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&empty[s]);
+                if (++s == (uint32_t)ns) {
+                    s = 0;
+                    par ^= 1u;
+                }
             }
         }
     }
@@ -1041,6 +1055,7 @@ cudaError_t launch_reduce_ring(const float* a, const float* b, const Geom& g, do
         P.items = g.nz * g.ny * P.nseg;
     }
     P.mode = mode;
+    P.all_whole = P.rpi > 0 ? (g.ny % P.rpi == 0) : (g.nx % P.se == 0);
     P.status = status;
     const size_t smem = (size_t)RR_NS * RR_STAGE * sizeof(float) + 2 * (size_t)RR_NS * sizeof(uint64_t);
     static int per_sm[2] = {0, 0};
@@ -1068,7 +1083,7 @@ cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g
                           int nblocks, double* out, int mode, void* lam_out, int* status, cudaStream_t s)
 {
     if (esize == 4) {
-        // FP32: the ring-staged kernel, one block per SM (at most nblocks)
+        // FP32: the ring-staged kernel, two blocks per SM (at most nblocks)
         int nb = 1;
         cudaError_t e = launch_reduce_ring((const float*)a, (const float*)b, g, partials, nblocks, mode,
                                            (float*)lam_out, status, s, &nb);

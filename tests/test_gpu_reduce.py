@@ -8,7 +8,8 @@ padded rows of one plane when a row fits a stage (9216 floats for one field,
 block share out the rows of an item, or slices of a row when an item has
 fewer rows than warps.  The shapes cover both kinds of item, ragged last
 items (rows left over in a plane, a short last segment, rows whose length is
-not a multiple of four), several items per block and fewer items than
+not a multiple of four), grids whose items are all whole (the kernel then
+skips item positions), several items per block and fewer items than
 blocks.
 
 Tolerances: the GPU accumulates each block's values in a compensated float
@@ -34,7 +35,9 @@ SHAPES = [
     (3, 16389),         # two or four segments per row, ragged last one
     (40, 52, 68),       # 3D, four items per plane
     (2, 3, 24583),      # 3D segments
-    (96, 96, 96),       # 3D, 576 items
+    (96, 96, 96),       # 3D, 576 items, every item whole
+    (64, 64),           # every row item whole
+    (2, 18432),         # every segment whole (one field and two)
 ]
 
 
