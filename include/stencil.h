@@ -387,7 +387,10 @@ st_status stencil_residual(st_grid_t g, const void* u, const void* target, void*
  * ceil(nsteps/ckpt_every) checkpoints, ckpt_every-1 levels for the
  * recomputation of a segment, and the ckpt_every-1 inner levels of the last
  * segment, which the forward run keeps so that the reverse pass need not
- * recompute them.
+ * recompute them; for a 3D handle of stencil_create_conservative, also
+ * ckpt_every-1 levels of lambda (its reverse pass runs a segment's
+ * transposed steps first and the segment's coefficient gradient after, in
+ * one pass over the kept lambda levels).
  */
 st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int ckpt_every, size_t* bytes);
 

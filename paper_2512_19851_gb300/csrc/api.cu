@@ -934,6 +934,12 @@ static size_t state_bytes(st_grid_t g) { return (size_t)((g->g.elems * g->g.esiz
 // m-1 inner levels of the last segment kept by the forward run.
 static int64_t ws_recompute_levels(int64_t nck, int m) { return nck > 1 ? m - 1 : 0; }
 static size_t ws_last_offset(int64_t nck, int m, size_t sb) { return (size_t)(nck + ws_recompute_levels(nck, m)) * sb; }
+// The conservative operator on the staged 3D pipeline runs its transposed
+// steps as the forward sweep on lambda (the matrix is symmetric) and its
+// coefficient gradient in a separate pass per segment, which reads the
+// segment's lambda levels: m - 1 more levels after the last segment's.
+static bool cons_split(st_grid_t g) { return g->fam.kind == FAM_CONS && g->fam.variant == 1; }
+static size_t ws_lambda_offset(int64_t nck, int m, size_t sb) { return ws_last_offset(nck, m, sb) + (size_t)(m - 1) * sb; }
 
 
 st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* bytes)
@@ -943,7 +949,7 @@ st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* byte
     const int64_t nck = (nsteps + m - 1) / m;
     // checkpoints, the recomputation buffer of a segment, and the states of
     // the last segment kept from the forward run
-    *bytes = state_bytes(g) * (size_t)(nck + ws_recompute_levels(nck, m) + (m - 1));
+    *bytes = state_bytes(g) * (size_t)(nck + ws_recompute_levels(nck, m) + (m - 1) + (cons_split(g) ? m - 1 : 0));
     return ST_OK;
 }
 
@@ -1036,18 +1042,24 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
     auto state = [&](int64_t c, int j) -> void* {
         return j == 0 ? (void*)(base + (size_t)c * sb) : (void*)(seg + (size_t)(j - 1) * sb);
     };
-    if (g->bc == ST_DIRICHLET)
-        for (int j = 1; j <= ws_recompute_levels(nck, m); ++j)
-            ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, state(0, j), g->g, g->bc_value, s));
-    const int fuse = star3d_adjoint_fuse(g->fam);  // steps per optimised transpose launch (0: generic)
-    void* lin = lambda;
-    void* lout = lambda_tmp;
-    char* last = base + ws_last_offset(nck, m, sb);  // the last segment's states, kept by the forward run
     // the second-to-last segment's states are in the recomputation levels if
     // the forward run that filled this workspace left them there and no
     // reverse pass has recomputed another segment into them since
     const bool kept2 = nck >= 2 && g->kept2_ws == ws && g->kept2_n == nsteps && g->kept2_m == m;
     if (nck >= 3) g->kept2_ws = nullptr;
+    // the recomputation levels' Dirichlet ghosts (that forward run set them
+    // when it stored the kept states there)
+    if (g->bc == ST_DIRICHLET && !kept2)
+        for (int j = 1; j <= ws_recompute_levels(nck, m); ++j)
+            ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, state(0, j), g->g, g->bc_value, s));
+    const int fuse = star3d_adjoint_fuse(g->fam);  // steps per optimised transpose launch (0: generic)
+    const bool split = cons_split(g) && g->bc != ST_NEUMANN;
+    char* lamws = base + ws_lambda_offset(nck, m, sb);  // lambda levels of a segment (split form)
+    if (split && g->bc == ST_DIRICHLET)
+        for (int j = 1; j < m; ++j) ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, lamws + (size_t)(j - 1) * sb, g->g, 0.0, s));
+    void* lin = lambda;
+    void* lout = lambda_tmp;
+    char* last = base + ws_last_offset(nck, m, sb);  // the last segment's states, kept by the forward run
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t t0 = c * m;
         const int L = (int)std::min<int64_t>(m, nsteps - t0);
@@ -1060,6 +1072,27 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
             if (g->bc == ST_NEUMANN) ST_CUDA_TRY(launch_mirror_ghosts(g->g.esize, state(c, j - 1), g->g, s));
             SweepArgs a = sweep_args(g, state(c, j - 1), state(c, j), t0 + j - 1);
             ST_CUDA_TRY(launch_family(g->fam, a, s));
+        }
+        if (split) {
+            // lambda_L (lin) down to lambda_0 (lout) by the forward sweep on
+            // lambda, the inner levels kept; then the segment's gradient
+            auto lv = [&](int jj) -> void* {
+                return jj == L ? lin : (jj == 0 ? lout : (void*)(lamws + (size_t)(jj - 1) * sb));
+            };
+            for (int jj = L - 1; jj >= 0; --jj) ST_CUDA_TRY(launch_family(g->fam, sweep_args(g, lv(jj + 1), lv(jj), 0), s));
+            const int gm = cons_grad_max_pairs();
+            for (int hi = L - 1; grad && hi >= 0; hi -= gm) {
+                const void* us[64];
+                const void* ls[64];
+                int n = 0;
+                for (int jj = hi; jj >= 0 && n < gm; --jj, ++n) {
+                    us[n] = st(jj);
+                    ls[n] = lv(jj + 1);
+                }
+                ST_CUDA_TRY(launch_cons_grad(g->fam, us, ls, n, grad, s));
+            }
+            std::swap(lin, lout);
+            continue;
         }
         int j = L - 1;
         while (j >= 0) {

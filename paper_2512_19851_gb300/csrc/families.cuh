@@ -97,6 +97,12 @@ cudaError_t launch_cons_sweep(const Family& f, const SweepArgs& a, cudaStream_t 
 bool star3d_cons_supported(const Geom& g);
 cudaError_t launch_star3d_cons(const Family& f, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_cons_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
+// The conservative operator's coefficient gradient of n <= cons_grad_max_pairs()
+// transposed steps (3D): gk += sum over k of the step term of (u[k], lam[k]),
+// u[k] the state u_t and lam[k] lambda_{t+1} of one step.
+cudaError_t launch_cons_grad(const Family& f, const void* const* u, const void* const* lam, int n, double* gk,
+                             cudaStream_t s);
+int cons_grad_max_pairs();
 
 // ---------------------------------------------------------------------------
 // Batched plan (k_batch.cu)

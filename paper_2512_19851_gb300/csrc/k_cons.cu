@@ -201,6 +201,164 @@ __global__ void __launch_bounds__(256) k_cons_adjoint(const T* __restrict__ u, c
     }
 }
 
+// The coefficient gradient of up to GMAX transposed steps in one pass, for
+// the reverse pass whose transposed steps run as the forward sweep on lambda
+// (the matrix is symmetric): pair k holds the state u_t and lambda_{t+1} of
+// one step.  A 32 x 8 block walks GCZ planes; for each plane it brings the
+// plane of every pair (tile and a one-cell halo, both fields) into a 4-plane
+// shared ring by asynchronous element copies, the next plane's copies in
+// flight while the current plane is computed, so a thread keeps up to
+// 2 GMAX copies per plane going instead of waiting for one plane at a time.
+// Each point adds the pairs' terms (k_cons_adjoint's step term) in pair
+// order, in a compensated single-precision pair for FP32 grids (plain double
+// for FP64), and sends the sum to the FP64 gradient as one L2 reduction per
+// launch instead of one per step.
+constexpr int GMAX = 8;   // pairs per launch
+constexpr int GCZ = 32;   // planes per block
+constexpr int GTX = 32, GTY = 8, GHY = GTY + 2;
+// A staged row holds the tile's 32 columns and one 16-byte group on each
+// side (the x halo is its inner element): GW(T) elements, copied as 16-byte
+// groups from a 16-byte aligned start (interior rows start 16-byte aligned
+// and x0 is a multiple of 32).
+template <typename T>
+__host__ __device__ constexpr int gvn() { return 16 / (int)sizeof(T); }
+template <typename T>
+__host__ __device__ constexpr int gw() { return GTX + 2 * gvn<T>(); }
+template <typename T>
+__host__ __device__ constexpr int gplane() { return GHY * gw<T>(); }
+
+template <typename T>
+struct GradPairs {
+    const T* u[GMAX];
+    const T* lam[GMAX];
+    int n;
+};
+
+template <typename T>
+struct GAcc;  // the per-point accumulator
+template <>
+struct GAcc<float> {
+    float h = 0.f, l = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = h + x;
+        const float bb = s - h;
+        l += (h - (s - bb)) + (x - bb);
+        h = s;
+    }
+    // to the FP64 gradient as one L2 reduction
+    __device__ __forceinline__ void send(double* g) const { atomicAdd(g, (double)h + (double)l); }
+};
+template <>
+struct GAcc<double> {
+    double h = 0.0;
+    __device__ __forceinline__ void add(double x) { h += x; }
+    __device__ __forceinline__ void send(double* g) const { atomicAdd(g, h); }
+};
+
+template <typename T>
+constexpr size_t grad_smem(int n) { return (size_t)4 * n * 2 * gplane<T>() * sizeof(T); }
+
+template <typename T, bool PER>
+__global__ void __launch_bounds__(GTX * GTY) k_cons_grad(const __grid_constant__ GradPairs<T> G,
+                                                         double* __restrict__ gk,
+                                                         const __grid_constant__ GenParams P, int64_t xend)
+{
+    constexpr int VN = gvn<T>(), W = gw<T>(), HP = gplane<T>(), NCH = W / VN;  // 16-byte groups per row
+    extern __shared__ __align__(16) unsigned char graw[];
+    T* ring = reinterpret_cast<T*>(graw);  // [slot 4][pair GMAX][field 2][HP]
+    ptx::griddep_wait();
+    ptx::griddep_trigger();
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * GTX + tx;
+    const int64_t x0 = (int64_t)blockIdx.x * GTX, y0 = (int64_t)blockIdx.y * GTY;
+    const int64_t x = x0 + tx, y = y0 + ty;
+    const int64_t z0 = (int64_t)blockIdx.z * GCZ;
+    const int nzc = (int)(P.nz - z0 < GCZ ? P.nz - z0 : GCZ);
+    const int n = G.n;
+    const bool own = x < P.nx && y < P.ny;
+    const bool ixm = PER || x > 0, ixp = PER || x + 1 < P.nx, iym = PER || y > 0, iyp = PER || y + 1 < P.ny;
+    auto at = [&](int slot, int k, int f) { return ring + ((size_t)(slot * n + k) * 2 + f) * HP; };
+    // This thread's 16-byte group of a staged plane (at most one: GHY * NCH
+    // <= the block's threads), fixed for the whole block: staged row hy,
+    // group hc, i.e. grid row y0 - 1 + hy and columns x0 - VN + VN hc ...
+    // Periodic: a group that crosses the row's wrap is copied element-wise
+    // (gidx = -1 marks it); Dirichlet: groups outside the padded row, and rows
+    // past the ghost row, are not copied.
+    const int hy = tid / NCH, hc = tid - hy * NCH;
+    bool cp = tid < GHY * NCH;
+    int64_t yy = y0 - 1 + hy;
+    const int64_t gx = x0 - VN + (int64_t)VN * hc;  // first column of the group
+    bool whole = true;                               // the group copies in one 16-byte piece
+    if (cp) {
+        if (PER) {
+            yy = wrapc(yy, P.ny);
+            whole = gx >= 0 && gx + VN <= P.nx;
+        } else {
+            cp = yy <= P.ny && gx + VN <= xend;  // xend: columns from x = 0 to the padded row's end
+        }
+    }
+    const int so = hy * W + hc * VN;  // shared offset of the group in a plane
+    auto issue = [&](int64_t z) {
+        if (cp && z <= z0 + nzc) {
+            const int slot = (int)((z - z0 + 1) & 3);
+            const int64_t zz = PER ? wrapc(z, P.nz) : z;
+            const int64_t row = P.origin + zz * P.plane + yy * P.pitch;
+            if (whole) {
+                for (int k = 0; k < n; ++k) {
+                    ptx::cp_async_16(at(slot, k, 0) + so, G.u[k] + row + gx);
+                    ptx::cp_async_16(at(slot, k, 1) + so, G.lam[k] + row + gx);
+                }
+            } else {
+                for (int e = 0; e < VN; ++e) {
+                    const int64_t xx = wrapc(gx + e, P.nx);
+                    for (int k = 0; k < n; ++k) {
+                        ptx::cp_async_elem<sizeof(T)>(at(slot, k, 0) + so + e, G.u[k] + row + xx);
+                        ptx::cp_async_elem<sizeof(T)>(at(slot, k, 1) + so + e, G.lam[k] + row + xx);
+                    }
+                }
+            }
+        }
+        ptx::cp_async_commit();
+    };
+    issue(z0 - 1);
+    issue(z0);
+    issue(z0 + 1);
+    const int c = (ty + 1) * W + tx + VN;
+    for (int zi = 0; zi < nzc; ++zi) {
+        const int64_t z = z0 + zi;
+        issue(z + 2);                    // in flight while plane z is computed
+        ptx::cp_async_wait_group<1>();  // planes up to z + 1 have landed
+        __syncthreads();
+        if (own) {
+            // slot bases of planes z - 1, z, z + 1; pair k's fields at
+            // offsets 2 k HP (u) and 2 k HP + HP (lambda)
+            const T* Rm = ring + (size_t)(zi & 3) * n * 2 * HP;
+            const T* Rc = ring + (size_t)((zi + 1) & 3) * n * 2 * HP;
+            const T* Rp = ring + (size_t)((zi + 2) & 3) * n * 2 * HP;
+            const bool izm = PER || z > 0, izp = PER || z + 1 < P.nz;
+            GAcc<T> acc;
+            for (int k = 0, o = c; k < n; ++k, o += 2 * HP) {
+                const T uc = Rc[o], lc = Rc[o + HP];
+                T g = T(0);
+                auto term = [&](bool inside, T un, T ln) {
+                    const T du = un - uc;
+                    g += inside ? T(0.5) * du * (lc - ln) : du * lc;
+                };
+                term(izm, Rm[o], Rm[o + HP]);
+                term(izp, Rp[o], Rp[o + HP]);
+                term(iym, Rc[o - W], Rc[o - W + HP]);
+                term(iyp, Rc[o + W], Rc[o + W + HP]);
+                term(ixm, Rc[o - 1], Rc[o - 1 + HP]);
+                term(ixp, Rc[o + 1], Rc[o + 1 + HP]);
+                acc.add(g);
+            }
+            acc.send(gk + P.origin + z * P.plane + y * P.pitch + x);
+        }
+        __syncthreads();  // before plane z + 3 reuses plane z - 1's slot
+    }
+    ptx::cp_async_wait_all();
+}
+
 dim3 cons_grid(const GenParams& P)
 {
     return dim3((unsigned)((P.nx + 31) / 32), (unsigned)((P.ny + 7) / 8), (unsigned)((P.nz + CZ - 1) / CZ));
@@ -248,6 +406,36 @@ cudaError_t launch_cons_sweep(const Family& f, const SweepArgs& a, cudaStream_t 
     if (f.variant == 1) return launch_star3d_cons(f, a, s);
     return f.g.esize == 8 ? sweep_t<double>(f, a, s) : sweep_t<float>(f, a, s);
 }
+
+cudaError_t launch_cons_grad(const Family& f, const void* const* u, const void* const* lam, int n, double* gk,
+                             cudaStream_t s)
+{
+    const GenParams& P = f.gp;
+    if (P.nz * P.ny * P.nx == 0 || n <= 0) return cudaSuccess;
+    if (f.g.ndim != 3 || n > GMAX) return cudaErrorInvalidValue;
+    const dim3 g((unsigned)((P.nx + GTX - 1) / GTX), (unsigned)((P.ny + GTY - 1) / GTY),
+                 (unsigned)((P.nz + GCZ - 1) / GCZ)),
+        b(GTX, GTY);
+    auto go = [&](auto zero) -> cudaError_t {
+        using T = decltype(zero);
+        GradPairs<T> G{};
+        G.n = n;
+        for (int k = 0; k < n; ++k) {
+            G.u[k] = static_cast<const T*>(u[k]);
+            G.lam[k] = static_cast<const T*>(lam[k]);
+        }
+        const size_t smem = grad_smem<T>(n);
+        auto fn = f.periodic ? k_cons_grad<T, true> : k_cons_grad<T, false>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem<T>(GMAX));
+        if (e != cudaSuccess) return e;
+        return launch_dependent(fn, g, b, smem, s, G, gk, P, (int64_t)(f.g.pitch - f.g.xl));
+    };
+    return f.g.esize == 8 ? go(0.0) : go(0.f);
+}
+
+// Pairs per launch for the reverse pass: up to 5 keeps three blocks of
+// 64 KB (FP32) resident per SM.
+int cons_grad_max_pairs() { return 5; }
 
 cudaError_t launch_cons_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s)
 {

@@ -100,6 +100,22 @@ __device__ __forceinline__ void cp_async_elem(void* dst, const void* src)
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Asynchronous 16-byte copy global -> shared, bypassing L1 (both addresses
+// 16-byte aligned).  Completion: cp_async_wait_all / cp_async_wait_group.
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// Close the group of the thread's element copies issued since the last
+// commit; wait until at most N of its committed groups are still in flight.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Programmatic dependent launch.  A kernel launched with a programmatic
 // dependency on the previous kernel of its stream (launch_dependent) may be
 // scheduled while that kernel still runs; griddep_wait() blocks until every

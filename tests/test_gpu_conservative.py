@@ -103,3 +103,17 @@ def test_gradient_2d_and_checkpoint_interval():
         assert np.array_equal(o[1], outs[0][1]) and np.array_equal(o[2], outs[0][2])
     (uT, lam0, gk, loss), (loss_r, uT_r, lam_r, gk_r) = gpu_grad((48, 37), torch.float64, False, 0.2, 25, 6)
     assert rel_err(lam0, lam_r) <= 1e-12 and rel_err(gk, gk_r) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 1e-9)])
+def test_gradient_3d_checkpoint_interval(dtype, tol):
+    """3D (transposed steps as the forward sweep on lambda, the coefficient
+    gradient in one pass per segment): m = 30, 7 and 1 give bitwise equal
+    lambda_0 (the same sweeps whatever m is); the gradient groups each
+    segment's terms before adding them to the FP64 accumulator (in a
+    compensated single-precision pair for FP32), so different m agree to that
+    grouping's rounding."""
+    outs = [gpu_grad((20, 18, 23), dtype, False, 0.2, 30, m)[0] for m in (30, 7, 1)]
+    for o in outs[1:]:
+        assert np.array_equal(o[1], outs[0][1])
+        assert rel_err(o[2], outs[0][2]) <= tol
