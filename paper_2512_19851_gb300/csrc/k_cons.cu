@@ -209,10 +209,11 @@ __global__ void __launch_bounds__(256) k_cons_adjoint(const T* __restrict__ u, c
 // shared ring by asynchronous element copies, the next plane's copies in
 // flight while the current plane is computed, so a thread keeps up to
 // 2 GMAX copies per plane going instead of waiting for one plane at a time.
-// Each point adds the pairs' terms (k_cons_adjoint's step term) in pair
-// order, in a compensated single-precision pair for FP32 grids (plain double
-// for FP64), and sends the sum to the FP64 gradient as one L2 reduction per
-// launch instead of one per step.
+// Each point adds the pairs' terms (k_cons_adjoint's step term, its face
+// products chained by fma) in pair order, in the grid's precision (a sum of
+// at most a few terms, each already rounded to that precision), and sends
+// the sum to the FP64 gradient as one L2 reduction per launch instead of one
+// per step: the accumulation over the run stays in FP64.
 constexpr int GMAX = 8;   // pairs per launch
 constexpr int GCZ = 32;   // planes per block
 constexpr int GTX = 32, GTY = 8, GHY = GTY + 2;
@@ -232,28 +233,6 @@ struct GradPairs {
     const T* u[GMAX];
     const T* lam[GMAX];
     int n;
-};
-
-template <typename T>
-struct GAcc;  // the per-point accumulator
-template <>
-struct GAcc<float> {
-    float h = 0.f, l = 0.f;
-    __device__ __forceinline__ void add(float x)
-    {
-        const float s = h + x;
-        const float bb = s - h;
-        l += (h - (s - bb)) + (x - bb);
-        h = s;
-    }
-    // to the FP64 gradient as one L2 reduction
-    __device__ __forceinline__ void send(double* g) const { atomicAdd(g, (double)h + (double)l); }
-};
-template <>
-struct GAcc<double> {
-    double h = 0.0;
-    __device__ __forceinline__ void add(double x) { h += x; }
-    __device__ __forceinline__ void send(double* g) const { atomicAdd(g, h); }
 };
 
 template <typename T>
@@ -336,23 +315,28 @@ __global__ void __launch_bounds__(GTX * GTY) k_cons_grad(const __grid_constant__
             const T* Rc = ring + (size_t)((zi + 1) & 3) * n * 2 * HP;
             const T* Rp = ring + (size_t)((zi + 2) & 3) * n * 2 * HP;
             const bool izm = PER || z > 0, izp = PER || z + 1 < P.nz;
-            GAcc<T> acc;
+            // a face's term (u_q - u_p) w with w = A lambda_p - B lambda_q:
+            // interior face A = B = 1/2, ghost face A = 1, B = 0 (the same
+            // values as the fused kernel's 1/2 du (lambda_p - lambda_q) and
+            // du lambda_p: the halving is exact)
+            const T Azm = izm ? T(0.5) : T(1), Bzm = izm ? T(0.5) : T(0);
+            const T Azp = izp ? T(0.5) : T(1), Bzp = izp ? T(0.5) : T(0);
+            const T Aym = iym ? T(0.5) : T(1), Bym = iym ? T(0.5) : T(0);
+            const T Ayp = iyp ? T(0.5) : T(1), Byp = iyp ? T(0.5) : T(0);
+            const T Axm = ixm ? T(0.5) : T(1), Bxm = ixm ? T(0.5) : T(0);
+            const T Axp = ixp ? T(0.5) : T(1), Bxp = ixp ? T(0.5) : T(0);
+            T acc = T(0);  // the pairs' sum (each term is rounded in T already)
             for (int k = 0, o = c; k < n; ++k, o += 2 * HP) {
                 const T uc = Rc[o], lc = Rc[o + HP];
-                T g = T(0);
-                auto term = [&](bool inside, T un, T ln) {
-                    const T du = un - uc;
-                    g += inside ? T(0.5) * du * (lc - ln) : du * lc;
-                };
-                term(izm, Rm[o], Rm[o + HP]);
-                term(izp, Rp[o], Rp[o + HP]);
-                term(iym, Rc[o - W], Rc[o - W + HP]);
-                term(iyp, Rc[o + W], Rc[o + W + HP]);
-                term(ixm, Rc[o - 1], Rc[o - 1 + HP]);
-                term(ixp, Rc[o + 1], Rc[o + 1 + HP]);
-                acc.add(g);
+                T g = (Rm[o] - uc) * fma(-Bzm, Rm[o + HP], Azm * lc);
+                g = fma(Rp[o] - uc, fma(-Bzp, Rp[o + HP], Azp * lc), g);
+                g = fma(Rc[o - W] - uc, fma(-Bym, Rc[o - W + HP], Aym * lc), g);
+                g = fma(Rc[o + W] - uc, fma(-Byp, Rc[o + W + HP], Ayp * lc), g);
+                g = fma(Rc[o - 1] - uc, fma(-Bxm, Rc[o - 1 + HP], Axm * lc), g);
+                g = fma(Rc[o + 1] - uc, fma(-Bxp, Rc[o + 1 + HP], Axp * lc), g);
+                acc += g;
             }
-            acc.send(gk + P.origin + z * P.plane + y * P.pitch + x);
+            atomicAdd(gk + P.origin + z * P.plane + y * P.pitch + x, (double)acc);
         }
         __syncthreads();  // before plane z + 3 reuses plane z - 1's slot
     }

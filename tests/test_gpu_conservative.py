@@ -105,14 +105,16 @@ def test_gradient_2d_and_checkpoint_interval():
     assert rel_err(lam0, lam_r) <= 1e-12 and rel_err(gk, gk_r) <= 1e-12
 
 
-@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 1e-9)])
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 1e-5)])
 def test_gradient_3d_checkpoint_interval(dtype, tol):
     """3D (transposed steps as the forward sweep on lambda, the coefficient
-    gradient in one pass per segment): m = 30, 7 and 1 give bitwise equal
-    lambda_0 (the same sweeps whatever m is); the gradient groups each
-    segment's terms before adding them to the FP64 accumulator (in a
-    compensated single-precision pair for FP32), so different m agree to that
-    grouping's rounding."""
+    gradient in one pass per few steps): m = 30, 7 and 1 give bitwise equal
+    lambda_0 (the same sweeps whatever m is); the gradient adds up to five
+    steps' terms in the grid's precision before the FP64 accumulator, so
+    different m agree to that grouping's rounding: a few units of the
+    working precision relative to the terms, amplified by the cancellation
+    between a point's terms over the run (the bound the varcoef adjoint's
+    pairing test uses)."""
     outs = [gpu_grad((20, 18, 23), dtype, False, 0.2, 30, m)[0] for m in (30, 7, 1)]
     for o in outs[1:]:
         assert np.array_equal(o[1], outs[0][1])
