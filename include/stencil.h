@@ -390,7 +390,10 @@ st_status stencil_residual(st_grid_t g, const void* u, const void* target, void*
  * recompute them; for a 3D handle of stencil_create_conservative, also
  * ckpt_every-1 levels of lambda (its reverse pass runs a segment's
  * transposed steps first and the segment's coefficient gradient after, in
- * one pass over the kept lambda levels).
+ * one pass over the kept lambda levels); for an FP32 handle of the 3D
+ * symmetric 7-point star with per-cell weights (its fused two-step
+ * transpose), also one level of FP32 for the partial coefficient gradient
+ * of a segment.
  */
 st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int ckpt_every, size_t* bytes);
 
@@ -418,7 +421,11 @@ st_status stencil_step_ckpt(st_grid_t g, int nsteps, int ckpt_every, void* works
  * field-layout buffers of the grid's dtype; grad_coeff (may be NULL) is a
  * field-layout buffer of DOUBLES into which
  *     sum_t lambda_{t+1}[p] * sum_k beta_k u_t[p + o_k]     (= dL/dkappa_p)
- * is ACCUMULATED (+=).  The transpose step is
+ * is ACCUMULATED (+=): in double per pass, except that an FP32 handle on
+ * the fused 3D transpose (see stencil_adjoint_workspace) first sums a
+ * checkpoint segment's terms in FP32 and adds that sum in double once per
+ * segment, so its gradient depends on ckpt_every by those roundings.  The
+ * transpose step is
  *     lambda_t[q] = sum_k w_k(q - o_k) lambda_{t+1}[q - o_k],
  * over the points q - o_k that are interior (wrapped when periodic); ghost
  * cells are boundary data, not variables.  With ST_NEUMANN a step reads

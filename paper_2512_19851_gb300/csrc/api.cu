@@ -940,6 +940,10 @@ static size_t ws_last_offset(int64_t nck, int m, size_t sb) { return (size_t)(nc
 // segment's lambda levels: m - 1 more levels after the last segment's.
 static bool cons_split(st_grid_t g) { return g->fam.kind == FAM_CONS && g->fam.variant == 1; }
 static size_t ws_lambda_offset(int64_t nck, int m, size_t sb) { return ws_last_offset(nck, m, sb) + (size_t)(m - 1) * sb; }
+// FP32 grids on the fused transpose keep the checkpoint segment's gradient in
+// an FP32 partial field (one more level, after the others), added to the
+// FP64 gradient once per segment.
+static bool grad_partial(st_grid_t g) { return g->g.esize == 4 && g->has_beta && star3d_adjoint_fuse(g->fam) > 0; }
 
 
 st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* bytes)
@@ -949,7 +953,8 @@ st_status stencil_adjoint_workspace(st_grid_t g, int nsteps, int m, size_t* byte
     const int64_t nck = (nsteps + m - 1) / m;
     // checkpoints, the recomputation buffer of a segment, and the states of
     // the last segment kept from the forward run
-    *bytes = state_bytes(g) * (size_t)(nck + ws_recompute_levels(nck, m) + (m - 1) + (cons_split(g) ? m - 1 : 0));
+    *bytes = state_bytes(g) * (size_t)(nck + ws_recompute_levels(nck, m) + (m - 1) + (cons_split(g) ? m - 1 : 0) +
+                                        (grad_partial(g) ? 1 : 0));
     return ST_OK;
 }
 
@@ -1054,6 +1059,15 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
             ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, state(0, j), g->g, g->bc_value, s));
     const int fuse = star3d_adjoint_fuse(g->fam);  // steps per optimised transpose launch (0: generic)
     const bool split = cons_split(g) && g->bc != ST_NEUMANN;
+    // the FP32 partial gradient of a segment (after every other level): the
+    // first pass of a segment stores its terms, the others add theirs, and
+    // the sum goes into grad after the segment; cleared once here so that
+    // its ghost and padding cells add 0
+    void* gpart = nullptr;
+    if (grad && grad_partial(g) && g->bc != ST_NEUMANN) {
+        gpart = base + ws_lambda_offset(nck, m, sb) + (cons_split(g) ? (size_t)(m - 1) * sb : 0);
+        ST_CUDA_TRY(cudaMemsetAsync(gpart, 0, (size_t)g->g.elems * g->g.esize, s));
+    }
     char* lamws = base + ws_lambda_offset(nck, m, sb);  // lambda levels of a segment (split form)
     if (split && g->bc == ST_DIRICHLET)
         for (int j = 1; j < m; ++j) ST_CUDA_TRY(launch_fill_ghosts(g->g.esize, lamws + (size_t)(j - 1) * sb, g->g, 0.0, s));
@@ -1104,6 +1118,8 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
             a.lam_out = lout;
             a.kappa = g->has_beta ? g->buf[ST_SLOT_COEFF] : nullptr;
             a.gk = grad;
+            a.gpart = gpart;
+            a.gfirst = j == L - 1;
             a.steps = k;
             a.status = g->d_status;
             if (g->bc == ST_NEUMANN)  // the transpose of the mirror-then-sweep step
@@ -1113,6 +1129,7 @@ st_status stencil_adjoint(st_grid_t g, int nsteps, int m, const void* ws, void* 
             std::swap(lin, lout);
             j -= k;
         }
+        if (gpart) ST_CUDA_TRY(launch_grad_flush(gpart, grad, g->g.elems, s));
     }
     if (lin != lambda)
         ST_CUDA_TRY(cudaMemcpyAsync(lambda, lin, (size_t)g->g.elems * g->g.esize, cudaMemcpyDeviceToDevice, s));

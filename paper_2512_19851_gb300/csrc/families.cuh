@@ -70,6 +70,8 @@ struct AdjointArgs {
     void* lam_out;       // lambda_{t+1-steps}
     const void* kappa;
     double* gk;          // FP64 gradient accumulator (NULL: no gradient)
+    void* gpart;         // FP32 grids on the fused kernel: the segment's FP32 partial gradient
+    int gfirst;          // this pass is the first of its checkpoint segment (FP32 partial gradient)
     int steps;           // transpose steps fused in this launch (1 or 2)
     int* status;
 };
@@ -81,7 +83,11 @@ cudaError_t launch_family_adjoint(const Family& f, const AdjointArgs& a, cudaStr
 // Optimised kernels (return cudaErrorNotSupported when the case is not theirs)
 cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_star3d_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
+// gk += part (an FP32 partial gradient into the FP64 gradient), n elements, a
+// multiple of 4, both buffers 16-byte aligned.
+cudaError_t launch_grad_flush(void* part, double* gk, int64_t n, cudaStream_t s);
 int star3d_adjoint_fuse(const Family& f);
+// gk += part, part = 0 over n elements (part: FP32 partial gradient).
 // Two sweeps per pass of the constant symmetric 7-point star (FP32): a.in -> a.out
 bool star3d_pair_supported(const Family& f);
 cudaError_t launch_star3d_pair(const Family& f, const SweepArgs& a, double bc_value, cudaStream_t s);

@@ -33,14 +33,18 @@
 //    arithmetic on ghost data: ghosts are boundary data, not variables.
 //  * Each fused level evaluates exactly the expressions of a single-step pass
 //    in the same order, so lambda rounds exactly like K single-step passes.
-//    The gradient goes to the FP64 accumulator by reductions performed at L2
-//    (the SMs never wait on it): a single-step pass adds its term; a fused
+//    A single-step pass sends its gradient term of a point once; a fused
 //    pass holds level 1's term of a plane in registers until level 2 reaches
-//    that plane one iteration later and adds the two terms (in T) as one
-//    reduction, which halves the reductions, conversions and shared-memory
-//    transposes of the gradient.  The gradient then depends on how the steps
-//    are paired into passes (pairs are taken from the top of each checkpoint
-//    segment), by one rounding of T per pair.
+//    that plane one iteration later and sends the two terms' sum (in T)
+//    once, which halves the gradient traffic and shared-memory transposes.
+//    FP64 grids send it to the FP64 gradient by reductions performed at L2
+//    (the SMs never wait on them).  FP32 grids sum a checkpoint segment's
+//    terms in an FP32 partial gradient, added to the FP64 gradient once per
+//    segment (put_grad, k_grad_flush): the FP64 accumulation and its
+//    conversions run once per segment rather than once per pass.  The gradient then depends on
+//    how the steps are paired into passes (pairs are taken from the top of
+//    each checkpoint segment) and, in FP32, on the segment length, by
+//    roundings of T.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -72,6 +76,7 @@ struct AdjParams {
     uint32_t stage_elems, kap_off, ua_off, ub_off;  // lambda at offset 0 of a stage
     uint32_t ring_elems;            // one plane of the mu ring: TY + 2 rows
     int grad;                       // gradient requested
+    int gfirst;                     // FP32 grids: the first pass of a checkpoint segment
     double ac, bc, an, bn;
     int* status;
 };
@@ -230,33 +235,58 @@ __device__ __forceinline__ void nsum(const XCtx& X, const T (&zm)[AV<T>::N], con
     }
 }
 
-// Add one step's gradient terms of a row group to the FP64 gradient.  The
-// additions are fire-and-forget reductions performed at L2 (the thread never
-// waits on them).  When the warp's 32 lanes hold 32 consecutive whole groups
-// of one row (`fast`, warp-uniform) the terms are first exchanged through the
-// warp's shared scratch so that each reduction instruction covers 32
-// consecutive doubles (8 sectors instead of 32).  Either way a point's terms
-// all come from one thread, in step order, and same-thread atomics on one
-// address take effect in program order, so every point sums its terms (or
-// pairs of terms) in step order.
+// One point's gradient term (or pair of terms) of a pass.  FP64 grids add it
+// to the FP64 gradient by a reduction performed at L2.  FP32 grids keep the
+// terms of a checkpoint segment in an FP32 partial gradient (64 MB at 256^3;
+// no FP64 instruction runs for it on the SM): the segment's first pass
+// stores its term there (`first`, the same for the whole launch), the
+// others add theirs by L2 reductions, and k_grad_flush adds the partial to
+// the FP64 gradient after the segment's last pass.  No thread waits on any
+// of these accesses.
 template <typename T>
-__device__ __forceinline__ void add_grad(const XCtx& X, bool fast, double* wsc, int lane, int64_t off, bool ok,
-                                         double* __restrict__ g64, const T (&t)[AV<T>::N])
+__device__ __forceinline__ void put_grad(T* __restrict__ gacc, bool first, int64_t i, T v)
+{
+    if (sizeof(T) == 4 && first) gacc[i] = v;
+    else atomicAdd(gacc + i, v);
+}
+
+// Add one step's gradient terms of a row group (see put_grad).  FP32: a
+// whole group goes out as one 16-byte store or vector reduction.  FP64:
+// when the warp's 32 lanes hold 32 consecutive whole groups of one row
+// (`fast`, warp-uniform) the terms are first exchanged through the warp's
+// shared scratch so that each reduction instruction covers 32 consecutive
+// doubles (8 sectors instead of 32).  Either way a point's terms all come
+// from one thread, in step order, and same-thread accesses to one address
+// take effect in program order, so every point sums its terms (or pairs of
+// terms) in step order.
+template <typename T>
+__device__ __forceinline__ void add_grad(const XCtx& X, bool fast, T* wsc, int lane, int64_t off, bool ok,
+                                         T* __restrict__ gacc, bool first, const T (&t)[AV<T>::N])
 {
     constexpr int VN = AV<T>::N;
+    if constexpr (sizeof(T) == 4) {
+        if (ok && X.xfull) {
+            if (first) vst(gacc + off, t);
+            else ptx::red_add_v4(gacc + off, t[0], t[1], t[2], t[3]);
+        } else if (ok) {
+#pragma unroll
+            for (int e = 0; e < VN; ++e)
+                if (X.x + e < X.nx) put_grad(gacc, first, off + e, t[e]);
+        }
+        return;
+    }
     if (fast) {
         const int64_t base = __shfl_sync(0xffffffffu, off, 0);
 #pragma unroll
-        for (int e = 0; e < VN; e += 2)
-            *reinterpret_cast<double2*>(wsc + VN * lane + e) = make_double2((double)t[e], (double)t[e + 1]);
+        for (int e = 0; e < VN; ++e) wsc[VN * lane + e] = t[e];
         __syncwarp();
 #pragma unroll
-        for (int e = 0; e < VN; ++e) atomicAdd(g64 + base + lane + 32 * e, wsc[lane + 32 * e]);
+        for (int e = 0; e < VN; ++e) put_grad(gacc, first, base + lane + 32 * e, wsc[lane + 32 * e]);
         __syncwarp();
     } else if (ok) {
 #pragma unroll
         for (int e = 0; e < VN; ++e)
-            if (X.xfull || X.x + e < X.nx) atomicAdd(g64 + off + e, (double)t[e]);
+            if (X.xfull || X.x + e < X.nx) put_grad(gacc, first, off + e, t[e]);
     }
 }
 
@@ -294,7 +324,7 @@ __device__ __forceinline__ void store_pair(bool okw, const XCtx& X, bool act, in
 template <typename T, int K, bool PERIODIC, bool UNIT>
 __global__ void __launch_bounds__(A_BLOCK, 1)
 k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __restrict__ kappa,
-          const T* __restrict__ ua, const T* __restrict__ ub, double* __restrict__ g64,
+          const T* __restrict__ ua, const T* __restrict__ ub, T* __restrict__ g64,
           const __grid_constant__ AdjParams P)
 {
     constexpr int VN = AV<T>::N;
@@ -305,8 +335,8 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
     uint64_t* empty = full + P.NS;
     uint64_t* rfull = empty + P.NS;    // K == 2: a ring plane is written (one arrival per consumer warp)
     uint64_t* rempty = rfull + A_RING;  // K == 2: a ring plane is read
-    // per consumer warp: 32 x VN doubles of gradient terms in transit
-    double* wscr = reinterpret_cast<double*>(rempty + A_RING) + (size_t)(threadIdx.x >> 5) * 32 * AV<T>::N;
+    // per consumer warp: 32 x VN gradient terms in transit
+    T* wscr = reinterpret_cast<T*>(rempty + A_RING) + (size_t)(threadIdx.x >> 5) * 32 * AV<T>::N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -469,9 +499,9 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
         // carried state (registers), per owned row: mu and u_t of the plane below the level-1 centre
         T m0p[2][VN], uap[2][VN];
         // level 2 (K == 2): lambda_1 and w_c at its centre, u_{t-1} below its centre (its mu_1
-        // planes are read back from the ring); hm0: the carried mu rows of a halo warp's second
-        // sub-task
-        T l1p[2][VN], wcp[2][VN], ubp[2][VN], hm0[2][VN];
+        // planes are read back from the ring).  A halo warp's second sub-task carries its mu
+        // rows in uap, which halo warps have no other use for (one register set fewer)
+        T l1p[2][VN], wcp[2][VN], ubp[2][VN];
         // level-1 results of this iteration, handed to level 2
         T l1n[2][VN], wcn[2][VN], m1n[2][VN], g1n[2][VN];  // g1n: this step's gradient term
 #pragma unroll
@@ -479,7 +509,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
                 m0p[i][e] = uap[i][e] = T(0);
-                l1p[i][e] = wcp[i][e] = ubp[i][e] = hm0[i][e] = T(0);
+                l1p[i][e] = wcp[i][e] = ubp[i][e] = T(0);
                 l1n[i][e] = wcn[i][e] = m1n[i][e] = g1n[i][e] = T(0);
             }
 
@@ -537,7 +567,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                                     ubp[i][e] = uv[i + 1][e];
                                 }
                                 add_grad(X, fastw, wscr, lane, P.origin + c2 * P.plane + (y0 + rr0 + i) * P.pitch + x,
-                                         act && rr0 + i < tye, g64, gp);
+                                         act && rr0 + i < tye, g64, P.gfirst != 0, gp);
                             }
                         }
                     }
@@ -639,13 +669,13 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 #pragma unroll
                         for (int i = 0; i < 2; ++i)
                             add_grad(X, fastw, wscr, lane, P.origin + c1 * P.plane + (y0 + rr0 + i) * P.pitch + x,
-                                     act && rr0 + i < tye, g64, g1n[i]);
+                                     act && rr0 + i < tye, g64, P.gfirst != 0, g1n[i]);
                     }
                 }
             } else if (K == 2) {
                 // ------------------------------------------------ halo rows, level 1 only
                 // Two sub-tasks per halo warp (x groups 32 apart by the halo warp
-                // count); the second keeps its carried mu rows in hm0.
+                // count); the second keeps its carried mu rows in uap.
                 auto halo = [&](const XCtx& Xh, bool acth, T (&m0)[2][VN]) {
                     const int xh = Xh.x;
 #pragma unroll
@@ -708,7 +738,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
                 const int s2 = warp - P.pair_warps + P.halo_warps;  // second sub-task (warp-uniform)
                 if (32 * s2 < ngx) {
                     const int gx2 = 32 * s2 + lane;
-                    halo(make_xctx<VN, PERIODIC>(gx2, lane, ngx, (int)P.nx), gx2 < ngx, hm0);
+                    halo(make_xctx<VN, PERIODIC>(gx2, lane, ngx, (int)P.nx), gx2 < ngx, uap);
                 }
             }
 
@@ -922,6 +952,8 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
     P.ub_off = P.ua_off + (uint32_t)((c.TY + 2) * g.pitch);
     P.ring_elems = (uint32_t)((c.TY + 2) * g.pitch);
     P.grad = a.gk != nullptr ? 1 : 0;
+    if (P.grad && sizeof(T) == 4 && !a.gpart) return cudaErrorInvalidValue;
+    P.gfirst = a.gfirst;
     const StarCoef& k = f.sc;
     P.ac = k.c_a;
     P.bc = k.c_b;
@@ -941,8 +973,9 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
         attr[unit] = true;
     }
     const int grid = (int)std::min<int64_t>(P.flat ? (int64_t)P.nyt * P.nz : P.units, adj_sm_count());
+    T* gacc = sizeof(T) == 8 ? reinterpret_cast<T*>(a.gk) : static_cast<T*>(a.gpart);
     return launch_dependent(fn, dim3(grid), dim3((c.CW + 1) * 32), smem, s, (const T*)a.lam_in, (T*)a.lam_out,
-                            (const T*)a.kappa, (const T*)a.u, (const T*)a.u2, a.gk, P);
+                            (const T*)a.kappa, (const T*)a.u, (const T*)a.u2, gacc, P);
 }
 
 }  // namespace
@@ -959,6 +992,49 @@ int star3d_adjoint_fuse(const Family& f)
     AdjCfg c;
     if (adj_cfg(f.g, 2, &c)) return 2;
     return adj_cfg(f.g, 1, &c) ? 1 : 0;
+}
+
+// The exact double of a finite nonzero normal float, by rebiasing its
+// exponent field (IEEE 754 binary32 -> binary64) on the integer units, so
+// that k_grad_flush issues one FP64 instruction per point (the add); zeros,
+// subnormals, infinities and NaNs take the hardware conversion.
+__device__ __forceinline__ double widen_exact(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint64_t bits = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + (1023u - 127u)) << 52) |
+                          ((uint64_t)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// gk += part over the whole padded buffer (the partial's ghost and padding
+// cells stay 0: the buffer is cleared once per reverse pass and the passes
+// write interior points only).  16-byte groups; n is a multiple of 4.
+__global__ void __launch_bounds__(256) k_grad_flush(const float4* __restrict__ part, double2* __restrict__ gk, int64_t n4)
+{
+    ptx::griddep_wait();
+    ptx::griddep_trigger();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 v = part[i];
+        double2 a = gk[2 * i], b = gk[2 * i + 1];
+        a.x += widen_exact(v.x);
+        a.y += widen_exact(v.y);
+        b.x += widen_exact(v.z);
+        b.y += widen_exact(v.w);
+        gk[2 * i] = a;
+        gk[2 * i + 1] = b;
+    }
+}
+
+cudaError_t launch_grad_flush(void* part, double* gk, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (n % 4 != 0 || ((uintptr_t)part | (uintptr_t)gk) % 16 != 0) return cudaErrorInvalidValue;
+    const int64_t n4 = n / 4;
+    return launch_dependent(k_grad_flush, dim3((unsigned)std::min<int64_t>((n4 + 255) / 256, (int64_t)1 << 30)), dim3(256),
+                            0, s, static_cast<const float4*>(part), reinterpret_cast<double2*>(gk), n4);
 }
 
 cudaError_t launch_star3d_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s)

@@ -125,6 +125,14 @@ __device__ __forceinline__ void cp_async_wait_group()
 // the stream reads or writes.  griddep_trigger() lets the dependent grid be
 // scheduled once every CTA of this grid has issued it or exited; the
 // dependent still waits for this grid's completion in its own griddep_wait.
+// Four consecutive floats added at L2 by one reduction (16-byte aligned
+// address; relaxed, GPU scope; the thread does not wait for it).
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

@@ -27,6 +27,11 @@ TOL32_GRAD = 1e-3
 # (|sum of terms| is at least ~1e-2 of sum |terms| on these fields).
 PAIR32 = 1e-5
 PAIR64 = 1e-13
+# FP32 grids: a checkpoint segment's terms are summed in an FP32 partial
+# gradient (up to m terms, each rounding 2^-24 relative to the running sum)
+# before the FP64 accumulator, so runs with different segments agree to that
+# grouping's rounding, amplified by the same cancellation.
+SEG32 = 1e-4
 ALPHA = [1.0] + [0.0] * 6
 BETA = [-6.0] + [1.0] * 6
 
@@ -122,9 +127,12 @@ def test_gradient_full_size_two_segments():
     assert rel_err(lam0, lam_r) <= TOL32_FWD, kern
     assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
     # the recomputed segment (two steps per pass) holds the same states as the
-    # forward run's single sweeps: keeping every state gives the same bits
+    # forward run's single sweeps: keeping every state gives the same lambda
+    # bits; the gradient sums each segment's terms in FP32 before the FP64
+    # accumulator, so it agrees to that grouping's rounding
     kept = gpu_grad(v, steps, steps, torch.float32)
-    assert np.array_equal(lam0, kept[1]) and np.array_equal(gk, kept[2])
+    assert np.array_equal(lam0, kept[1])
+    assert rel_err(gk, kept[2]) <= SEG32
 
 
 @pytest.mark.parametrize("periodic,bc", [(False, 0.0), (False, 0.3), (True, 0.0)])
@@ -147,7 +155,7 @@ def test_gradient_wide_rows_matches_oracle(periodic, bc):
     groups, the last one ragged) and FP64 rows of 70 points (35 groups), so a
     tile's halo rows take two 32-group sub-tasks per halo warp, the second
     partly filled.  FP32 m = 5 and m = 1 give the same lambda_0 bitwise and
-    gradients within the pairing tolerance."""
+    gradients within the segment-grouping tolerance."""
     steps, m = 10, 5
     v = inputs.varcoef3d(shape=(14, 22, 150))
     loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, bc, steps, m)
@@ -157,7 +165,7 @@ def test_gradient_wide_rows_matches_oracle(periodic, bc):
     assert rel_err(gk, gk_r) <= TOL32_GRAD, kern
     other = gpu_grad(v, steps, 1, torch.float32, periodic, bc)
     assert np.array_equal(lam0, other[1])
-    assert rel_err(other[2], gk) <= PAIR32
+    assert rel_err(other[2], gk) <= SEG32
     v = inputs.varcoef3d(shape=(14, 22, 70))
     loss_r, uT_r, lam_r, gk_r = oracle.varcoef7_gradient(v.u0, v.kappa, v.target, periodic, bc, steps, m)
     uT, lam0, gk, loss, kern = gpu_grad(v, steps, m, torch.float64, periodic, bc)
@@ -168,17 +176,17 @@ def test_gradient_wide_rows_matches_oracle(periodic, bc):
 
 def test_checkpoint_interval_does_not_change_gradient_fp32():
     """FP32 grids: fused two-step passes round lambda exactly like single
-    steps, so m = 1, 6 and 20 give bitwise equal lambda_0.  The gradient adds
-    the two fused steps' terms of a point before the FP64 accumulator, so it
-    is bitwise equal where the steps pair up alike (m = 6 and 20 over 20 steps:
-    every segment has an even length) and within PAIR32 otherwise (m = 1)."""
+    steps, so m = 1, 6 and 20 give bitwise equal lambda_0.  The gradient sums
+    a checkpoint segment's terms in an FP32 partial field before adding it to
+    the FP64 accumulator, so different m agree within SEG32."""
     v = inputs.varcoef3d(shape=(20, 26, 44))
     base = gpu_grad(v, 20, 20, torch.float32, True)
     other = gpu_grad(v, 20, 6, torch.float32, True)
-    assert np.array_equal(base[1], other[1]) and np.array_equal(base[2], other[2])
+    assert np.array_equal(base[1], other[1])
+    assert rel_err(other[2], base[2]) <= SEG32
     other = gpu_grad(v, 20, 1, torch.float32, True)
     assert np.array_equal(base[1], other[1])
-    assert rel_err(other[2], base[2]) <= PAIR32
+    assert rel_err(other[2], base[2]) <= SEG32
 
 
 def test_checkpoint_interval_does_not_change_gradient():
@@ -344,10 +352,10 @@ def test_kept_second_to_last_segment_and_repeated_reverse(dtype):
     """The forward run keeps the second-to-last segment's states in the
     recomputation levels, and the first reverse pass reads them; a second
     reverse pass on the same record recomputes that segment (the first one
-    overwrote the levels).  Both give the bits of a run that keeps every
-    state (one segment; the same pairing of steps, since every segment has an
-    even length), and of a reverse pass whose workspace the handle does not
-    know as holding them."""
+    overwrote the levels).  All three reverse passes give the same bits, and
+    those of a run that keeps every state (one segment; the same pairing of
+    steps, since every segment has an even length) for lambda_0 and the FP64
+    gradient; the FP32 gradient, summed per segment in FP32, within SEG32."""
     v = inputs.varcoef3d(shape=(18, 22, 40))
     steps, m = 24, 6
     g = make(v.u0.shape, dtype)
@@ -362,4 +370,8 @@ def test_kept_second_to_last_segment_and_repeated_reverse(dtype):
     _, lam_all, gk_all, _, _ = gpu_grad(v, steps, steps, dtype)
     for got in (first, second, third):
         assert np.array_equal(got[0], lam_all)
-        assert np.array_equal(got[1], gk_all)
+        if dtype == torch.float64:
+            assert np.array_equal(got[1], gk_all)
+        else:  # FP32 partial sums per segment before the FP64 accumulator
+            assert rel_err(got[1], gk_all) <= SEG32
+    assert np.array_equal(first[1], second[1]) and np.array_equal(first[1], third[1])
