@@ -68,8 +68,8 @@ struct AdjParams {
     int rz, r, xl;
     int TY, NS, CW;                 // rows per tile, stages, consumer warps
     int nyt, nzc, units;
-    int flat;                       // 1: CTA b takes planes [T b / G, T (b + 1) / G) of the tile-major
-                                    // sequence of the T = nyt * nz (tile, plane) pairs, G = gridDim.x
+    int flat;                       // 1, 2: CTA b takes a contiguous range of the tile-major sequence
+                                    // of the nyt * nz (tile, plane) pairs (UnitIter)
     int ngx, npair, pair_warps;     // row-pair tasks fill warps [0, pair_warps); halo row tasks the rest
     int halo_warps;                 // K == 2: halo warps; each covers x groups [32 w, 32 w + 32) and,
                                     // one warp count further, [32 (w + halo_warps), ...)
@@ -138,16 +138,35 @@ __device__ __forceinline__ void atimeout(int* status)
     if (status) atomicCAS(status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
 }
 
+// Flat mode: position in the tile-major sequence of (tile, plane) pairs of
+// the point v of a cost axis on which every tile takes nz + w units, its
+// first w standing for the w warm-up iterations a unit starting there costs.
+__host__ __device__ __forceinline__ uint32_t flat_cut(uint64_t v, uint32_t nz, uint32_t nyt, uint32_t w)
+{
+    const uint64_t per = (uint64_t)nz + w;
+    const uint64_t t = v / per;
+    if (t >= nyt) return nyt * nz;
+    const int64_t in = (int64_t)(v - t * per) - (int64_t)w;
+    return (uint32_t)(t * nz + (in < 0 ? 0 : (uint64_t)in));
+}
+
 // The units of this CTA in order: a y tile and a z range [z0, z1).  Flat
-// mode needs nyt * nz < 2^31 (checked on the host).
+// mode needs nyt * (nz + 2K) < 2^31 (checked on the host).
+template <int K>
 struct UnitIter {
     uint32_t a, b;  // flat: next and end (tile, plane) pair of this CTA; otherwise a = unit index
     __device__ UnitIter(const AdjParams& P)
     {
         if (P.flat) {
-            const uint64_t T = (uint64_t)P.nyt * (uint64_t)P.nz;
-            a = (uint32_t)(T * blockIdx.x / gridDim.x);
-            b = (uint32_t)(T * (blockIdx.x + 1) / gridDim.x);
+            // flat == 2: equal shares of the cost axis, so that a CTA whose
+            // range crosses into the next tile, and pays a second pipeline
+            // warm-up (2K iterations), gets correspondingly fewer planes;
+            // flat == 1: equal shares of planes (the host picks the one whose
+            // longest CTA is shorter)
+            const uint32_t nz = (uint32_t)P.nz, nyt = (uint32_t)P.nyt, w = P.flat == 2 ? 2 * K : 0;
+            const uint64_t V = (uint64_t)nyt * (nz + w);
+            a = flat_cut(V * blockIdx.x / gridDim.x, nz, nyt, w);
+            b = flat_cut(V * (blockIdx.x + 1) / gridDim.x, nz, nyt, w);
         } else {
             a = blockIdx.x;
             b = 0;
@@ -364,7 +383,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
         // ------------------------------------------------------------ producer
         if (lane != 0) return;
         uint32_t gq = 0;
-        UnitIter it(P);
+        UnitIter<K> it(P);
         int yt;
         int64_t z0, z1;
         while (it.next(P, yt, z0, z1)) {
@@ -475,7 +494,7 @@ k_adjoint(const T* __restrict__ lam_in, T* __restrict__ lam_out, const T* __rest
 
     bool dead = false;
     uint32_t gq = 0, gr = 0;
-    UnitIter uit(P);
+    UnitIter<K> uit(P);
     int yt;
     int64_t z0, z1;
     while (uit.next(P, yt, z0, z1)) {
@@ -932,7 +951,7 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
     P.nyt = (int)((g.ny + c.TY - 1) / c.TY);
     P.nzc = c.nzc;
     P.units = P.nyt * P.nzc;
-    // Flat distribution: every CTA gets the same number of (tile, plane)
+    // Flat distribution: every CTA gets an equal share of the (tile, plane)
     // pairs, cut from the tile-major sequence, so all SMs take part however
     // the tile count divides (256^3 FP32: 26 tiles of 10 rows give 130
     // tile-by-chunk units for 152 SMs; flat: 106.3 instead of 113.2 us per
@@ -941,7 +960,29 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
     // tiles then meet their shared halo rows at different times, so those
     // come from DRAM more often.  The tiles-by-chunks grid remains for
     // sequences too long for 32-bit positions.
-    P.flat = (int64_t)P.nyt * g.nz < ((int64_t)1 << 31);
+    P.flat = (int64_t)P.nyt * (g.nz + 2 * K) < ((int64_t)1 << 31);
+    const int grid = (int)std::min<int64_t>(P.flat ? (int64_t)P.nyt * P.nz : P.units, adj_sm_count());
+    if (P.flat) {
+        // iterations of the longest CTA under either split (256^3 FP32: 49
+        // on the cost axis against 52 with equal shares of planes)
+        auto longest = [&](uint32_t w) {
+            const uint32_t nz = (uint32_t)g.nz, nyt = (uint32_t)P.nyt;
+            const uint64_t V = (uint64_t)nyt * (nz + w);
+            int64_t worst = 0;
+            for (int b = 0; b < grid; ++b) {
+                const uint32_t lo = flat_cut(V * b / grid, nz, nyt, w), hi = flat_cut(V * (b + 1) / grid, nz, nyt, w);
+                int64_t cost = 0;
+                for (uint32_t p = lo; p < hi;) {
+                    const uint32_t e = std::min(hi, (p / nz + 1) * nz);
+                    cost += (int64_t)(e - p) + 2 * K;
+                    p = e;
+                }
+                worst = std::max(worst, cost);
+            }
+            return worst;
+        };
+        P.flat = longest(2 * K) < longest(0) ? 2 : 1;
+    }
     P.ngx = (int)((g.nx + AV<T>::N - 1) / AV<T>::N);
     P.npair = c.npair;
     P.pair_warps = c.pair_warps;
@@ -972,7 +1013,6 @@ cudaError_t launch_adj_t(const Family& f, const AdjointArgs& a, const AdjCfg& c,
         if (e != cudaSuccess) return e;
         attr[unit] = true;
     }
-    const int grid = (int)std::min<int64_t>(P.flat ? (int64_t)P.nyt * P.nz : P.units, adj_sm_count());
     T* gacc = sizeof(T) == 8 ? reinterpret_cast<T*>(a.gk) : static_cast<T*>(a.gpart);
     return launch_dependent(fn, dim3(grid), dim3((c.CW + 1) * 32), smem, s, (const T*)a.lam_in, (T*)a.lam_out,
                             (const T*)a.kappa, (const T*)a.u, (const T*)a.u2, gacc, P);
