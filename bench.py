@@ -229,20 +229,35 @@ def run_ours(args):
     # ---------------- end to end through the public API (host buffers)
     src = torch.from_numpy(u0.astype(np.float32)).pin_memory()
     dst = torch.empty((N3, N3, N3), dtype=torch.float32).pin_memory()
-    for _ in range(2):
-        abi.stencil_run_host(g.h, SWEEPS, src.data_ptr(), dst.data_ptr(), stream)
-    torch.cuda.synchronize(dev)
+    # every step is a job: its field copied in from pinned host memory, 100
+    # sweeps, the result copied out; one pipelined call runs the steps, so a
+    # job's copies overlap its neighbours' sweeps (the first input and the
+    # last output are exposed)
     e_steps = max(3, min(args.steps, 20))
+    abi.stencil_run_host_many(g.h, SWEEPS, [src.data_ptr()] * 2, [dst.data_ptr()] * 2, stream)
+    torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(e_steps):
-        abi.stencil_run_host(g.h, SWEEPS, src.data_ptr(), dst.data_ptr(), stream)
+    abi.stencil_run_host_many(g.h, SWEEPS, [src.data_ptr()] * e_steps, [dst.data_ptr()] * e_steps, stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e_ms = aggregate_ms(e0.elapsed_time(e1) / e_steps, pg, dev)
+    # the same through the one-job call, copies not overlapped
+    abi.stencil_run_host(g.h, SWEEPS, src.data_ptr(), dst.data_ptr(), stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(3):
+        abi.stencil_run_host(g.h, SWEEPS, src.data_ptr(), dst.data_ptr(), stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e1_ms = aggregate_ms(e0.elapsed_time(e1) / 3, pg, dev)
     e2e = {"value": job_value(pts, 1, ws, e_ms), "unit": "GLUP/s", "h2d_bytes_per_step": int(src.numel() * 4),
-           "d2h_bytes_per_step": int(dst.numel() * 4), "ms_per_step": e_ms,
-           "api": "stencil_run_host (pinned host in, 100 sweeps, pinned host out)"}
+           "d2h_bytes_per_step": int(dst.numel() * 4), "ms_per_step": e_ms, "jobs": e_steps,
+           "api": "stencil_run_host_many (one call for all timed steps; per step a pinned host field in by the "
+                  "copy engines, 100 sweeps, the result out to pinned host memory)",
+           "single_job_call": {"value": job_value(pts, 1, ws, e1_ms), "ms_per_step": e1_ms,
+                               "api": "stencil_run_host (pack kernels read and write the pinned host buffers; "
+                                      "nothing overlaps)"}}
     g.close()
     del src, dst
 

@@ -312,6 +312,27 @@ st_status stencil_tune_config(st_grid_t g, int* cfg);
 st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* host_uT,
                            void* stream);
 
+/*
+ * Pipelined form of stencil_run_host for a stream of independent jobs on
+ * one grid (each its own initial field): for i in [0, njobs), copies
+ * host_in[i] (dense interior, C order, the grid's dtype) into the current
+ * level, runs nsteps, and copies the newest level's interior to
+ * host_out[i].  The host copies run on the copy engines, through two dense
+ * device staging buffers (interior size each, allocated by the first call
+ * and reused), on the handle's copy streams: job i+1's input arrives and
+ * job i-1's result leaves while job i sweeps, so with pinned host buffers
+ * the host traffic overlaps the sweeps (pageable buffers work, but their
+ * copies may block the calling thread and overlap nothing).  Every copy and
+ * kernel of the call is ordered after the caller's earlier work on
+ * `stream`, and everything later on `stream` after all of them: the
+ * results are on the host once `stream` reaches that point.  Jobs run in
+ * order; host_out[i] may equal host_out[j] (the later job's result stays)
+ * but must not overlap any host_in[k].  njobs = 0 does nothing.  One time
+ * level only.
+ */
+st_status stencil_run_host_many(st_grid_t g, int nsteps, int njobs, const void* const* host_in,
+                                void* const* host_out, void* stream);
+
 /* Defined by: Sec. III-B "Execution graph" (the frontend's sync call hands
  * the recorded work to the backend and returns when it has run) and Sec.
  * II-A "Asynchronous detection of kernel completion" (the host learns of a

@@ -66,6 +66,7 @@ SIGNATURES = {
     "stencil_tune": (_I, [_VP, _I, _VP]),
     "stencil_tune_config": (_I, [_VP, _PI]),
     "stencil_run_host": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "stencil_run_host_many": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "stencil_sync": (_I, [_VP]),
     "stencil_reduce": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "stencil_residual": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
@@ -250,6 +251,19 @@ def stencil_run_host(h, nsteps, host_u0_ptr, host_uT_ptr, stream=None) -> None:
     _check(lib().stencil_run_host(h, int(nsteps), ctypes.c_void_p(int(host_u0_ptr)),
                                   ctypes.c_void_p(int(host_uT_ptr)), ctypes.c_void_p(_stream(stream))),
            "stencil_run_host")
+
+
+def stencil_run_host_many(h, nsteps, host_in_ptrs, host_out_ptrs, stream=None) -> None:
+    """Jobs i = 0..n-1: host_in_ptrs[i] -> nsteps -> host_out_ptrs[i], host
+    copies overlapping the sweeps (pinned buffers)."""
+    n = len(host_in_ptrs)
+    if len(host_out_ptrs) != n:
+        raise ValueError("stencil_run_host_many: as many output as input pointers")
+    ins = (ctypes.c_void_p * max(n, 1))(*[int(p) for p in host_in_ptrs])
+    outs = (ctypes.c_void_p * max(n, 1))(*[int(p) for p in host_out_ptrs])
+    _check(lib().stencil_run_host_many(h, int(nsteps), n, ctypes.cast(ins, ctypes.c_void_p),
+                                       ctypes.cast(outs, ctypes.c_void_p), ctypes.c_void_p(_stream(stream))),
+           "stencil_run_host_many")
 
 
 def stencil_sync(h) -> None:

@@ -111,10 +111,12 @@ struct st_grid_s {
     bool pairs = false;         // two-step passes chosen by stencil_tune (3D 7-point heat, FP32)
     bool caller_ghosts = false; // ST_FLAG_CALLER_GHOSTS: Dirichlet ghost cells hold the caller's values
     void* staging = nullptr;    // dense interior buffer of stencil_run_host
+    void* staging2 = nullptr;   // stencil_run_host_many: the outgoing dense buffer
     // stencil_run_host splits each host copy over a few streams so that
     // several copy engines share it (created on first use)
     cudaStream_t cstream[4] = {};
     cudaEvent_t cfork = nullptr, cjoin[4] = {};
+    cudaEvent_t cpack = nullptr, cunpack = nullptr;  // stencil_run_host_many hand-offs
 };
 
 static void drop_graphs(st_grid_t g)
@@ -336,6 +338,9 @@ st_status stencil_destroy(st_grid_t g)
         delete g->plan;
     }
     if (g->staging) cudaFree(g->staging);
+    if (g->staging2) cudaFree(g->staging2);
+    if (g->cpack) cudaEventDestroy(g->cpack);
+    if (g->cunpack) cudaEventDestroy(g->cunpack);
     for (int c = 0; c < 4; ++c) {
         if (g->cstream[c]) cudaStreamDestroy(g->cstream[c]);
         if (g->cjoin[c]) cudaEventDestroy(g->cjoin[c]);
@@ -881,6 +886,81 @@ st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* h
         ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 1, s));
         ST_CUDA_TRY(copy4(host_uT, g->staging, cudaMemcpyDeviceToHost));
     }
+    return ST_OK;
+}
+
+st_status stencil_run_host_many(st_grid_t g, int nsteps, int njobs, const void* const* host_in,
+                                void* const* host_out, void* stream)
+{
+    if (!g) return fail(ST_ERR_ARG, "stencil_run_host_many: NULL handle");
+    if (njobs < 0 || (njobs > 0 && (!host_in || !host_out)))
+        return fail(ST_ERR_ARG, "stencil_run_host_many: njobs >= 0 and two arrays of njobs host pointers");
+    for (int i = 0; i < njobs; ++i)
+        if (!host_in[i] || !host_out[i]) return fail(ST_ERR_ARG, "stencil_run_host_many: NULL host buffer");
+    if (g->levels != 1) return fail(ST_ERR_UNSUPPORTED, "stencil_run_host_many: one time level only");
+    st_status rc = check_ready(g, "stencil_run_host_many");
+    if (rc != ST_OK) return rc;
+    if (njobs == 0) return ST_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geom& G = g->g;
+    const size_t bytes = (size_t)G.npoints * G.esize;
+    for (void** b : {&g->staging, &g->staging2})
+        if (!*b && cudaMalloc(b, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(ST_ERR_OOM, "stencil_run_host_many: staging allocation failed");
+        }
+    if (!g->cfork) {
+        for (int c = 0; c < 4; ++c) {
+            ST_CUDA_TRY(cudaStreamCreateWithFlags(&g->cstream[c], cudaStreamNonBlocking));
+            ST_CUDA_TRY(cudaEventCreateWithFlags(&g->cjoin[c], cudaEventDisableTiming));
+        }
+        ST_CUDA_TRY(cudaEventCreateWithFlags(&g->cfork, cudaEventDisableTiming));
+    }
+    if (!g->cpack) {
+        ST_CUDA_TRY(cudaEventCreateWithFlags(&g->cpack, cudaEventDisableTiming));
+        ST_CUDA_TRY(cudaEventCreateWithFlags(&g->cunpack, cudaEventDisableTiming));
+    }
+    // Copy engines carry the host traffic on the handle's copy streams, each
+    // direction in two pieces: streams 0-1 bring job i's input into staging
+    // while job i-1 sweeps, streams 2-3 take job i-1's result out of
+    // staging2 while job i sweeps.  Hand-offs: an input copy waits until the
+    // previous pack has read staging (cpack); an unpack waits until the
+    // previous output copy has read staging2 (cjoin[2..3]).  Both start
+    // ordered after the caller's earlier work on `stream`.
+    const size_t piece = (bytes / 2 + 255) / 256 * 256;
+    auto pieces = [&](int c0, cudaEvent_t after, void* dst, const void* src, cudaMemcpyKind kind) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            const int c = c0 + k;
+            const size_t off = std::min(bytes, (size_t)k * piece), n = std::min(piece, bytes - off);
+            e = cudaStreamWaitEvent(g->cstream[c], after, 0);
+            if (e == cudaSuccess && n > 0)
+                e = cudaMemcpyAsync((char*)dst + off, (const char*)src + off, n, kind, g->cstream[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(g->cjoin[c], g->cstream[c]);
+        }
+        return e;
+    };
+    ST_CUDA_TRY(cudaEventRecord(g->cpack, s));
+    ST_CUDA_TRY(cudaEventRecord(g->cjoin[2], s));
+    ST_CUDA_TRY(cudaEventRecord(g->cjoin[3], s));
+    for (int i = 0; i < njobs; ++i) {
+        ST_CUDA_TRY(pieces(0, g->cpack, g->staging, host_in[i], cudaMemcpyHostToDevice));
+        ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[0], 0));
+        ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[1], 0));
+        ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 0, s));
+        ST_CUDA_TRY(cudaEventRecord(g->cpack, s));
+        rc = stencil_step(g, nsteps, stream);
+        if (rc != ST_OK) return rc;
+        ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[2], 0));
+        ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[3], 0));
+        ST_CUDA_TRY(launch_pack(G.esize, g->staging2, g->buf[g->cur], G, 1, s));
+        ST_CUDA_TRY(cudaEventRecord(g->cunpack, s));
+        ST_CUDA_TRY(pieces(2, g->cunpack, host_out[i], g->staging2, cudaMemcpyDeviceToHost));
+    }
+    // the last results are on the host once `stream` passes this point
+    ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[2], 0));
+    ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[3], 0));
+    g->last = s;
     return ST_OK;
 }
 
