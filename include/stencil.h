@@ -268,8 +268,10 @@ st_status stencil_restore(st_grid_t g, const void* src, int64_t step, void* stre
  * Advance nsteps >= 0 steps on `stream`: refresh stale ghosts, then sweep,
  * each launch writing the other slot.  When stencil_tune chose two-step
  * passes (the constant symmetric 7-point star, FP32, no source) a launch
- * advances two steps (temporal blocking; the results equal single steps bit
- * for bit), so the newest level's slot follows the launch count:
+ * advances two steps, and when it chose the k-step static-tile kernel (FP64
+ * 2D grids) a launch advances up to k steps (temporal blocking; the results
+ * equal single steps bit for bit), so the newest level's slot follows the
+ * launch count:
  * stencil_current() tells which.  Enqueued as one
  * CUDA graph per (handle, nsteps, current slot) after the first call with
  * that nsteps; the launch sequence is the same either way.
@@ -279,9 +281,11 @@ st_status stencil_step(st_grid_t g, int nsteps, void* stream);
 /*
  * Autotune the launch configuration of this grid for nsteps-step calls (2D
  * grids on the persistent tile kernel: tile shape, threads per block, steps
- * per shared-memory pass; FP64 2D grids within the 3x3 neighbourhood: the
- * tuned tile kernel, one dependent launch per pass, against the
- * one-thread-per-point kernel, keeping the faster; the FP32 constant
+ * per shared-memory pass; FP64 2D grids within the 3x3 neighbourhood
+ * (constant weights, no source): the one-thread-per-point kernel, the tuned
+ * tile kernel with one dependent launch per pass, and a static-tile kernel
+ * running k steps per launch in shared memory over several tile shapes and
+ * k in 1..8 (the same bits as single sweeps), keeping the fastest; the FP32 constant
  * symmetric 3D 7-point star: one sweep or two sweeps per pass over HBM;
  * other families have nothing to tune and return ST_OK).  Times the candidates on the bound data and restores the
  * current level afterwards (the other slot is scratch); synchronises

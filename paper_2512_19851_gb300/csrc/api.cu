@@ -4,6 +4,7 @@
 // the batched form.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -102,6 +103,9 @@ struct st_grid_s {
     // one-thread-per-point kernel; plan_use tells which runs
     bool plan_optional = false;
     bool plan_use = true;
+    // the same FP64 2D grids on k_tb2d: tile x, tile y, steps per launch
+    // (tb[2] == 0: not in use); chosen by stencil_tune, or by ST_TB2D_CFG
+    int tb[3] = {0, 0, 0};
     // the workspace whose recomputation levels hold the inner states of the
     // second-to-last segment, written by the last stencil_step_ckpt (run of
     // kept2_n steps, checkpoints every kept2_m); cleared once a reverse pass
@@ -263,6 +267,15 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
         !g->caller_ghosts && bc != ST_NEUMANN && !(flags & ST_FLAG_GENERIC)) {
         g->plan_optional = true;
         g->plan_use = (flags & ST_FLAG_TILE_PASSES) != 0;
+        // "TX,TY,K": run k_tb2d with that configuration (tests, tuning sweeps)
+        const char* env = std::getenv("ST_TB2D_CFG");
+        int tx = 0, ty = 0, tk = 0;
+        if (!g->plan_use && env && std::sscanf(env, "%d,%d,%d", &tx, &ty, &tk) == 3 && tx >= 1 && ty >= 1 &&
+            tk >= 1 && tb2d_smem(tx, ty, tk) <= 200 * 1024 && tb2d_supports(g->fam)) {
+            g->tb[0] = tx;
+            g->tb[1] = ty;
+            g->tb[2] = tk;
+        }
     }
     if (g->fam.kind == FAM_2D_TILE || g->plan_optional) {
         std::vector<int32_t> off2(2 * npts);
@@ -383,7 +396,10 @@ st_status stencil_info(st_grid_t g, int* radius, int* npts, const char** kernel_
     if (!g) return fail(ST_ERR_ARG, "stencil_info: NULL handle");
     if (radius) *radius = g->radius;
     if (npts) *npts = g->npts;
-    if (kernel_name) *kernel_name = (g->plan_optional && g->plan_use) ? "tile2d_passes" : g->fam.name;
+    if (kernel_name)
+        *kernel_name = (g->plan_optional && g->plan_use) ? "tile2d_passes"
+                       : (g->plan_optional && g->tb[2] > 0) ? "tb2d_passes"
+                                                              : g->fam.name;
     return ST_OK;
 }
 
@@ -601,16 +617,28 @@ static bool use_pairs(st_grid_t g)
     return g->pairs && !g->caller_ghosts && g->bc != ST_NEUMANN && g->src < 0 && star3d_pair_supported(g->fam);
 }
 
+// k steps per launch on k_tb2d (small FP64 2D grids, chosen by stencil_tune)
+static bool use_tb(st_grid_t g) { return g->plan_optional && !g->plan_use && g->tb[2] > 0 && g->src < 0; }
+
 // Slot of the newest level after n steps from slot `cur`: every launch (one
 // sweep or one two-step pass) writes the other slot.
 static int final_slot(st_grid_t g, int cur, int n)
 {
-    const int launches = use_pairs(g) ? n / 2 + (n & 1) : n;
+    const int launches = use_tb(g) ? (n + g->tb[2] - 1) / g->tb[2] : use_pairs(g) ? n / 2 + (n & 1) : n;
     return (launches & 1) ? 1 - cur : cur;
 }
 
 static st_status enqueue_steps(st_grid_t g, int cur, int64_t step0, int n, cudaStream_t s)
 {
+    if (use_tb(g)) {
+        for (int i = 0; i < n;) {
+            const int ks = std::min(g->tb[2], n - i);
+            ST_CUDA_TRY(launch_tb2d(g->fam, g->buf[cur], g->buf[1 - cur], g->tb[0], g->tb[1], ks, g->bc_value, s));
+            i += ks;
+            cur = 1 - cur;
+        }
+        return ST_OK;
+    }
     const bool pairs = use_pairs(g);
     for (int i = 0; i < n;) {
         const int nxt = 1 - cur;
@@ -765,9 +793,46 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
     rc = tune_batch_plan(*g->plan, std::vector<Geom>{g->g}, &a, &b, nsteps, g->cur, s);
     drop_graphs(g);
     if (rc != ST_OK || !g->plan_optional) return rc;
-    // the optional tile plan against the one-thread-per-point kernel, each as
-    // the captured step sequence stencil_step runs (second of two runs);
-    // the current level is put back after every run
+    // the one-thread-per-point kernel, the tuned tile plan and k_tb2d over
+    // tile shapes and steps per launch, each timed as the captured step
+    // sequence stencil_step runs (second of two runs); the fastest is kept,
+    // and the current level is put back after every run
+    struct Cand {
+        bool plan;
+        int tb[3];
+    };
+    std::vector<Cand> cands = {{false, {0, 0, 0}}, {true, {0, 0, 0}}};
+    if (tb2d_supports(g->fam)) {
+        // fixed shapes, plus for one, two and three tiles per SM the shapes
+        // with the least halo work (area of tile + 8-cell halo) that give at
+        // most that many tiles: the busiest SM sets a pass's time, and
+        // co-resident CTAs overlap one another's loads and stores with
+        // arithmetic (256^2, 100 steps: 14 x 16 tiles, two per SM, 3 steps
+        // per launch, 1.60 us per step against 2.20 for one launch per step)
+        std::vector<std::pair<int, int>> shapes = {{32, 16}, {32, 8}, {16, 16}, {16, 8}, {64, 8}, {16, 32}};
+        int nsm = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                     cudaSuccess)
+            nsm = 0;
+        (void)cudaGetLastError();
+        const int64_t nx = g->g.nx, ny = g->g.ny;
+        for (int per = 1; per <= 3 && nsm > 0; ++per) {
+            std::vector<std::pair<int64_t, std::pair<int, int>>> best;
+            for (int ty = 4; ty <= 64; ++ty) {
+                const int64_t rows = (ny + ty - 1) / ty;
+                const int64_t cols_max = (int64_t)per * nsm / rows;
+                if (cols_max < 1) continue;
+                const int tx = (int)std::max<int64_t>(4, (nx + cols_max - 1) / cols_max);
+                if (tx > 128) continue;
+                best.push_back({(int64_t)(tx + 8) * (ty + 8), {tx, ty}});
+            }
+            std::sort(best.begin(), best.end());
+            for (size_t i = 0; i < best.size() && i < 3; ++i) shapes.push_back(best[i].second);
+        }
+        for (const auto& sh : shapes)
+            for (int k : {1, 2, 3, 4, 5, 6, 8})
+                if (k <= nsteps) cands.push_back({false, {sh.first, sh.second, k}});
+    }
     const size_t bytes = (size_t)g->g.elems * g->g.esize;
     void* keep = nullptr;
     if (cudaMalloc(&keep, bytes) != cudaSuccess) {
@@ -777,12 +842,13 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
     const int cur0 = g->cur;
     const int64_t step0 = g->step;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    float ms[2] = {0.f, 0.f};
+    std::vector<float> ms(cands.size(), 0.f);
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(keep, g->buf[cur0], bytes, cudaMemcpyDeviceToDevice, s);
-    for (int v = 0; v < 2 && e == cudaSuccess && rc == ST_OK; ++v) {
-        g->plan_use = v == 1;
+    for (size_t v = 0; v < cands.size() && e == cudaSuccess && rc == ST_OK; ++v) {
+        g->plan_use = cands[v].plan;
+        std::memcpy(g->tb, cands[v].tb, sizeof(g->tb));
         drop_graphs(g);
         for (int rep = 0; rep < 2 && e == cudaSuccess && rc == ST_OK; ++rep) {
             e = cudaEventRecord(e0, s);
@@ -796,7 +862,12 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    g->plan_use = e == cudaSuccess && rc == ST_OK && ms[1] < ms[0];
+    size_t best = 0;
+    if (e == cudaSuccess && rc == ST_OK)
+        for (size_t v = 1; v < cands.size(); ++v)
+            if (ms[v] < ms[best]) best = v;
+    g->plan_use = cands[best].plan;
+    std::memcpy(g->tb, cands[best].tb, sizeof(g->tb));
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(keep);
@@ -809,6 +880,13 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
 st_status stencil_tune_config(st_grid_t g, int* cfg)
 {
     if (!g || !cfg) return fail(ST_ERR_ARG, "stencil_tune_config: NULL argument");
+    if (use_tb(g)) {
+        cfg[0] = g->tb[0];
+        cfg[1] = g->tb[1];
+        cfg[2] = 512;
+        cfg[3] = g->tb[2];
+        return ST_OK;
+    }
     if (!g->plan || !g->plan_use) {
         cfg[0] = cfg[1] = cfg[2] = 0;
         cfg[3] = star3d_pair_supported(g->fam) ? (g->pairs ? 2 : 1) : 0;

@@ -96,6 +96,13 @@ cudaError_t launch_tile2d(const Family& f, const SweepArgs& a, cudaStream_t s);
 bool wave_supports(const FamilyDesc& d);
 cudaError_t launch_wave(const Family& f, const SweepArgs& a, cudaStream_t s);
 bool tile2d_supports(const FamilyDesc& d, int* variant, const char** name);
+// FP64 2D grids, offsets within the 3x3 neighbourhood, constant weights: ks
+// steps of the sweep in one launch of TX x TY tiles (k_2d.cu); the same bits
+// as ks single sweeps.  tb2d_smem: its dynamic shared memory for k steps.
+bool tb2d_supports(const Family& f);
+size_t tb2d_smem(int TX, int TY, int k);
+cudaError_t launch_tb2d(const Family& f, const void* in, void* out, int TX, int TY, int ks, double bc,
+                        cudaStream_t s);
 cudaError_t launch_cons_sweep(const Family& f, const SweepArgs& a, cudaStream_t s);
 // The conservative operator's 3D forward on the staged pipeline of k_star1
 // (variant 1 of FAM_CONS); its coefficient field's ghosts must mirror the

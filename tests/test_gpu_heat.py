@@ -386,12 +386,49 @@ def test_2d_fp64_tile_passes_match_oracle(shape, periodic, bc, offsets_kind):
     assert rel_err(g.current().cpu().numpy(), ref) <= TOL64, g.kernel
     g.set_field(u0)
     g.tune(37)
-    assert g.kernel in ("tile2d_passes", "generic_point")
+    assert g.kernel in ("tile2d_passes", "generic_point", "tb2d_passes")
     g.set_field(u0)
     g.step(37)
     g.sync()
     assert rel_err(g.current().cpu().numpy(), ref) <= TOL64, g.kernel
     g.close()
+
+
+@pytest.mark.parametrize("cfg", ["32,16,4", "32,14,3", "16,16,8", "64,4,1", "7,5,6"])
+@pytest.mark.parametrize("periodic,bc", [(False, 0.0), (False, 0.3), (True, 0.0)])
+@pytest.mark.parametrize("shape,offsets_kind", [((256, 256), "star5"), ((37, 300), "box9"), ((3, 130), "star5"),
+                                                ((2, 65), "box9")])
+def test_2d_fp64_tb2d_passes_equal_single_sweeps(monkeypatch, cfg, periodic, bc, shape, offsets_kind):
+    """k_tb2d (k steps per launch in shared memory; ST_TB2D_CFG = "TX,TY,k"
+    forces the configuration): bitwise equal to the one-thread-per-point
+    kernel and within 1e-12 of the FP64 oracle, over split calls whose
+    lengths are not multiples of k, tiles larger than the grid, ragged last
+    tiles and periodic halos wider than the grid."""
+    from paper_2512_19851_gb300.grid import Grid
+    u0 = inputs.heat2d(shape=shape)
+    if offsets_kind == "star5":
+        offs, w = five_point(0.2)
+    else:
+        offs = inputs.OFFSETS_BOX9
+        w = list(np.random.default_rng(9).random(9))
+        w = [x / sum(w) for x in w]
+    monkeypatch.setenv("ST_TB2D_CFG", cfg)
+    g = Grid(shape, offs, w, periodic=periodic, bc_value=bc, dtype=torch.float64)
+    monkeypatch.delenv("ST_TB2D_CFG")
+    assert g.kernel == "tb2d_passes"
+    from paper_2512_19851_gb300 import abi
+    assert list(abi.stencil_tune_config(g.h)) == [int(cfg.split(",")[0]), int(cfg.split(",")[1]), 512,
+                                                 int(cfg.split(",")[2])]
+    g.set_field(u0)
+    g.step(20)
+    g.step(17)
+    g.sync()
+    got = g.current().cpu().numpy()
+    g.close()
+    ref_gpu, kern = run_const(u0, offs, w, periodic, bc, 37, torch.float64, generic=True)
+    assert kern == "generic_point"
+    assert np.array_equal(got, ref_gpu)
+    assert rel_err(got, oracle.sweep_const(u0, offs, w, periodic, bc, 37)) <= TOL64
 
 
 def test_heat2d_fp64_workload_on_tile_passes():
