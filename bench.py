@@ -233,7 +233,7 @@ def run_ours(args):
     # sweeps, the result copied out; one pipelined call runs the steps, so a
     # job's copies overlap its neighbours' sweeps (the first input and the
     # last output are exposed)
-    e_steps = max(3, min(args.steps, 20))
+    e_steps = max(3, args.steps)  # as many steps as the device-resident timing
     abi.stencil_run_host_many(g.h, SWEEPS, [src.data_ptr()] * 2, [dst.data_ptr()] * 2, stream)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
