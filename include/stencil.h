@@ -321,12 +321,19 @@ st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* h
  * one grid (each its own initial field): for i in [0, njobs), copies
  * host_in[i] (dense interior, C order, the grid's dtype) into the current
  * level, runs nsteps, and copies the newest level's interior to
- * host_out[i].  The host copies run on the copy engines, through two dense
- * device staging buffers (interior size each, allocated by the first call
- * and reused), on the handle's copy streams: job i+1's input arrives and
- * job i-1's result leaves while job i sweeps, so with pinned host buffers
- * the host traffic overlaps the sweeps (pageable buffers work, but their
- * copies may block the calling thread and overlap nothing).  Every copy and
+ * host_out[i].  The host copies run on the copy engines, on the handle's
+ * copy streams: job i+1's input arrives and job i-1's result leaves while
+ * job i sweeps, so with pinned host buffers the host traffic overlaps the
+ * sweeps (pageable buffers work, but their copies may block the calling
+ * thread and overlap nothing).  Inputs are copied by rows into a
+ * field-layout buffer that the job's first sweep reads, and every job's
+ * last sweep but the last job's writes another one that is copied out; a
+ * zero-flux or caller-ghost boundary, a source, a 2D grid on the tile
+ * kernel or nsteps = 0 use dense staging buffers and pack kernels instead.
+ * The buffers (field or interior size) are allocated by the first call that
+ * needs them and reused.  Every job's result has the bits stencil_run_host
+ * gives for its input, and afterwards the current level holds the last
+ * job's result.  Every copy and
  * kernel of the call is ordered after the caller's earlier work on
  * `stream`, and everything later on `stream` after all of them: the
  * results are on the host once `stream` reaches that point.  Jobs run in

@@ -116,6 +116,11 @@ struct st_grid_s {
     bool caller_ghosts = false; // ST_FLAG_CALLER_GHOSTS: Dirichlet ghost cells hold the caller's values
     void* staging = nullptr;    // dense interior buffer of stencil_run_host
     void* staging2 = nullptr;   // stencil_run_host_many: the outgoing dense buffer
+    // stencil_run_host_many: field-layout buffers that a job's first sweep
+    // reads (its input copied in by the copy engines) and its last sweep
+    // writes (copied out from there)
+    void* pad_in = nullptr;
+    void* pad_out = nullptr;
     // stencil_run_host splits each host copy over a few streams so that
     // several copy engines share it (created on first use)
     cudaStream_t cstream[4] = {};
@@ -352,6 +357,8 @@ st_status stencil_destroy(st_grid_t g)
     }
     if (g->staging) cudaFree(g->staging);
     if (g->staging2) cudaFree(g->staging2);
+    if (g->pad_in) cudaFree(g->pad_in);
+    if (g->pad_out) cudaFree(g->pad_out);
     if (g->cpack) cudaEventDestroy(g->cpack);
     if (g->cunpack) cudaEventDestroy(g->cunpack);
     for (int c = 0; c < 4; ++c) {
@@ -971,6 +978,7 @@ st_status stencil_run_host_many(st_grid_t g, int nsteps, int njobs, const void* 
                                 void* const* host_out, void* stream)
 {
     if (!g) return fail(ST_ERR_ARG, "stencil_run_host_many: NULL handle");
+    if (nsteps < 0) return fail(ST_ERR_ARG, "stencil_run_host_many: negative step count");
     if (njobs < 0 || (njobs > 0 && (!host_in || !host_out)))
         return fail(ST_ERR_ARG, "stencil_run_host_many: njobs >= 0 and two arrays of njobs host pointers");
     for (int i = 0; i < njobs; ++i)
@@ -982,11 +990,31 @@ st_status stencil_run_host_many(st_grid_t g, int nsteps, int njobs, const void* 
     cudaStream_t s = (cudaStream_t)stream;
     const Geom& G = g->g;
     const size_t bytes = (size_t)G.npoints * G.esize;
-    for (void** b : {&g->staging, &g->staging2})
-        if (!*b && cudaMalloc(b, bytes) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return fail(ST_ERR_OOM, "stencil_run_host_many: staging allocation failed");
+    const size_t fbytes = (size_t)G.elems * G.esize;
+    // Direct form: a job's input is copied (by rows, at the same rate as a
+    // contiguous copy) into the interior of pad_in, which its first sweep
+    // reads; every job but the last writes its last sweep to pad_out, whose
+    // interior is copied out.  No pack kernel runs, and the grid's own levels
+    // hold the last job's states.  Boundaries whose sweeps need the input's
+    // ghost cells refreshed from the grid (zero flux, caller-owned ghosts) or
+    // a step index (a source) take the dense staging form: pack and unpack
+    // kernels around the grid's levels; so do grids on the 2D tile plan,
+    // whose kernel sums the offsets in its own order (the single sweeps at
+    // both ends of a job would round differently from stencil_step).
+    const bool direct = nsteps >= 1 && g->bc != ST_NEUMANN && !g->caller_ghosts && g->src < 0 &&
+                        !(g->plan && g->plan_use);
+    for (void** b : {&g->staging, &g->staging2, &g->pad_in, &g->pad_out}) {
+        const bool need = (b == &g->staging2) || (b == &g->staging ? !direct : direct);
+        if (need && !*b) {
+            if (cudaMalloc(b, (b == &g->pad_in || b == &g->pad_out) ? fbytes : bytes) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return fail(ST_ERR_OOM, "stencil_run_host_many: staging allocation failed");
+            }
+            // the first sweep reads pad_in's Dirichlet ghost cells
+            if (b == &g->pad_in && g->bc == ST_DIRICHLET)
+                ST_CUDA_TRY(launch_fill_ghosts(G.esize, g->pad_in, G, g->bc_value, s));
         }
+    }
     if (!g->cfork) {
         for (int c = 0; c < 4; ++c) {
             ST_CUDA_TRY(cudaStreamCreateWithFlags(&g->cstream[c], cudaStreamNonBlocking));
@@ -999,14 +1027,14 @@ st_status stencil_run_host_many(st_grid_t g, int nsteps, int njobs, const void* 
         ST_CUDA_TRY(cudaEventCreateWithFlags(&g->cunpack, cudaEventDisableTiming));
     }
     // Copy engines carry the host traffic on the handle's copy streams, each
-    // direction in two pieces: streams 0-1 bring job i's input into staging
-    // while job i-1 sweeps, streams 2-3 take job i-1's result out of
-    // staging2 while job i sweeps.  Hand-offs: an input copy waits until the
-    // previous pack has read staging (cpack); an unpack waits until the
-    // previous output copy has read staging2 (cjoin[2..3]).  Both start
+    // direction in two pieces: streams 0-1 bring job i's input in while job
+    // i-1 sweeps, streams 2-3 take job i-1's result out while job i sweeps.
+    // Hand-offs: an input copy waits until the previous job has read the
+    // input buffer (cpack); the kernel that fills the output buffer waits
+    // until the previous output copy has read it (cjoin[2..3]).  Both start
     // ordered after the caller's earlier work on `stream`.
     const size_t piece = (bytes / 2 + 255) / 256 * 256;
-    auto pieces = [&](int c0, cudaEvent_t after, void* dst, const void* src, cudaMemcpyKind kind) -> cudaError_t {
+    auto dense_pieces = [&](int c0, cudaEvent_t after, void* dst, const void* src, cudaMemcpyKind kind) -> cudaError_t {
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             const int c = c0 + k;
@@ -1018,22 +1046,95 @@ st_status stencil_run_host_many(st_grid_t g, int nsteps, int njobs, const void* 
         }
         return e;
     };
+    // dense host field <-> interior of a field-layout buffer, planes split in two
+    auto pad_pieces = [&](int c0, cudaEvent_t after, void* pad, void* host, bool to_device) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        char* interior = (char*)pad + (size_t)G.origin * G.esize;
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            const int c = c0 + k;
+            const size_t z0 = (size_t)G.nz * k / 2, z1 = (size_t)G.nz * (k + 1) / 2;
+            e = cudaStreamWaitEvent(g->cstream[c], after, 0);
+            if (e == cudaSuccess && z1 > z0) {
+                cudaMemcpy3DParms q = {};
+                const cudaPitchedPtr hp = make_cudaPitchedPtr(host, (size_t)G.nx * G.esize, (size_t)G.nx * G.esize,
+                                                              (size_t)G.ny);
+                const cudaPitchedPtr dp = make_cudaPitchedPtr(interior, (size_t)G.pitch * G.esize,
+                                                              (size_t)G.nx * G.esize, (size_t)G.pny);
+                q.srcPtr = to_device ? hp : dp;
+                q.dstPtr = to_device ? dp : hp;
+                q.srcPos = make_cudaPos(0, 0, z0);
+                q.dstPos = make_cudaPos(0, 0, z0);
+                q.extent = make_cudaExtent((size_t)G.nx * G.esize, (size_t)G.ny, z1 - z0);
+                q.kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+                e = cudaMemcpy3DAsync(&q, g->cstream[c]);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(g->cjoin[c], g->cstream[c]);
+        }
+        return e;
+    };
+    auto sweep = [&](const void* in, void* out) -> st_status {
+        ST_CUDA_TRY(launch_family(g->fam, sweep_args(g, in, out, g->step), s));
+        g->step += 1;
+        return ST_OK;
+    };
     ST_CUDA_TRY(cudaEventRecord(g->cpack, s));
     ST_CUDA_TRY(cudaEventRecord(g->cjoin[2], s));
     ST_CUDA_TRY(cudaEventRecord(g->cjoin[3], s));
     for (int i = 0; i < njobs; ++i) {
-        ST_CUDA_TRY(pieces(0, g->cpack, g->staging, host_in[i], cudaMemcpyHostToDevice));
+        const bool last = i == njobs - 1;
+        if (direct)
+            ST_CUDA_TRY(pad_pieces(0, g->cpack, g->pad_in, const_cast<void*>(host_in[i]), true));
+        else
+            ST_CUDA_TRY(dense_pieces(0, g->cpack, g->staging, host_in[i], cudaMemcpyHostToDevice));
         ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[0], 0));
         ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[1], 0));
-        ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 0, s));
-        ST_CUDA_TRY(cudaEventRecord(g->cpack, s));
-        rc = stencil_step(g, nsteps, stream);
-        if (rc != ST_OK) return rc;
-        ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[2], 0));
-        ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[3], 0));
-        ST_CUDA_TRY(launch_pack(G.esize, g->staging2, g->buf[g->cur], G, 1, s));
-        ST_CUDA_TRY(cudaEventRecord(g->cunpack, s));
-        ST_CUDA_TRY(pieces(2, g->cunpack, host_out[i], g->staging2, cudaMemcpyDeviceToHost));
+        bool out_padded = false;
+        if (!direct) {
+            ST_CUDA_TRY(launch_pack(G.esize, g->staging, g->buf[g->cur], G, 0, s));
+            ST_CUDA_TRY(cudaEventRecord(g->cpack, s));
+            rc = stencil_step(g, nsteps, stream);
+            if (rc != ST_OK) return rc;
+        } else if (nsteps == 1 && !last) {
+            ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[2], 0));
+            ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[3], 0));
+            rc = sweep(g->pad_in, g->pad_out);
+            if (rc != ST_OK) return rc;
+            ST_CUDA_TRY(cudaEventRecord(g->cpack, s));
+            out_padded = true;
+        } else {
+            // the first sweep reads pad_in and writes the current level
+            rc = refresh_ghosts(g, s);
+            if (rc != ST_OK) return rc;
+            rc = sweep(g->pad_in, g->buf[g->cur]);
+            if (rc != ST_OK) return rc;
+            ST_CUDA_TRY(cudaEventRecord(g->cpack, s));
+            if (nsteps >= 3) {
+                rc = stencil_step(g, nsteps - 2, stream);
+                if (rc != ST_OK) return rc;
+            }
+            if (nsteps >= 2) {
+                if (!last) {
+                    ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[2], 0));
+                    ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[3], 0));
+                    rc = sweep(g->buf[g->cur], g->pad_out);
+                    out_padded = true;
+                } else {
+                    rc = sweep(g->buf[g->cur], g->buf[1 - g->cur]);
+                    g->cur = 1 - g->cur;
+                }
+                if (rc != ST_OK) return rc;
+            }
+        }
+        if (out_padded) {
+            ST_CUDA_TRY(cudaEventRecord(g->cunpack, s));
+            ST_CUDA_TRY(pad_pieces(2, g->cunpack, g->pad_out, host_out[i], false));
+        } else {
+            ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[2], 0));
+            ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[3], 0));
+            ST_CUDA_TRY(launch_pack(G.esize, g->staging2, g->buf[g->cur], G, 1, s));
+            ST_CUDA_TRY(cudaEventRecord(g->cunpack, s));
+            ST_CUDA_TRY(dense_pieces(2, g->cunpack, host_out[i], g->staging2, cudaMemcpyDeviceToHost));
+        }
     }
     // the last results are on the host once `stream` passes this point
     ST_CUDA_TRY(cudaStreamWaitEvent(s, g->cjoin[2], 0));

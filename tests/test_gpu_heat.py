@@ -280,43 +280,54 @@ def test_run_host_end_to_end(nx, pinned_in, pinned_out):
         g.close()
 
 
-@pytest.mark.parametrize("nx,periodic", [(64, True), (45, False)])
+@pytest.mark.parametrize("shape,bc", [((18, 29, 64), "periodic"), ((18, 29, 45), "dirichlet"),
+                                      ((37, 70), "dirichlet"), ((12, 17, 40), "neumann")])
 @pytest.mark.parametrize("pinned", [True, False])
-def test_run_host_many_pipelined_jobs(nx, periodic, pinned):
+def test_run_host_many_pipelined_jobs(shape, bc, pinned):
     """Three independent jobs through one pipelined call (input copies,
-    sweeps and output copies overlapping across jobs on the copy streams):
+    sweeps and output copies overlapping across jobs on the copy streams;
+    inputs copied into a field-layout buffer that the first sweep reads, all
+    but the last job's results written by the last sweep to another one;
+    zero-flux grids through the dense staging form): for 0, 1, 2 and 9 steps
     every job's result equals the oracle's and, bit for bit, what
-    stencil_run_host gives for the same input; two jobs may share an output
+    stencil_run_host gives for the same input, and the grid's current level
+    holds the last job's result afterwards; two jobs may share an output
     buffer (the later result stays); a zero-job call does nothing."""
     from paper_2512_19851_gb300 import abi
     from paper_2512_19851_gb300.grid import Grid
-    shape = (18, 29, nx)
-    offs, w = seven_point(0.1)
-    rng = np.random.default_rng(nx + int(periodic))
+    offs, w = seven_point(0.1) if len(shape) == 3 else five_point(0.2)
+    periodic = bc == "periodic"
+    rng = np.random.default_rng(sum(shape) + len(bc))
     for dtype, npdt in ((torch.float32, np.float32), (torch.float64, np.float64)):
-        g = Grid(shape, offs, w, periodic=periodic, bc_value=0.25, dtype=dtype)
+        g = Grid(shape, offs, w, periodic=periodic, bc_value=0.25, dtype=dtype, neumann=bc == "neumann")
         fields = [rng.random(shape) for _ in range(3)]
         srcs = [torch.from_numpy(f.astype(npdt)) for f in fields]
-        dsts = [torch.full(shape, -1.0, dtype=dtype) for _ in range(3)]
         if pinned:
             srcs = [t.pin_memory() for t in srcs]
-            dsts = [t.pin_memory() for t in dsts]
         s = torch.cuda.current_stream()
-        abi.stencil_run_host_many(g.h, 9, [t.data_ptr() for t in srcs], [t.data_ptr() for t in dsts], s)
-        abi.stencil_run_host_many(g.h, 9, [], [], s)
-        g.sync()
-        one = torch.empty(shape, dtype=dtype)
-        for f, src, dst in zip(fields, srcs, dsts):
-            ref = oracle.sweep_const(f, offs, w, periodic, 0.25, 9)
-            assert rel_err(dst.numpy(), ref) <= (TOL64 if dtype == torch.float64 else TOL32)
-            abi.stencil_run_host(g.h, 9, src.data_ptr(), one.data_ptr(), s)
+        for nsteps in (0, 1, 2, 9):
+            dsts = [torch.full(shape, -1.0, dtype=dtype) for _ in range(3)]
+            if pinned:
+                dsts = [t.pin_memory() for t in dsts]
+            abi.stencil_run_host_many(g.h, nsteps, [t.data_ptr() for t in srcs], [t.data_ptr() for t in dsts], s)
+            abi.stencil_run_host_many(g.h, nsteps, [], [], s)
             g.sync()
-            assert np.array_equal(one.numpy(), dst.numpy())
-        shared = torch.empty(shape, dtype=dtype)
-        abi.stencil_run_host_many(g.h, 9, [srcs[0].data_ptr(), srcs[2].data_ptr()],
-                                  [shared.data_ptr(), shared.data_ptr()], s)
-        g.sync()
-        assert np.array_equal(shared.numpy(), dsts[2].numpy())
+            assert np.array_equal(g.current().cpu().numpy(), dsts[2].numpy())
+            one = torch.empty(shape, dtype=dtype)
+            for f, src, dst in zip(fields, srcs, dsts):
+                if bc == "neumann":
+                    ref = oracle.sweep_neumann(f, offs, w, nsteps)
+                else:
+                    ref = oracle.sweep_const(f, offs, w, periodic, 0.25, nsteps)
+                assert rel_err(dst.numpy(), ref) <= (TOL64 if dtype == torch.float64 else TOL32)
+                abi.stencil_run_host(g.h, nsteps, src.data_ptr(), one.data_ptr(), s)
+                g.sync()
+                assert np.array_equal(one.numpy(), dst.numpy())
+            shared = torch.empty(shape, dtype=dtype)
+            abi.stencil_run_host_many(g.h, nsteps, [srcs[0].data_ptr(), srcs[2].data_ptr()],
+                                      [shared.data_ptr(), shared.data_ptr()], s)
+            g.sync()
+            assert np.array_equal(shared.numpy(), dsts[2].numpy())
         g.close()
 
 
