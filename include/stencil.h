@@ -301,6 +301,9 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream);
 st_status stencil_tune_config(st_grid_t g, int* cfg);
 
 /*
+ * Defined by: Sec. III-B, the frontend's arrays filled from host data and
+ * read back with get() around the run of nodes that sync() executes; here
+ * that round trip is one call.
  * End-to-end form of stencil_step for callers whose data is on the host:
  * copies host_u0 (dense interior, C order, the grid's dtype) into the current
  * level, runs nsteps, copies the newest level's interior to host_uT.  A
@@ -317,6 +320,9 @@ st_status stencil_run_host(st_grid_t g, int nsteps, const void* host_u0, void* h
                            void* stream);
 
 /*
+ * Defined by: the same round trip as stencil_run_host (Sec. III-B), for the
+ * end-to-end measurement of a workload run again and again on new host
+ * data; the paper has no batched form of it.
  * Pipelined form of stencil_run_host for a stream of independent jobs on
  * one grid (each its own initial field): for i in [0, njobs), copies
  * host_in[i] (dense interior, C order, the grid's dtype) into the current
