@@ -265,3 +265,57 @@ def test_tile_passes_flag_selects_the_fp64_tile_option():
     assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES, abi.ST_NEUMANN) == "generic_point"
     assert name((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES | abi.ST_FLAG_GENERIC) == "generic_point"
 
+
+
+def test_tb2d_configuration_override(monkeypatch):
+    """ST_TB2D_CFG = "TX,TY,k" starts an FP64 2D grid within the 3x3
+    neighbourhood on the k-step static-tile kernel with that configuration;
+    malformed or oversized values, other grids and ST_FLAG_TILE_PASSES leave
+    the usual choice."""
+    offs = [(0, 0), (-1, 0), (1, 0), (0, -1), (0, 1)]
+
+    def made(dims, dtype, flags=0, bc=abi.ST_DIRICHLET, offsets=offs):
+        off = np.asarray(offsets, dtype=np.int32).reshape(-1)
+        h = abi.stencil_create(len(dims), dims, 0, off, [0.2] * (len(off) // len(dims)), None, bc, 0.0, dtype, 1,
+                               flags)
+        n = abi.stencil_info(h)[2]
+        cfg = list(abi.stencil_tune_config(h))
+        abi.stencil_destroy(h)
+        return n, cfg
+
+    monkeypatch.setenv("ST_TB2D_CFG", "16,14,3")
+    assert made((64, 80), abi.ST_F64) == ("tb2d_passes", [16, 14, 512, 3])
+    assert made((64, 80), abi.ST_F64, bc=abi.ST_PERIODIC)[0] == "tb2d_passes"
+    assert made((64, 80), abi.ST_F64, abi.ST_FLAG_TILE_PASSES)[0] == "tile2d_passes"
+    assert made((64, 80), abi.ST_F32)[0] == "tile2d_persistent"
+    assert made((64, 80), abi.ST_F64, bc=abi.ST_NEUMANN)[0] == "generic_point"
+    assert made((64, 80), abi.ST_F64, offsets=[(0, 0), (-2, 0), (2, 0), (0, -2), (0, 2)])[0] == "generic_point"
+    assert made((8, 9, 10), abi.ST_F64, offsets=[(0, 0, 0), (0, 0, 1), (0, 0, -1)])[0] != "tb2d_passes"
+    for bad in ("16,14", "0,14,3", "16,14,0", "x,y,z", "1000,1000,8"):
+        monkeypatch.setenv("ST_TB2D_CFG", bad)
+        assert made((64, 80), abi.ST_F64)[0] == "generic_point", bad
+    monkeypatch.delenv("ST_TB2D_CFG")
+    assert made((64, 80), abi.ST_F64) == ("generic_point", [0, 0, 0, 0])
+
+
+def test_run_host_many_arguments():
+    """Argument and state checks of the pipelined host form run before any
+    device work: a NULL handle, a negative step count or a NULL host pointer
+    is ST_ERR_ARG, an unbound grid ST_ERR_STATE, and the binding rejects
+    lists of different lengths."""
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_run_host_many(None, 1, [], [])
+    assert e.value.code == abi.ST_ERR_ARG
+    h = _create()
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_run_host_many(h, -1, [], [])
+    assert e.value.code == abi.ST_ERR_ARG
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_run_host_many(h, 1, [0], [0])
+    assert e.value.code == abi.ST_ERR_ARG
+    with pytest.raises(abi.StencilError) as e:
+        abi.stencil_run_host_many(h, 1, [], [])
+    assert e.value.code == abi.ST_ERR_STATE
+    with pytest.raises(ValueError):
+        abi.stencil_run_host_many(h, 1, [64], [])
+    abi.stencil_destroy(h)
