@@ -376,9 +376,10 @@ def extra_configs(dev, hbm_peak):
     g.set_field(u0)
     cfg = g.tune(100)
     t = _time(lambda: abi.stencil_step(g.h, 100, s), 20, s)
+    alu_us = 256 * 256 * 5 / FP64_INSTR_PER_S * 1e6
     out["heat2d_f64"] = {"glups": 256 * 256 * 100 / t / 1e9, "us_per_step": t / 100 * 1e6,
                          "us_per_run": t * 1e6, "kernel": g.kernel, "config": list(cfg),
-                         "alu_bound_us_per_step": 256 * 256 * 5 / FP64_INSTR_PER_S * 1e6}
+                         "bound": "alu", "alu_bound_us_per_step": alu_us, "alu_frac": alu_us / (t / 100 * 1e6)}
     g.close()
     # wave, radius-4 leapfrog FP32, 1000 steps
     wv = inputs.wave3d(n=N3, steps=1000)
