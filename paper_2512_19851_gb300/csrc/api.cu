@@ -275,8 +275,8 @@ st_status stencil_create(st_grid_t* out, int ndim, const int64_t* dims, int radi
         // "TX,TY,K": run k_tb2d with that configuration (tests, tuning sweeps)
         const char* env = std::getenv("ST_TB2D_CFG");
         int tx = 0, ty = 0, tk = 0;
-        if (!g->plan_use && env && std::sscanf(env, "%d,%d,%d", &tx, &ty, &tk) == 3 && tx >= 1 && ty >= 1 &&
-            tk >= 1 && tb2d_smem(tx, ty, tk) <= 200 * 1024 && tb2d_supports(g->fam)) {
+        if (!g->plan_use && env && std::sscanf(env, "%d,%d,%d", &tx, &ty, &tk) == 3 &&
+            tb2d_fits(g->g.nx, g->g.ny, tx, ty, tk) && tb2d_supports(g->fam)) {
             g->tb[0] = tx;
             g->tb[1] = ty;
             g->tb[2] = tk;
@@ -838,7 +838,8 @@ st_status stencil_tune(st_grid_t g, int nsteps, void* stream)
         }
         for (const auto& sh : shapes)
             for (int k : {1, 2, 3, 4, 5, 6, 8})
-                if (k <= nsteps) cands.push_back({false, {sh.first, sh.second, k}});
+                if (k <= nsteps && tb2d_fits(nx, ny, sh.first, sh.second, k))
+                    cands.push_back({false, {sh.first, sh.second, k}});
     }
     const size_t bytes = (size_t)g->g.elems * g->g.esize;
     void* keep = nullptr;

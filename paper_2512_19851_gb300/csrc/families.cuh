@@ -101,6 +101,8 @@ bool tile2d_supports(const FamilyDesc& d, int* variant, const char** name);
 // as ks single sweeps.  tb2d_smem: its dynamic shared memory for k steps.
 bool tb2d_supports(const Family& f);
 size_t tb2d_smem(int TX, int TY, int k);
+// the launch limits of a TX x TY tile grid of k steps on an nx x ny grid
+bool tb2d_fits(int64_t nx, int64_t ny, int TX, int TY, int k);
 cudaError_t launch_tb2d(const Family& f, const void* in, void* out, int TX, int TY, int ks, double bc,
                         cudaStream_t s);
 cudaError_t launch_cons_sweep(const Family& f, const SweepArgs& a, cudaStream_t s);

@@ -138,6 +138,13 @@ __global__ void __launch_bounds__(TB_THREADS) k_tb2d(const double* __restrict__ 
 
 size_t tb2d_smem(int TX, int TY, int k) { return 2 * (size_t)(TX + 2 * k) * (TY + 2 * k) * sizeof(double); }
 
+bool tb2d_fits(int64_t nx, int64_t ny, int TX, int TY, int k)
+{
+    return TX >= 1 && TY >= 1 && k >= 1 && TX + 2 * k <= 1024 && (int64_t)TX * TY <= (1 << 18) &&
+           tb2d_smem(TX, TY, k) <= 200 * 1024 && (nx + TX - 1) / TX <= 0x7fffffff && (ny + TY - 1) / TY <= 65535 &&
+           nx < 0x7fffffff && ny < 0x7fffffff;
+}
+
 bool tb2d_supports(const Family& f)
 {
     const GenParams& G = f.gp;
@@ -149,9 +156,7 @@ bool tb2d_supports(const Family& f)
 
 cudaError_t launch_tb2d(const Family& f, const void* in, void* out, int TX, int TY, int ks, double bc, cudaStream_t s)
 {
-    if (!tb2d_supports(f) || TX < 1 || TY < 1 || ks < 1 || TX + 2 * ks > 1024 || TX * TY > (1 << 18) ||
-        tb2d_smem(TX, TY, ks) > 200 * 1024)
-        return cudaErrorInvalidValue;
+    if (!tb2d_supports(f) || !tb2d_fits(f.g.nx, f.g.ny, TX, TY, ks)) return cudaErrorInvalidValue;
     const GenParams& G = f.gp;
     TB2Params P{};
     P.nx = (int)f.g.nx;
