@@ -404,6 +404,22 @@ st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_
 st_status stencil_reduce_noalloc(st_grid_t g, const void* a, const void* b, double* dev_out, void* stream);
 
 /*
+ * Defined by: Sec. III-A, Example 1's loop of stencil steps followed by a
+ * read of a result (the configurations reduce the field after its steps:
+ * the heat workload's norms, in double precision).
+ * stencil_step(g, nsteps) followed by stencil_reduce of the newest level
+ * (dev_out[0..2] = sum u, sum u^2, max |u| over the interior, in double
+ * precision).  For a constant symmetric 3D 7-point star in FP32 (Dirichlet or
+ * periodic, no source) the last sweep computes the reduction of the values
+ * it writes (compensated float pairs per thread, combined in double in a
+ * fixed order), so the step reads its field once; results are deterministic
+ * and agree with stencil_reduce to its precision (about 1e-13 relative to
+ * sum |u|), not bit for bit.  Other grids run the two calls.  nsteps = 0
+ * reduces the current level.
+ */
+st_status stencil_step_reduce(st_grid_t g, int nsteps, double* dev_out, void* stream);
+
+/*
  * Defined by: the adjoint workload's loss L = 0.5 ||u_T - u_target||^2, whose
  * gradient dL/du_T = u_T - u_target seeds the transpose sweep; no
  * counterpart in the paper.

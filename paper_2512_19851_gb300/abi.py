@@ -63,6 +63,7 @@ SIGNATURES = {
     "stencil_snapshot": (_I, [_VP, _VP, _PI64, _VP]),
     "stencil_restore": (_I, [_VP, _VP, _I64, _VP]),
     "stencil_step": (_I, [_VP, _I, _VP]),
+    "stencil_step_reduce": (_I, [_VP, _I, _VP, _VP]),
     "stencil_tune": (_I, [_VP, _I, _VP]),
     "stencil_tune_config": (_I, [_VP, _PI]),
     "stencil_run_host": (_I, [_VP, _I, _VP, _VP, _VP]),
@@ -245,6 +246,13 @@ def stencil_tune_config(h):
     cfg = (ctypes.c_int * 4)()
     _check(lib().stencil_tune_config(h, cfg), "stencil_tune_config")
     return tuple(cfg)
+
+
+def stencil_step_reduce(h, nsteps, out_ptr, stream=None) -> None:
+    """nsteps sweeps, then (sum, sum of squares, max |u|) of the newest level
+    into the 3 doubles at out_ptr (device)."""
+    _check(lib().stencil_step_reduce(h, int(nsteps), ctypes.c_void_p(int(out_ptr)), ctypes.c_void_p(_stream(stream))),
+           "stencil_step_reduce")
 
 
 def stencil_run_host(h, nsteps, host_u0_ptr, host_uT_ptr, stream=None) -> None:

@@ -1171,6 +1171,35 @@ st_status stencil_reduce(st_grid_t g, const void* a, const void* b, double* dev_
     return ST_OK;
 }
 
+st_status stencil_step_reduce(st_grid_t g, int nsteps, double* dev_out, void* stream)
+{
+    if (!g || !dev_out) return fail(ST_ERR_ARG, "stencil_step_reduce: NULL argument");
+    if (nsteps < 0) return fail(ST_ERR_ARG, "stencil_step_reduce: negative step count");
+    st_status rc = check_ready(g, "stencil_step_reduce");
+    if (rc != ST_OK) return rc;
+    rc = ensure_scratch(g);
+    if (rc != ST_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the last sweep reduces the level it writes where the family has that
+    // kernel (FP32 constant symmetric 3D star, no ghost refresh from outside
+    // the sweep, no source); otherwise the sweeps, then stencil_reduce
+    const bool fused = nsteps >= 1 && star3d_reduce_supported(g->fam) && g->levels == 1 && g->src < 0 &&
+                       !g->caller_ghosts && g->bc != ST_NEUMANN && g->g.npoints > 0;
+    if (!fused) {
+        rc = stencil_step(g, nsteps, stream);
+        if (rc != ST_OK) return rc;
+        return stencil_reduce(g, g->buf[g->cur], nullptr, dev_out, stream);
+    }
+    rc = stencil_step(g, nsteps - 1, stream);  // also refreshes stale ghosts
+    if (rc != ST_OK) return rc;
+    g->last = s;
+    SweepArgs a = sweep_args(g, g->buf[g->cur], g->buf[1 - g->cur], g->step);
+    ST_CUDA_TRY(launch_star3d_reduce(g->fam, a, g->d_partials, g->red_blocks, dev_out, s));
+    g->cur = 1 - g->cur;
+    g->step += 1;
+    return ST_OK;
+}
+
 st_status stencil_residual(st_grid_t g, const void* u, const void* target, void* lambda, double* dev_loss,
                            void* stream)
 {

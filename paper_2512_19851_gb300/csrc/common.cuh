@@ -101,6 +101,8 @@ cudaError_t launch_generic_adjoint(int esize, const void* u_t, const void* lam_i
 cudaError_t launch_neumann_adjoint(int esize, const void* lam_in, void* lam_out, const GenParams& P, int r, int rz,
                                    cudaStream_t s);
 cudaError_t launch_fill_ghosts(int esize, void* buf, const Geom& g, double value, cudaStream_t s);
+// dev_out = the combination of nblocks (sum, sum of squares, max) partials
+cudaError_t launch_reduce_final(const double* partials, int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_mirror_ghosts(int esize, void* buf, const Geom& g, cudaStream_t s);
 cudaError_t launch_pack(int esize, void* dense, void* padded, const Geom& g, int dir, cudaStream_t s);
 // Grid size of the reduction kernels for grid g: the blocks resident at once

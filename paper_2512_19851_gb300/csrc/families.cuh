@@ -83,6 +83,12 @@ cudaError_t launch_family_adjoint(const Family& f, const AdjointArgs& a, cudaStr
 // Optimised kernels (return cudaErrorNotSupported when the case is not theirs)
 cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_star3d_adjoint(const Family& f, const AdjointArgs& a, cudaStream_t s);
+// One sweep of a constant symmetric FP32 3D star that also reduces the level it
+// writes into out = (sum, sum of squares, max |u|) over the interior, through
+// `partials` (3 doubles per block, room for `cap` blocks).
+bool star3d_reduce_supported(const Family& f);
+cudaError_t launch_star3d_reduce(const Family& f, const SweepArgs& a, double* partials, int cap, double* out,
+                                 cudaStream_t s);
 // gk += part (an FP32 partial gradient into the FP64 gradient), n elements, a
 // multiple of 4, both buffers 16-byte aligned.
 cudaError_t launch_grad_flush(void* part, double* gk, int64_t n, cudaStream_t s);

@@ -1110,4 +1110,11 @@ cudaError_t launch_reduce(int esize, const void* a, const void* b, const Geom& g
     return launch_dependent(k_reduce_final, dim3(1), dim3(256), 0, s, (const double*)partials, nblocks, out, mode);
 }
 
+// dev_out = the combination of nblocks (sum, sum of squares, max) partials
+// (the second kernel of a reduction whose first pass ran elsewhere).
+cudaError_t launch_reduce_final(const double* partials, int nblocks, double* out, cudaStream_t s)
+{
+    return launch_dependent(k_reduce_final, dim3(1), dim3(256), 0, s, partials, nblocks, out, 0);
+}
+
 }  // namespace st

@@ -46,6 +46,7 @@ struct Star1Params {
     double wc, wxm, wxp, wym, wyp, wzm, wzp;  // constant parts (alpha)
     double bc, bxm, bxp, bym, byp, bzm, bzp;  // per-cell parts (beta)
     int* status;
+    double* red;  // RED: per-block (sum, sum of squares, max |u|) of the written level, 3 doubles per block
 };
 
 template <typename T>
@@ -160,9 +161,36 @@ __device__ __forceinline__ void set_timeout(int* status)
     if (status) atomicCAS(status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
 }
 
+// RED: a running compensated sum in a float pair (Knuth's two-sum on each
+// addition; the low part gathers the rounding errors), about 48 bits.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float v)
+{
+    const float s = __fadd_rn(hi, v);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// RED: one written value into the thread's sum, sum of squares (the square's
+// rounding error, exact by an fma, goes to the low part) and max |v|.
+__device__ __forceinline__ void red_put(float (&acc)[5], float v)
+{
+    ff_add(acc[0], acc[1], v);
+    const float p = __fmul_rn(v, v);
+    ff_add(acc[2], acc[3], p);
+    acc[3] = __fadd_rn(acc[3], fmaf(v, v, -p));
+    acc[4] = fmaxf(acc[4], fabsf(v));
+}
+
 // CONS: the conservative face-averaged operator (KAPPA set): the coefficient
 // tile carries the same halo rows as u and is staged for every plane.
-template <typename T, bool KAPPA, bool SYM, bool PERIODIC, int G, bool CONS = false>
+// RED (FP32): the sweep also reduces the level it writes, as stencil_reduce
+// would (sum, sum of squares, max |u| over the interior), so the step that
+// ends with a reduction reads its field once: every consumer thread adds its
+// written values to compensated float pairs, the consumer warps combine them
+// in double in a fixed order, and the block's partial goes to P.red.
+template <typename T, bool KAPPA, bool SYM, bool PERIODIC, int G, bool CONS = false, bool RED = false>
 __global__ void __launch_bounds__(block_threads<CONS>(), 1)
 k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kappa, const __grid_constant__ Star1Params P)
 {
@@ -251,6 +279,10 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
     const int NC = consumer_warps<CONS>() * 32;
     const int ngx = (int)((P.nx + VN - 1) / VN);
     const unsigned FULLM = 0xffffffffu;
+    // RED: sum (hi, lo), sum of squares (hi, lo), max |u| of this thread's written values
+    float racc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    // A wait that runs out records the timeout and leaves; with RED it leaves
+    // the streaming loop for the consumers' final combination instead.
     uint32_t gq = 0;
     for (int u = blockIdx.x; u < P.units; u += gridDim.x) {
         const int yt = u % P.nyt, zc = u / P.nyt;
@@ -285,7 +317,8 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
         T kbl[CONS ? G : 1][2][VN], kcn[CONS ? G : 1][2][VN], kab[CONS ? G : 1][2][VN];
         if (!wait_q(0) || !wait_q(1)) {
             set_timeout(P.status);
-            return;
+            if constexpr (RED) goto red_combine;
+            else return;
         }
 #pragma unroll
         for (int g = 0; g < G; ++g)
@@ -307,7 +340,8 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
         for (int i = 0; i < zce; ++i) {
             if (!ptx::mbar_wait_warp(&full[slot_a], par_a)) {
                 set_timeout(P.status);
-                return;
+                if constexpr (RED) goto red_combine;
+                else return;
             }
             const T* sa = ring + (size_t)slot_a * P.stage_elems + P.xl;
             const T* sc = ring + (size_t)slot_c * P.stage_elems + P.xl;
@@ -380,8 +414,15 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                         T* op = oplane + (int64_t)(trow[g] + r) * P.pitch + x;
                         if (x + VN <= P.nx) {
                             stv(op, o);
+                            if constexpr (RED) {
+#pragma unroll
+                                for (int j = 0; j < VN; ++j) red_put(racc, o[j]);
+                            }
                         } else {
-                            for (int j = 0; j < VN && x + j < P.nx; ++j) op[j] = o[j];
+                            for (int j = 0; j < VN && x + j < P.nx; ++j) {
+                                op[j] = o[j];
+                                if constexpr (RED) red_put(racc, o[j]);
+                            }
                         }
                     }
                 }
@@ -407,6 +448,41 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
             }
         }
         gq = base + zce + 2;
+    }
+    if constexpr (!RED) {
+        return;  // (the label below is RED's; this keeps it referenced in every instance)
+        goto red_combine;
+    }
+red_combine:
+    if constexpr (RED) {
+        // the consumer warps only (the producer warp has left): named barrier 1
+        double* wred = reinterpret_cast<double*>(empty + P.NS);  // 3 doubles per consumer warp
+        double rs = (double)racc[0] + (double)racc[1];
+        double rq = (double)racc[2] + (double)racc[3];
+        double rm = (double)racc[4];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rs += __shfl_down_sync(FULLM, rs, o);
+            rq += __shfl_down_sync(FULLM, rq, o);
+            rm = fmax(rm, __shfl_down_sync(FULLM, rm, o));
+        }
+        if (lane == 0) {
+            wred[3 * warp + 0] = rs;
+            wred[3 * warp + 1] = rq;
+            wred[3 * warp + 2] = rm;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");
+        if (threadIdx.x == 0) {
+            double bs = 0.0, bq = 0.0, bm = 0.0;
+            for (int w = 0; w < consumer_warps<CONS>(); ++w) {
+                bs += wred[3 * w + 0];
+                bq += wred[3 * w + 1];
+                bm = fmax(bm, wred[3 * w + 2]);
+            }
+            P.red[3 * blockIdx.x + 0] = bs;
+            P.red[3 * blockIdx.x + 1] = bq;
+            P.red[3 * blockIdx.x + 2] = bm;
+        }
     }
 }
 
@@ -487,8 +563,9 @@ bool pick_cfg(const Geom& g, int kappa, Cfg* c)
     return true;
 }
 
-template <typename T, bool KAPPA, bool SYM, bool PERIODIC, bool CONS = false>
-cudaError_t launch_t(const Family& f, const SweepArgs& a, cudaStream_t s)
+template <typename T, bool KAPPA, bool SYM, bool PERIODIC, bool CONS = false, bool RED = false>
+cudaError_t launch_t(const Family& f, const SweepArgs& a, cudaStream_t s, double* red = nullptr, int red_cap = 0,
+                     int* red_blocks = nullptr)
 {
     const Geom& g = f.g;
     const int kmode = CONS ? K_HALO : (KAPPA ? K_TILE : K_NONE);
@@ -529,15 +606,22 @@ cudaError_t launch_t(const Family& f, const SweepArgs& a, cudaStream_t s)
     P.bxm = k.b[2][0][0];
     P.bxp = k.b[2][1][0];
     P.status = a.status;
-    const size_t smem = (size_t)c.NS * P.stage_elems * sizeof(T) + 2 * sizeof(uint64_t) * c.NS;
+    P.red = red;
+    // RED: 3 doubles per consumer warp for the block's combination
+    const size_t smem = (size_t)c.NS * P.stage_elems * sizeof(T) + 2 * sizeof(uint64_t) * c.NS +
+                        (RED ? 3 * sizeof(double) * consumer_warps<CONS>() : 0);
     static bool attr_set[2] = {false, false};
-    auto fn = c.G == 1 ? k_star1<T, KAPPA, SYM, PERIODIC, 1, CONS> : k_star1<T, KAPPA, SYM, PERIODIC, 2, CONS>;
+    auto fn = c.G == 1 ? k_star1<T, KAPPA, SYM, PERIODIC, 1, CONS, RED> : k_star1<T, KAPPA, SYM, PERIODIC, 2, CONS, RED>;
     if (!attr_set[c.G - 1]) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         attr_set[c.G - 1] = true;
     }
     const int grid = (int)std::min<int64_t>(P.units, sm_count());
+    if (RED) {
+        if (!red || grid > red_cap) return cudaErrorInvalidValue;
+        if (red_blocks) *red_blocks = grid;
+    }
     return launch_dependent(fn, dim3(grid), dim3(block_threads<CONS>()), smem, s, (const T*)a.in, (T*)a.out,
                             (const T*)a.kappa, P);
 }
@@ -571,6 +655,29 @@ cudaError_t launch_star3d(const Family& f, const SweepArgs& a, cudaStream_t s)
     if (dbl) return f.has_beta ? ST_DISPATCH(double, true) : ST_DISPATCH(double, false);
     return f.has_beta ? ST_DISPATCH(float, true) : ST_DISPATCH(float, false);
 #undef ST_DISPATCH
+}
+
+// The sweep fused with the reduction of the level it writes: FP32, constant
+// symmetric weights (the 3D heat workloads).
+bool star3d_reduce_supported(const Family& f)
+{
+    if (f.kind != FAM_STAR3D || f.g.esize != 4 || f.has_beta) return false;
+    const StarCoef& k = f.sc;
+    for (int ax = 0; ax < 3; ++ax)
+        for (int sd = 0; sd < 2; ++sd)
+            if (k.a[ax][sd][0] != k.a[0][0][0]) return false;
+    return true;
+}
+
+cudaError_t launch_star3d_reduce(const Family& f, const SweepArgs& a, double* partials, int cap, double* out,
+                                 cudaStream_t s)
+{
+    if (!star3d_reduce_supported(f)) return cudaErrorNotSupported;
+    int nb = 0;
+    cudaError_t e = f.periodic ? launch_t<float, false, true, true, false, true>(f, a, s, partials, cap, &nb)
+                               : launch_t<float, false, true, false, false, true>(f, a, s, partials, cap, &nb);
+    if (e != cudaSuccess) return e;
+    return launch_reduce_final(partials, nb, out, s);
 }
 
 // The conservative face-averaged operator (3D) on the staged pipeline.

@@ -120,3 +120,66 @@ def test_reduce_rejects_misaligned_buffers():
         abi.stencil_reduce_noalloc(g.h, g.bufs[0].data_ptr(), g.bufs[1].data_ptr() + 8, out.data_ptr(),
                                    torch.cuda.current_stream())
     g.close()
+
+
+@pytest.mark.parametrize("shape,periodic", [((40, 52, 68), False), ((17, 23, 45), True), ((64, 64, 512), True),
+                                            ((3, 64, 8), False), ((130, 33, 96), True)])
+def test_step_reduce_fused_sweep_matches_oracle(shape, periodic):
+    """stencil_step_reduce: the last sweep of an FP32 constant symmetric 3D
+    star reduces the level it writes.  The field equals stencil_step's bit
+    for bit; the sums agree with the oracle's double sums of the same FP32
+    values within 1e-12 of sum |u| and the maximum exactly; nsteps = 0 reduces
+    the current level; every result is the same on a repeated run."""
+    from paper_2512_19851_gb300 import abi
+    from paper_2512_19851_gb300.grid import Grid
+    offs, w = seven_point(0.1)
+    u0 = (np.random.default_rng(sum(shape)).random(shape) - 0.3).astype(np.float32)
+    s = torch.cuda.current_stream()
+    outs = []
+    for rep in range(2):
+        g = Grid(shape, offs, w, periodic=periodic, bc_value=0.5, dtype=torch.float32)
+        g.set_field(u0)
+        out = torch.zeros(3, dtype=torch.float64, device=g.device)
+        abi.stencil_step_reduce(g.h, 7, out.data_ptr(), s)
+        g.sync()
+        got = g.current().cpu().numpy()
+        outs.append(out.cpu().numpy())
+        out0 = torch.zeros(3, dtype=torch.float64, device=g.device)
+        abi.stencil_step_reduce(g.h, 0, out0.data_ptr(), s)
+        g.sync()
+        g.close()
+        _check(out0.cpu().numpy(), oracle.reduce(got), got.astype(np.float64))
+    assert np.array_equal(outs[0], outs[1])
+    g = Grid(shape, offs, w, periodic=periodic, bc_value=0.5, dtype=torch.float32)
+    g.set_field(u0)
+    g.step(7)
+    g.sync()
+    ref_field = g.current().cpu().numpy()
+    g.close()
+    assert np.array_equal(got, ref_field)
+    _check(outs[0], oracle.reduce(got), got.astype(np.float64))
+
+
+def test_step_reduce_unfused_grids_equal_the_two_calls():
+    """Grids without the fused sweep (FP64, per-cell weights) run stencil_step
+    and stencil_reduce: the same bits as the two calls."""
+    from paper_2512_19851_gb300 import abi
+    from paper_2512_19851_gb300.grid import Grid
+    offs, w = seven_point(0.1)
+    shape = (20, 24, 36)
+    u0 = np.random.default_rng(3).random(shape)
+    s = torch.cuda.current_stream()
+    res = []
+    for fused_call in (True, False):
+        g = Grid(shape, offs, w, periodic=True, dtype=torch.float64)
+        g.set_field(u0)
+        out = torch.zeros(3, dtype=torch.float64, device=g.device)
+        if fused_call:
+            abi.stencil_step_reduce(g.h, 5, out.data_ptr(), s)
+        else:
+            abi.stencil_step(g.h, 5, s)
+            abi.stencil_reduce(g.h, g.bufs[g.current_slot()].data_ptr(), 0, out.data_ptr(), s)
+        g.sync()
+        res.append(out.cpu().numpy())
+        g.close()
+    assert np.array_equal(res[0], res[1])
