@@ -161,27 +161,34 @@ __device__ __forceinline__ void set_timeout(int* status)
     if (status) atomicCAS(status, 0, (int)ST_ERR_DEVICE_TIMEOUT);
 }
 
-// RED: a running compensated sum in a float pair (Knuth's two-sum on each
-// addition; the low part gathers the rounding errors), about 48 bits.
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float v)
-{
-    const float s = __fadd_rn(hi, v);
-    const float bp = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
-    hi = s;
-    lo = __fadd_rn(lo, e);
-}
+// RED: the thread's running sum and sum of squares as compensated float pairs
+// (Knuth's two-sum on each addition, the low part gathering the rounding
+// errors; about 48 bits), in two streams (even and odd values) advanced
+// together by packed FP32x2 instructions, and max |v|.
+__device__ __forceinline__ float2 padd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
-// RED: one written value into the thread's sum, sum of squares (the square's
-// rounding error, exact by an fma, goes to the low part) and max |v|.
-__device__ __forceinline__ void red_put(float (&acc)[5], float v)
-{
-    ff_add(acc[0], acc[1], v);
-    const float p = __fmul_rn(v, v);
-    ff_add(acc[2], acc[3], p);
-    acc[3] = __fadd_rn(acc[3], fmaf(v, v, -p));
-    acc[4] = fmaxf(acc[4], fabsf(v));
-}
+struct RedAcc {
+    float2 hs{0.f, 0.f}, ls{0.f, 0.f}, hq{0.f, 0.f}, lq{0.f, 0.f};
+    float m = 0.f;
+    __device__ __forceinline__ static void two_sum(float2& hi, float2& lo, float2 x)
+    {
+        const float2 s = padd2(hi, x);
+        const float2 bp = psub2(s, hi);
+        const float2 e = padd2(psub2(hi, psub2(s, bp)), psub2(x, bp));
+        hi = s;
+        lo = padd2(lo, e);
+    }
+    // two written values (a ragged end passes 0 for the second: an exact no-op)
+    __device__ __forceinline__ void put(float2 x)
+    {
+        two_sum(hs, ls, x);
+        const float2 p = __fmul2_rn(x, x);
+        two_sum(hq, lq, p);
+        lq = padd2(lq, __ffma2_rn(x, x, make_float2(-p.x, -p.y)));  // the square's exact rounding error
+        m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.y)));
+    }
+};
 
 // CONS: the conservative face-averaged operator (KAPPA set): the coefficient
 // tile carries the same halo rows as u and is staged for every plane.
@@ -279,8 +286,7 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
     const int NC = consumer_warps<CONS>() * 32;
     const int ngx = (int)((P.nx + VN - 1) / VN);
     const unsigned FULLM = 0xffffffffu;
-    // RED: sum (hi, lo), sum of squares (hi, lo), max |u| of this thread's written values
-    float racc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    RedAcc racc;  // RED: this thread's written values
     // A wait that runs out records the timeout and leaves; with RED it leaves
     // the streaming loop for the consumers' final combination instead.
     uint32_t gq = 0;
@@ -416,12 +422,12 @@ k_star1(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ kap
                             stv(op, o);
                             if constexpr (RED) {
 #pragma unroll
-                                for (int j = 0; j < VN; ++j) red_put(racc, o[j]);
+                                for (int j = 0; j < VN; j += 2) racc.put(make_float2(o[j], o[j + 1]));
                             }
                         } else {
                             for (int j = 0; j < VN && x + j < P.nx; ++j) {
                                 op[j] = o[j];
-                                if constexpr (RED) red_put(racc, o[j]);
+                                if constexpr (RED) racc.put(make_float2(o[j], 0.f));
                             }
                         }
                     }
@@ -457,9 +463,9 @@ red_combine:
     if constexpr (RED) {
         // the consumer warps only (the producer warp has left): named barrier 1
         double* wred = reinterpret_cast<double*>(empty + P.NS);  // 3 doubles per consumer warp
-        double rs = (double)racc[0] + (double)racc[1];
-        double rq = (double)racc[2] + (double)racc[3];
-        double rm = (double)racc[4];
+        double rs = ((double)racc.hs.x + (double)racc.ls.x) + ((double)racc.hs.y + (double)racc.ls.y);
+        double rq = ((double)racc.hq.x + (double)racc.lq.x) + ((double)racc.hq.y + (double)racc.lq.y);
+        double rm = (double)racc.m;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             rs += __shfl_down_sync(FULLM, rs, o);
